@@ -1,0 +1,852 @@
+/*
+ * eco_oracle.c -- plain, slow, obviously-correct CPU oracle for one environment
+ * step of the ecological simulator of arXiv 2510.18221 ("The Emergence of
+ * Complex Behavior in Large-Scale Ecological Environments").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call this file:
+ * only the test suite, the smoke check and the CPU-baseline leg of the
+ * benchmark load it.  It shares no code, header, table or constant generator
+ * with the CUDA library; every rule below is restated from the paper (and the
+ * concrete rule set the build fixes where the paper leaves a gap; each such
+ * reading is listed in the design notes).
+ *
+ * Paper passages followed (sections of the paper):
+ *   Sec. 3.1  Ecological Games: population function (alive mask + parents).
+ *   Sec. 3.2  Environment: grid world, resources, sensors, actions, move
+ *             cancellation, attack, eat, single-parent reproduction behind
+ *             the parent.
+ *   Sec. 3.3  Policies: per-agent MLP, softmax sampling, bfloat16 weights,
+ *             Kaiming init with zero biases, Gaussian mutation of all
+ *             parameters of the child.
+ *   App. E    the step runs every phase of the environment each step.
+ *
+ * Precision: the policy runs in FP64 on the FP32-stored master parameters
+ * (or on their exact dequantised BF16 / FP8-e4m3 forms).  All world state is
+ * integer.  Random numbers are Philox4x32-10 (Salmon et al., SC'11), keyed by
+ * (seed, stream) and counted by (step, index, sub, 0), so no draw depends on
+ * evaluation order.
+ *
+ * Build: gcc -std=c99 -O2 -ffp-contract=off -fopenmp -fPIC -shared -lm.
+ * OpenMP is used only across agents in the policy phase and across slots in
+ * weight initialisation; every agent's result is independent of the thread
+ * count.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Configuration and state (all arrays are owned by the caller).            */
+/* ------------------------------------------------------------------------ */
+
+enum {
+  ORC_FP32 = 0,
+  ORC_BF16 = 1,
+  ORC_FP8 = 2
+};
+
+enum {
+  ORC_AUTO_EAT = 1,     /* small config: eating is automatic on the cell   */
+  ORC_ROTATE_OBS = 2,   /* egocentric patch rotated so facing is "up"      */
+  ORC_CANCEL_ALL = 4,   /* the paper's rule: any contested move is cancelled */
+  ORC_GREEDY = 8        /* argmax of the logits, no Gumbel noise           */
+};
+
+/* Philox stream identifiers (key word 1). */
+enum {
+  ST_WALL = 1,
+  ST_FOOD_INIT = 2,
+  ST_PLACE = 3,
+  ST_FACING_INIT = 4,
+  ST_W_INIT = 5,
+  ST_SAMPLE = 6,
+  ST_CLAIM_MOVE = 7,
+  ST_CLAIM_ATTACK = 8,
+  ST_CLAIM_BIRTH = 9,
+  ST_MUTATE = 10,
+  ST_REGROW = 11
+};
+
+/* Action codes.  Small config: 0..5; mid and larger configs add 6..8. */
+enum {
+  A_STAY = 0,
+  A_NORTH = 1,
+  A_SOUTH = 2,
+  A_EAST = 3,
+  A_WEST = 4,
+  A_ATTACK = 5,
+  A_TURN_LEFT = 6,
+  A_TURN_RIGHT = 7,
+  A_EAT = 8
+};
+
+typedef struct {
+  int32_t side;        /* L: the grid is L x L and toroidal              */
+  int32_t slots;       /* S: agent slots (alive or free)                 */
+  int32_t init_alive;  /* K: agents placed at reset                      */
+  int32_t patch_k;     /* k: odd side of the egocentric patch            */
+  int32_t n_scalars;   /* 4 (energy + 3 zeros) or 8 (+ facing one-hot)   */
+  int32_t hidden;      /* H                                              */
+  int32_t n_actions;   /* A: 6 or 9                                      */
+  int32_t precision;   /* ORC_FP32 / ORC_BF16 / ORC_FP8                  */
+  int32_t flags;       /* ORC_* flags                                    */
+  uint32_t seed;
+  float sigma;         /* mutation standard deviation                    */
+  float food_density;  /* initial Bernoulli food probability             */
+  float regrow_p;      /* per-step Bernoulli regrowth probability        */
+  float wall_density;  /* Bernoulli wall probability                     */
+  int32_t e_init, e_metab, e_food, e_repro, attack_num, attack_den;
+} orc_config;
+
+typedef struct {
+  uint8_t *food;       /* [L*L] 0/1                                      */
+  uint8_t *wall;       /* [L*L] 0/1                                      */
+  int32_t *occ;        /* [L*L] slot standing on the cell, or -1         */
+  uint8_t *alive;      /* [S]                                            */
+  int32_t *x, *y;      /* [S] column, row                                */
+  uint8_t *facing;     /* [S] 0 N, 1 E, 2 S, 3 W                         */
+  int32_t *energy;     /* [S]                                            */
+  int32_t *parent;     /* [S] parent slot, -1 for founders               */
+  int32_t *birth_step; /* [S] step of birth, -1 for founders             */
+  float *master;       /* [S][P] parameters, logical order (see below)   */
+  int64_t *step;       /* the step counter t                             */
+} orc_state;
+
+typedef struct {
+  int64_t agent_steps;        /* agents alive when the step began        */
+  int64_t act[16];            /* histogram of chosen actions             */
+  int64_t moves;              /* successful moves                        */
+  int64_t move_blocked;       /* target wall or occupied at step start   */
+  int64_t move_lost;          /* lost the claim (or cancelled)           */
+  int64_t eaten;              /* food units eaten                        */
+  int64_t attacks;            /* attack actions taken                    */
+  int64_t attack_hits;        /* energy transfers made                   */
+  int64_t energy_transferred; /* energy moved by attacks                 */
+  int64_t deaths;
+  int64_t dead_energy;        /* sum of energies (<= 0) of agents that died */
+  int64_t births;
+  int64_t failed_births;      /* birth-cell winners left without a slot   */
+  int64_t regrown;            /* cells that regrew food                  */
+  int64_t alive;              /* alive at the end of the step            */
+  int64_t food_total;         /* food cells at the end of the step       */
+  int64_t energy_total;       /* sum of alive energies at the end        */
+} orc_stats;
+
+/* ------------------------------------------------------------------------ */
+/* Parameter layout (logical order).  Sec. 3.3: a per-agent MLP.             */
+/* W1 [H][D] row-major, b1 [H], W2 [H][H], b2 [H], W3 [A][H], b3 [A].        */
+/* ------------------------------------------------------------------------ */
+
+int orc_obs_dim(const orc_config *c) {
+  return 3 * c->patch_k * c->patch_k + c->n_scalars;
+}
+
+int orc_n_params(const orc_config *c) {
+  int D = orc_obs_dim(c), H = c->hidden, A = c->n_actions;
+  return H * D + H + H * H + H + A * H + A;
+}
+
+/* Offsets of the six parameter blocks. */
+static void param_offsets(const orc_config *c, int *oW1, int *ob1, int *oW2,
+                          int *ob2, int *oW3, int *ob3) {
+  int D = orc_obs_dim(c), H = c->hidden, A = c->n_actions;
+  *oW1 = 0;
+  *ob1 = H * D;
+  *oW2 = *ob1 + H;
+  *ob2 = *oW2 + H * H;
+  *oW3 = *ob2 + H;
+  *ob3 = *oW3 + A * H;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, from Salmon, Moraes, Dror, Shaw, "Parallel random numbers: */
+/* as easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64 multiplies with  */
+/* a Weyl-sequence key schedule.                                            */
+/* ------------------------------------------------------------------------ */
+
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  int round;
+  for (round = 0; round < 10; round++) {
+    uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+    uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+    uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+    uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+    uint32_t n0 = hi1 ^ x1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ x3 ^ k1;
+    uint32_t n3 = lo0;
+    x0 = n0; x1 = n1; x2 = n2; x3 = n3;
+    k0 += 0x9E3779B9u; /* golden ratio            */
+    k1 += 0xBB67AE85u; /* sqrt(3) - 1             */
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* One draw: key = (seed, stream), counter = (a, b, d, 0). */
+static void draw4(const orc_config *c, uint32_t stream, uint32_t a, uint32_t b,
+                  uint32_t d, uint32_t out[4]) {
+  uint32_t ctr[4], key[2];
+  ctr[0] = a; ctr[1] = b; ctr[2] = d; ctr[3] = 0;
+  key[0] = c->seed; key[1] = stream;
+  orc_philox(ctr, key, out);
+}
+
+/* Uniform in (0,1): the top 24 bits with the lowest forced to one, times
+ * 2^-24.  An odd integer below 2^24 times a power of two is exact in FP32
+ * and FP64, and the value is never 0 or 1. */
+double orc_uniform(uint32_t r) {
+  return (double)((r >> 8) | 1u) * (1.0 / 16777216.0);
+}
+
+/* Four standard normals from one Philox block by Box-Muller
+ * (Box & Muller, 1958): pairs (u0,u1) and (u2,u3). */
+void orc_normals4(const uint32_t r[4], double n[4]) {
+  const double two_pi = 6.283185307179586476925286766559;
+  double u0 = orc_uniform(r[0]), u1 = orc_uniform(r[1]);
+  double u2 = orc_uniform(r[2]), u3 = orc_uniform(r[3]);
+  double rad0 = sqrt(-2.0 * log(u0));
+  double rad1 = sqrt(-2.0 * log(u2));
+  n[0] = rad0 * cos(two_pi * u1);
+  n[1] = rad0 * sin(two_pi * u1);
+  n[2] = rad1 * cos(two_pi * u3);
+  n[3] = rad1 * sin(two_pi * u3);
+}
+
+/* Standard Gumbel by inversion: -ln(-ln u). */
+double orc_gumbel(uint32_t r) {
+  double u = orc_uniform(r);
+  return -log(-log(u));
+}
+
+/* Bernoulli threshold: an event of probability p happens when a 32-bit
+ * draw is below floor(p * 2^32). */
+uint32_t orc_threshold(float p) {
+  double v = (double)p;
+  if (!(v > 0.0)) return 0u;
+  if (v >= 1.0) return 0xFFFFFFFFu;
+  return (uint32_t)floor(v * 4294967296.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Number formats (Sec. 3.3: bfloat16 weights; FP8 e4m3 with a per-row      */
+/* scale is the build's second streamed form).                              */
+/* ------------------------------------------------------------------------ */
+
+/* bfloat16 = the top 16 bits of an IEEE binary32, rounded to nearest with
+ * ties to even on the 16 dropped bits.  NaNs stay quiet NaNs. */
+uint16_t orc_bf16_rne(float f) {
+  uint32_t u, upper, lower;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7FFFFFFFu) > 0x7F800000u) return (uint16_t)((u >> 16) | 0x0040u);
+  upper = u >> 16;
+  lower = u & 0xFFFFu;
+  if (lower > 0x8000u || (lower == 0x8000u && (upper & 1u))) upper += 1u;
+  return (uint16_t)upper;
+}
+
+double orc_bf16_value(uint16_t b) {
+  uint32_t u = (uint32_t)b << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+/* Round half to even of a non-negative double. */
+static double round_half_even(double v) {
+  double fl = floor(v);
+  double diff = v - fl;
+  if (diff > 0.5) return fl + 1.0;
+  if (diff < 0.5) return fl;
+  return (fmod(fl, 2.0) == 0.0) ? fl : fl + 1.0;
+}
+
+/* OCP 8-bit floating point, E4M3 variant: 1 sign bit, 4 exponent bits with
+ * bias 7, 3 mantissa bits; no infinities; S.1111.111 is NaN, so the largest
+ * finite magnitude is 1.75 * 2^8 = 448.  Encoding rounds to nearest-even and
+ * saturates finite values beyond 448 to +-448 ("satfinite"). */
+uint8_t orc_e4m3_encode(float f) {
+  uint8_t sign = signbit(f) ? 0x80u : 0x00u;
+  double a;
+  int e;
+  double mant, q;
+  if (isnan(f)) return (uint8_t)(sign | 0x7Fu);
+  a = fabs((double)f);
+  if (a >= 448.0) return (uint8_t)(sign | 0x7Eu);
+  if (a < ldexp(1.0, -6)) {
+    /* subnormals: multiples of 2^-9; 8 * 2^-9 = 2^-6 is the least normal,
+     * whose code (exponent field 1, mantissa 0) is also 8 */
+    q = round_half_even(a * 512.0);
+    return (uint8_t)(sign | (uint8_t)q);
+  }
+  frexp(a, &e);  /* a = m * 2^e with m in [0.5, 1) */
+  e -= 1;        /* now a in [2^e, 2^(e+1)) */
+  mant = a / ldexp(1.0, e) - 1.0; /* in [0, 1), exact */
+  q = round_half_even(mant * 8.0);
+  if (q >= 8.0) {
+    q = 0.0;
+    e += 1;
+  }
+  return (uint8_t)(sign | (uint8_t)((e + 7) << 3) | (uint8_t)q);
+}
+
+double orc_e4m3_value(uint8_t b) {
+  int s = (b >> 7) & 1, ef = (b >> 3) & 15, m = b & 7;
+  double v;
+  if (ef == 15 && m == 7) return NAN;
+  if (ef == 0)
+    v = (double)m * ldexp(1.0, -9);
+  else
+    v = (1.0 + (double)m / 8.0) * ldexp(1.0, ef - 7);
+  return s ? -v : v;
+}
+
+/* Per-output-row scale of the FP8 form: the row's largest magnitude maps to
+ * the largest finite e4m3 value (IEEE binary32 division); an all-zero row
+ * uses scale 1. */
+float orc_fp8_row_scale(const float *row, int n) {
+  float mx = 0.0f, s;
+  int j;
+  for (j = 0; j < n; j++) {
+    float a = fabsf(row[j]);
+    if (a > mx) mx = a;
+  }
+  s = mx / 448.0f;
+  if (s == 0.0f) s = 1.0f;
+  return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry.  Column x grows to the east, row y to the south; the grid      */
+/* wraps around in both directions.                                         */
+/* ------------------------------------------------------------------------ */
+
+static const int DIR_DX[4] = {0, 1, 0, -1}; /* N E S W */
+static const int DIR_DY[4] = {-1, 0, 1, 0};
+
+static int wrap(int v, int L) {
+  int m = v % L;
+  return m < 0 ? m + L : m;
+}
+
+static int cell_of(int x, int y, int L) { return y * L + x; }
+
+/* The cell one step from (x, y) in direction dir. */
+static int neighbour(int x, int y, int dir, int L) {
+  return cell_of(wrap(x + DIR_DX[dir], L), wrap(y + DIR_DY[dir], L), L);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reset (Sec. 3.2 / 3.3): walls, food, founders on distinct free cells,     */
+/* random facings, Kaiming-style N(0, 1/fan_in) weights and zero biases.     */
+/* ------------------------------------------------------------------------ */
+
+static int cmp_u64(const void *a, const void *b) {
+  uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+  return (x > y) - (x < y);
+}
+
+static int cmp_i32(const void *a, const void *b) {
+  int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  return (x > y) - (x < y);
+}
+
+/* Initial parameters of one founder: weight p ~ N(0,1) / sqrt(fan_in) drawn
+ * from stream W_INIT at counter (slot, p/4), biases zero. */
+void orc_init_params(const orc_config *c, int32_t slot, float *row) {
+  int D = orc_obs_dim(c), H = c->hidden, A = c->n_actions;
+  int P = orc_n_params(c);
+  int oW1, ob1, oW2, ob2, oW3, ob3, p;
+  uint32_t r[4];
+  double n[4];
+  param_offsets(c, &oW1, &ob1, &oW2, &ob2, &oW3, &ob3);
+  (void)A;
+  for (p = 0; p < P; p++) {
+    double fan_in;
+    if ((p & 3) == 0) {
+      draw4(c, ST_W_INIT, (uint32_t)slot, (uint32_t)(p >> 2), 0u, r);
+      orc_normals4(r, n);
+    }
+    if (p >= ob1 && p < oW2) { row[p] = 0.0f; continue; }
+    if (p >= ob2 && p < oW3) { row[p] = 0.0f; continue; }
+    if (p >= ob3) { row[p] = 0.0f; continue; }
+    if (p < ob1) fan_in = (double)D;
+    else fan_in = (double)H; /* W2 and W3 both read H inputs */
+    row[p] = (float)(n[p & 3] / sqrt(fan_in));
+  }
+}
+
+int orc_reset(const orc_config *c, orc_state *s) {
+  int L = c->side, N = L * L, S = c->slots, K = c->init_alive;
+  int P = orc_n_params(c);
+  uint32_t thr_wall = orc_threshold(c->wall_density);
+  uint32_t thr_food = orc_threshold(c->food_density);
+  uint64_t *keys;
+  int32_t *chosen;
+  int cell, nfree = 0, i, slot;
+  uint32_t r[4];
+
+  if (K > S || K < 0) return -1;
+  for (cell = 0; cell < N; cell++) {
+    draw4(c, ST_WALL, (uint32_t)(cell >> 2), 0u, 0u, r);
+    s->wall[cell] = (uint8_t)(r[cell & 3] < thr_wall);
+    draw4(c, ST_FOOD_INIT, (uint32_t)(cell >> 2), 0u, 0u, r);
+    s->food[cell] = (uint8_t)(!s->wall[cell] && r[cell & 3] < thr_food);
+    s->occ[cell] = -1;
+  }
+
+  /* Founders: the K non-wall cells with the smallest (PLACE draw, cell)
+   * keys, then slots 0..K-1 in ascending cell order. */
+  keys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(N > 0 ? N : 1));
+  chosen = (int32_t *)malloc(sizeof(int32_t) * (size_t)(K > 0 ? K : 1));
+  for (cell = 0; cell < N; cell++) {
+    if (s->wall[cell]) continue;
+    draw4(c, ST_PLACE, (uint32_t)(cell >> 2), 0u, 0u, r);
+    keys[nfree++] = ((uint64_t)r[cell & 3] << 32) | (uint64_t)(uint32_t)cell;
+  }
+  if (nfree < K) {
+    free(keys);
+    free(chosen);
+    return -2;
+  }
+  qsort(keys, (size_t)nfree, sizeof(uint64_t), cmp_u64);
+  for (i = 0; i < K; i++) chosen[i] = (int32_t)(keys[i] & 0xFFFFFFFFu);
+  qsort(chosen, (size_t)K, sizeof(int32_t), cmp_i32);
+
+  for (slot = 0; slot < S; slot++) {
+    s->alive[slot] = 0;
+    s->x[slot] = 0;
+    s->y[slot] = 0;
+    s->facing[slot] = 0;
+    s->energy[slot] = 0;
+    s->parent[slot] = -1;
+    s->birth_step[slot] = -1;
+  }
+  for (i = 0; i < K; i++) {
+    cell = chosen[i];
+    s->alive[i] = 1;
+    s->x[i] = cell % L;
+    s->y[i] = cell / L;
+    draw4(c, ST_FACING_INIT, (uint32_t)(i >> 2), 0u, 0u, r);
+    s->facing[i] = (uint8_t)(r[i & 3] >> 30);
+    s->energy[i] = c->e_init;
+    s->occ[cell] = i;
+  }
+#pragma omp parallel for schedule(dynamic, 16)
+  for (slot = 0; slot < S; slot++) {
+    float *row = s->master + (size_t)slot * (size_t)P;
+    if (slot < K)
+      orc_init_params(c, slot, row);
+    else
+      memset(row, 0, sizeof(float) * (size_t)P);
+  }
+  *s->step = 0;
+  free(keys);
+  free(chosen);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Observation (Sec. 3.2 "Sensors"): a k x k patch around the agent with     */
+/* channels (food, agent, wall), rotated so that the agent's facing is the  */
+/* top row, flattened (row, column, channel), then the scalars             */
+/* [energy / e_repro, one-hot facing (8-scalar form), zeros].               */
+/* ------------------------------------------------------------------------ */
+
+void orc_observe(const orc_config *c, const orc_state *s, int32_t slot, double *x) {
+  int L = c->side, k = c->patch_k, R = k / 2;
+  int f = s->facing[slot];
+  int right = (f + 1) & 3;
+  int r, col, i, base = 3 * k * k;
+  for (r = 0; r < k; r++) {
+    for (col = 0; col < k; col++) {
+      int dx, dy, cell, idx = (r * k + col) * 3;
+      if (c->flags & ORC_ROTATE_OBS) {
+        int fwd = R - r, rt = col - R;
+        dx = fwd * DIR_DX[f] + rt * DIR_DX[right];
+        dy = fwd * DIR_DY[f] + rt * DIR_DY[right];
+      } else {
+        dx = col - R;
+        dy = r - R;
+      }
+      cell = cell_of(wrap(s->x[slot] + dx, L), wrap(s->y[slot] + dy, L), L);
+      x[idx + 0] = s->food[cell] ? 1.0 : 0.0;
+      x[idx + 1] = s->occ[cell] >= 0 ? 1.0 : 0.0;
+      x[idx + 2] = s->wall[cell] ? 1.0 : 0.0;
+    }
+  }
+  for (i = 0; i < c->n_scalars; i++) x[base + i] = 0.0;
+  x[base] = (double)s->energy[slot] / (double)c->e_repro;
+  if (c->n_scalars >= 8) x[base + 1 + f] = 1.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Policy (Sec. 3.3): h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2),           */
+/* logits = W3 h2 + b3; action sampled from softmax(logits) by Gumbel-max.   */
+/* ------------------------------------------------------------------------ */
+
+/* The parameters the policy actually multiplies with, in FP64:
+ *   FP32 form (or use_master): the master values;
+ *   BF16 form: every weight rounded to bfloat16, biases FP32;
+ *   FP8 form:  every weight row r of each layer quantised as
+ *              s_r * e4m3(w / s_r), biases FP32. */
+void orc_effective_params(const orc_config *c, const float *m, int use_master, double *w) {
+  int D = orc_obs_dim(c), H = c->hidden, A = c->n_actions, P = orc_n_params(c);
+  int oW1, ob1, oW2, ob2, oW3, ob3, p, row;
+  param_offsets(c, &oW1, &ob1, &oW2, &ob2, &oW3, &ob3);
+  for (p = 0; p < P; p++) w[p] = (double)m[p];
+  if (use_master || c->precision == ORC_FP32) return;
+  if (c->precision == ORC_BF16) {
+    for (p = 0; p < P; p++) {
+      int is_bias = (p >= ob1 && p < oW2) || (p >= ob2 && p < oW3) || p >= ob3;
+      if (!is_bias) w[p] = orc_bf16_value(orc_bf16_rne(m[p]));
+    }
+    return;
+  }
+  /* FP8: rows of W1 have D entries, rows of W2 and W3 have H entries */
+  for (row = 0; row < H + H + A; row++) {
+    int start, n, j;
+    float sc;
+    if (row < H) { start = oW1 + row * D; n = D; }
+    else if (row < 2 * H) { start = oW2 + (row - H) * H; n = H; }
+    else { start = oW3 + (row - 2 * H) * H; n = H; }
+    sc = orc_fp8_row_scale(m + start, n);
+    for (j = 0; j < n; j++) {
+      float q = m[start + j] / sc; /* IEEE binary32 division */
+      w[start + j] = (double)sc * orc_e4m3_value(orc_e4m3_encode(q));
+    }
+  }
+}
+
+/* Forward pass of one agent's MLP on observation x (FP64). */
+void orc_mlp(const orc_config *c, const double *w, const double *x, double *logits) {
+  int D = orc_obs_dim(c), H = c->hidden, A = c->n_actions;
+  int oW1, ob1, oW2, ob2, oW3, ob3, o, j;
+  double h1[512], h2[512];
+  param_offsets(c, &oW1, &ob1, &oW2, &ob2, &oW3, &ob3);
+  for (o = 0; o < H; o++) {
+    double acc = w[ob1 + o];
+    for (j = 0; j < D; j++) acc += w[oW1 + o * D + j] * x[j];
+    h1[o] = tanh(acc);
+  }
+  for (o = 0; o < H; o++) {
+    double acc = w[ob2 + o];
+    for (j = 0; j < H; j++) acc += w[oW2 + o * H + j] * h1[j];
+    h2[o] = tanh(acc);
+  }
+  for (o = 0; o < A; o++) {
+    double acc = w[ob3 + o];
+    for (j = 0; j < H; j++) acc += w[oW3 + o * H + j] * h2[j];
+    logits[o] = acc;
+  }
+}
+
+/* Policy phase for every alive agent.  For each agent: the logits, the
+ * sampled scores (logit + Gumbel, or the logit alone in GREEDY mode), the
+ * chosen action (the first maximum) and a bit mask of every action whose
+ * score lies within tol of the maximum: when more than one bit is set, the
+ * choice is not determined at that resolution and any flagged action is a
+ * valid outcome.  Dead slots get zeros and action 0. */
+int orc_policy(const orc_config *c, const orc_state *s, int use_master, double tol,
+               double *logits, double *scores, uint8_t *action, uint32_t *valid) {
+  int S = c->slots, A = c->n_actions, D = orc_obs_dim(c), P = orc_n_params(c);
+  int64_t t = *s->step;
+  int bad = 0;
+  if (A > 16 || c->hidden > 512 || c->e_repro <= 0) return -1;
+#pragma omp parallel
+  {
+    double *w = (double *)malloc(sizeof(double) * (size_t)P);
+    double *x = (double *)malloc(sizeof(double) * (size_t)D);
+    int slot;
+#pragma omp for schedule(dynamic, 32)
+    for (slot = 0; slot < S; slot++) {
+      double *lg = logits + (size_t)slot * A;
+      double *sc = scores + (size_t)slot * A;
+      int a, best = 0;
+      uint32_t mask = 0;
+      if (!w || !x) {
+        bad = 1;
+        continue;
+      }
+      if (!s->alive[slot]) {
+        for (a = 0; a < A; a++) { lg[a] = 0.0; sc[a] = 0.0; }
+        action[slot] = 0;
+        valid[slot] = 0;
+        continue;
+      }
+      orc_observe(c, s, slot, x);
+      orc_effective_params(c, s->master + (size_t)slot * (size_t)P, use_master, w);
+      orc_mlp(c, w, x, lg);
+      for (a = 0; a < A; a++) {
+        double g = 0.0;
+        if (!(c->flags & ORC_GREEDY)) {
+          uint32_t r[4];
+          draw4(c, ST_SAMPLE, (uint32_t)t, (uint32_t)slot, (uint32_t)(a >> 2), r);
+          g = orc_gumbel(r[a & 3]);
+        }
+        sc[a] = lg[a] + g;
+      }
+      for (a = 1; a < A; a++)
+        if (sc[a] > sc[best]) best = a;
+      for (a = 0; a < A; a++)
+        if (sc[best] - sc[a] <= tol) mask |= 1u << a;
+      action[slot] = (uint8_t)best;
+      valid[slot] = mask;
+    }
+    free(w);
+    free(x);
+  }
+  return bad ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mutation (Sec. 3.3): the child's parameters are the parent's plus          */
+/* sigma * N(0,1) on every parameter; the normal for parameter p comes from  */
+/* stream MUTATE at counter (step, parent slot, p/4).                        */
+/* ------------------------------------------------------------------------ */
+
+void orc_mutate(const orc_config *c, int64_t step, int32_t parent_slot,
+                const float *parent_row, float *child_row) {
+  int P = orc_n_params(c), p;
+  uint32_t r[4];
+  double n[4];
+  for (p = 0; p < P; p++) {
+    if ((p & 3) == 0) {
+      draw4(c, ST_MUTATE, (uint32_t)step, (uint32_t)parent_slot, (uint32_t)(p >> 2), r);
+      orc_normals4(r, n);
+    }
+    child_row[p] = (float)((double)parent_row[p] + (double)c->sigma * n[p & 3]);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Transition (Sec. 3.2 "Actions", "Resources and Agent Health").  Phase    */
+/* order: face/turn, move, eat, attack, metabolism + death, reproduction +  */
+/* mutation, regrowth.                                                       */
+/* ------------------------------------------------------------------------ */
+
+static uint64_t claim_key(const orc_config *c, uint32_t stream, int64_t t, int32_t slot) {
+  uint32_t r[4];
+  draw4(c, stream, (uint32_t)t, (uint32_t)slot, 0u, r);
+  /* the highest draw wins; equal draws go to the lower slot */
+  return ((uint64_t)r[0] << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)slot);
+}
+
+static int32_t claim_slot(uint64_t key) {
+  return (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFu));
+}
+
+int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
+                   orc_stats *st, int32_t *birth_parent, int32_t *birth_child) {
+  int L = c->side, N = L * L, S = c->slots, A = c->n_actions;
+  int P = orc_n_params(c);
+  int64_t t = *s->step;
+  uint32_t thr_regrow = orc_threshold(c->regrow_p);
+  uint64_t *best_cell = (uint64_t *)calloc((size_t)N, sizeof(uint64_t));
+  int32_t *count_cell = (int32_t *)calloc((size_t)N, sizeof(int32_t));
+  uint64_t *best_victim = (uint64_t *)calloc((size_t)S, sizeof(uint64_t));
+  int32_t *target = (int32_t *)malloc(sizeof(int32_t) * (size_t)S);
+  int32_t *esnap = (int32_t *)malloc(sizeof(int32_t) * (size_t)S);
+  int32_t *winners = (int32_t *)malloc(sizeof(int32_t) * (size_t)S);
+  int32_t *free_slots = (int32_t *)malloc(sizeof(int32_t) * (size_t)S);
+  int slot, cell, nwin = 0, nfree = 0, i;
+  static const int MOVE_DIR[5] = {-1, 0, 2, 1, 3}; /* action -> N S E W dir */
+
+  memset(st, 0, sizeof(*st));
+  if (!best_cell || !count_cell || !best_victim || !target || !esnap || !winners || !free_slots) {
+    free(best_cell); free(count_cell); free(best_victim); free(target);
+    free(esnap); free(winners); free(free_slots);
+    return -1;
+  }
+  for (slot = 0; slot < S; slot++) {
+    if (!s->alive[slot]) continue;
+    if (action[slot] >= A) {
+      free(best_cell); free(count_cell); free(best_victim); free(target);
+      free(esnap); free(winners); free(free_slots);
+      return -2;
+    }
+    st->agent_steps++;
+    st->act[action[slot]]++;
+  }
+
+  /* 1. Facing: a move action faces its direction whether or not the move
+   *    succeeds; turn-left / turn-right rotate by a quarter. */
+  for (slot = 0; slot < S; slot++) {
+    int a = action[slot];
+    if (!s->alive[slot]) continue;
+    if (a >= A_NORTH && a <= A_WEST) s->facing[slot] = (uint8_t)MOVE_DIR[a];
+    else if (A > A_TURN_LEFT && a == A_TURN_LEFT) s->facing[slot] = (uint8_t)((s->facing[slot] + 3) & 3);
+    else if (A > A_TURN_RIGHT && a == A_TURN_RIGHT) s->facing[slot] = (uint8_t)((s->facing[slot] + 1) & 3);
+  }
+
+  /* 2. Moves.  A move into a wall or into a cell occupied when the step
+   *    began is cancelled.  Several agents moving into one free cell: the
+   *    highest CLAIM_MOVE draw wins (ties to the lower slot), or, with the
+   *    paper's cancel-all rule, every contested move is cancelled. */
+  for (slot = 0; slot < S; slot++) {
+    int a = action[slot], tc;
+    uint64_t key;
+    target[slot] = -1;
+    if (!s->alive[slot] || a < A_NORTH || a > A_WEST) continue;
+    tc = neighbour(s->x[slot], s->y[slot], s->facing[slot], L);
+    if (s->wall[tc] || s->occ[tc] != -1) {
+      st->move_blocked++;
+      continue;
+    }
+    target[slot] = tc;
+    key = claim_key(c, ST_CLAIM_MOVE, t, slot);
+    if (key > best_cell[tc]) best_cell[tc] = key;
+    count_cell[tc]++;
+  }
+  for (slot = 0; slot < S; slot++) {
+    int tc = target[slot];
+    int won;
+    if (tc < 0) continue;
+    won = claim_slot(best_cell[tc]) == slot;
+    if ((c->flags & ORC_CANCEL_ALL) && count_cell[tc] > 1) won = 0;
+    if (!won) {
+      st->move_lost++;
+      continue;
+    }
+    s->occ[cell_of(s->x[slot], s->y[slot], L)] = -1;
+    s->occ[tc] = slot;
+    s->x[slot] = tc % L;
+    s->y[slot] = tc / L;
+    st->moves++;
+  }
+
+  /* 3. Eat: the food on the agent's cell (automatic in the small rule set,
+   *    the eat action otherwise) becomes e_food energy. */
+  for (slot = 0; slot < S; slot++) {
+    int here;
+    if (!s->alive[slot]) continue;
+    if (!((c->flags & ORC_AUTO_EAT) || (A > A_EAT && action[slot] == A_EAT))) continue;
+    here = cell_of(s->x[slot], s->y[slot], L);
+    if (s->food[here]) {
+      s->food[here] = 0;
+      s->energy[slot] += c->e_food;
+      st->eaten++;
+    }
+  }
+
+  /* 4. Attack on the faced cell.  A victim yields to one attacker (highest
+   *    CLAIM_ATTACK draw, ties to the lower slot), which takes
+   *    floor(e * num / den) of the victim's post-eat energy.  Every amount
+   *    is computed from the post-eat snapshot, so the outcome does not
+   *    depend on any order. */
+  for (slot = 0; slot < S; slot++) esnap[slot] = s->energy[slot];
+  for (slot = 0; slot < S; slot++) {
+    int tc, v;
+    uint64_t key;
+    if (!s->alive[slot] || action[slot] != A_ATTACK) continue;
+    st->attacks++;
+    tc = neighbour(s->x[slot], s->y[slot], s->facing[slot], L);
+    v = s->occ[tc];
+    if (v < 0) continue;
+    key = claim_key(c, ST_CLAIM_ATTACK, t, slot);
+    if (key > best_victim[v]) best_victim[v] = key;
+  }
+  for (slot = 0; slot < S; slot++) {
+    int32_t w, amount;
+    if (best_victim[slot] == 0) continue;
+    w = claim_slot(best_victim[slot]);
+    amount = (int32_t)(((int64_t)esnap[slot] * c->attack_num) / c->attack_den);
+    s->energy[slot] -= amount;
+    s->energy[w] += amount;
+    st->attack_hits++;
+    st->energy_transferred += amount;
+  }
+
+  /* 5. Metabolism and death: every agent pays e_metab; an agent whose
+   *    energy is then <= 0 dies and frees its cell and slot. */
+  for (slot = 0; slot < S; slot++) {
+    if (!s->alive[slot]) continue;
+    s->energy[slot] -= c->e_metab;
+    if (s->energy[slot] <= 0) {
+      st->deaths++;
+      st->dead_energy += s->energy[slot];
+      s->alive[slot] = 0;
+      s->occ[cell_of(s->x[slot], s->y[slot], L)] = -1;
+      s->energy[slot] = 0;
+    }
+  }
+
+  /* 6. Reproduction: an agent with energy >= e_repro places one child on
+   *    the cell behind it, if that cell is not a wall and is free after the
+   *    deaths.  One winner per cell (highest CLAIM_BIRTH draw, ties to the
+   *    lower slot).  Winners, in ascending slot order, take the free slots
+   *    in ascending order; winners left without a slot keep their energy.
+   *    The child gets floor(e/2), the parent keeps the rest; the child
+   *    faces as the parent did and carries the parent's parameters mutated
+   *    by sigma * N(0,1). */
+  for (i = 0; i < N; i++) best_cell[i] = 0;
+  for (slot = 0; slot < S; slot++) {
+    int tc;
+    uint64_t key;
+    target[slot] = -1;
+    if (!s->alive[slot] || s->energy[slot] < c->e_repro) continue;
+    tc = neighbour(s->x[slot], s->y[slot], (s->facing[slot] + 2) & 3, L);
+    if (s->wall[tc] || s->occ[tc] != -1) continue;
+    target[slot] = tc;
+    key = claim_key(c, ST_CLAIM_BIRTH, t, slot);
+    if (key > best_cell[tc]) best_cell[tc] = key;
+  }
+  for (slot = 0; slot < S; slot++) {
+    if (target[slot] >= 0 && claim_slot(best_cell[target[slot]]) == slot) winners[nwin++] = slot;
+    if (!s->alive[slot]) free_slots[nfree++] = slot;
+  }
+  for (i = 0; i < nwin; i++) {
+    int32_t p = winners[i], ch, e, ce, tc;
+    if (i >= nfree) {
+      st->failed_births++;
+      continue;
+    }
+    ch = free_slots[i];
+    tc = target[p];
+    e = s->energy[p];
+    ce = e / 2;
+    s->energy[p] = e - ce;
+    s->energy[ch] = ce;
+    s->alive[ch] = 1;
+    s->x[ch] = tc % L;
+    s->y[ch] = tc / L;
+    s->facing[ch] = s->facing[p];
+    s->parent[ch] = p;
+    s->birth_step[ch] = (int32_t)t;
+    s->occ[tc] = ch;
+    orc_mutate(c, t, p, s->master + (size_t)p * (size_t)P, s->master + (size_t)ch * (size_t)P);
+    if (birth_parent) birth_parent[st->births] = p;
+    if (birth_child) birth_child[st->births] = ch;
+    st->births++;
+  }
+
+  /* 7. Regrowth: every non-wall cell without food regrows one unit with
+   *    probability regrow_p (stream REGROW at counter (step, cell/4)). */
+  for (cell = 0; cell < N; cell++) {
+    uint32_t r[4];
+    if (s->wall[cell] || s->food[cell]) continue;
+    draw4(c, ST_REGROW, (uint32_t)t, (uint32_t)(cell >> 2), 0u, r);
+    if (r[cell & 3] < thr_regrow) {
+      s->food[cell] = 1;
+      st->regrown++;
+    }
+  }
+
+  for (slot = 0; slot < S; slot++) {
+    if (!s->alive[slot]) continue;
+    st->alive++;
+    st->energy_total += s->energy[slot];
+  }
+  for (cell = 0; cell < N; cell++) st->food_total += s->food[cell];
+  *s->step = t + 1;
+
+  free(best_cell); free(count_cell); free(best_victim); free(target);
+  free(esnap); free(winners); free(free_slots);
+  return 0;
+}

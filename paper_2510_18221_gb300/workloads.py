@@ -1,0 +1,87 @@
+"""Seeded synthetic workload definitions (inputs only, no simulation arithmetic).
+
+Each workload is a plain dictionary describing one environment: grid side,
+agent slots, founders, observation patch, MLP shape, streamed precision,
+rule flags and the constants of the rule set.  Both the CUDA library (through
+the binding) and the CPU oracle (in the tests) consume these dictionaries;
+neither derives anything from the other.
+
+The five workloads mirror the paper's scales (Sec. 3.2: grids from 64^2 to
+1024^2 with the initial population scaled with the area; App. E: runs of up
+to ~131k agent slots at 1024^2) with the concrete rule set the build fixes:
+binary food, int32 energy, a tanh MLP and fixed constants.
+"""
+from __future__ import annotations
+
+import copy
+
+import numpy as np
+
+_COMMON = dict(
+    e_init=100, e_metab=1, e_food=20, e_repro=200, attack_num=1, attack_den=2,
+)
+
+# 64x64 toroidal grid, 256 slots, 200 founders, 5x5x3 patch + 4 scalars = 79
+# inputs, MLP 79 -> 32 -> 32 -> 6, FP32, automatic eating.
+SMALL = dict(
+    name="small-64x64-256slots-79-32-32-6-fp32",
+    side=64, slots=256, init_alive=200, patch_k=5, n_scalars=4, hidden=32,
+    n_actions=6, precision="fp32", flags=("auto_eat", "rotate_obs"), seed=0,
+    sigma=0.02, food_density=0.1, regrow_p=0.01, wall_density=0.0, steps=100,
+    **_COMMON)
+
+# 512x512, 16,384 slots, 12,000 founders, 11x11x3 patch + 8 scalars = 371
+# inputs, MLP 371 -> 64 -> 64 -> 9, FP32, 2% walls.
+MID = dict(
+    name="mid-512x512-16384slots-371-64-64-9-fp32",
+    side=512, slots=16384, init_alive=12000, patch_k=11, n_scalars=8, hidden=64,
+    n_actions=9, precision="fp32", flags=("rotate_obs",), seed=0, sigma=0.01,
+    food_density=0.05, regrow_p=0.005, wall_density=0.02, steps=1000, **_COMMON)
+
+# 1024x1024, 65,536 slots, 50,000 founders, same MLP, weights streamed as BF16.
+PAPER = dict(MID, name="paper-1024x1024-65536slots-371-64-64-9-bf16",
+             side=1024, slots=65536, init_alive=50000, precision="bf16")
+
+# 2048x2048, 262,144 slots, 200,000 founders, 15x15x3 + 8 = 683 inputs,
+# MLP 683 -> 128 -> 128 -> 9, FP8 e4m3 with a per-row scale.
+LARGE = dict(MID, name="large-2048x2048-262144slots-683-128-128-9-fp8",
+             side=2048, slots=262144, init_alive=200000, patch_k=15, hidden=128,
+             precision="fp8", steps=500)
+
+WORKLOADS = {"small": SMALL, "mid": MID, "paper": PAPER, "large": LARGE}
+
+
+def get(name: str, **overrides) -> dict:
+    """A copy of a named workload with fields overridden."""
+    w = copy.deepcopy(WORKLOADS[name])
+    w.update(overrides)
+    return w
+
+
+def scaled(name: str, side: int, slots: int, init_alive: int, **overrides) -> dict:
+    """A named workload's rules and MLP on a different grid / population."""
+    return get(name, side=side, slots=slots, init_alive=init_alive,
+               name="%s-%dx%d-%dslots" % (name, side, side, slots), **overrides)
+
+
+def batched(n_envs: int = 64, seed: int = 0, base_seed: int = 0,
+            precision: str = "bf16") -> list:
+    """Independent environments of uneven size (the many-small-worlds shape of
+    the paper's self-averaging study, App. F.3): sides uniform over
+    {128, 256, 512, 1024}; founders lognormal with median 4,096 and log-sd 1,
+    clipped to [512, 32768] and to a quarter of the cells; slots = founders
+    * 1.3 rounded up to a multiple of 256.  Environment e uses seed
+    base_seed + e.  Sizes come from numpy's seeded generator (an input
+    generator, not a draw of the method)."""
+    rng = np.random.default_rng(seed)
+    envs = []
+    for e in range(n_envs):
+        side = int(rng.choice([128, 256, 512, 1024]))
+        n = int(round(float(np.exp(rng.normal(np.log(4096.0), 1.0)))))
+        n = max(512, min(32768, n))
+        n = min(n, side * side // 4)
+        slots = ((int(np.ceil(n * 1.3)) + 255) // 256) * 256
+        envs.append(get("mid", side=side, slots=slots, init_alive=n, seed=base_seed + e,
+                        precision=precision,
+                        name="batched-env%d-%dx%d-%dslots" % (e, side, side, slots)))
+    return envs
