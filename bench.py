@@ -1,0 +1,317 @@
+#!/usr/bin/env python3
+"""Throughput of the full environment step (policy + environment) on GB300.
+
+Metric: agent-steps per second -- the number of agents alive at the start
+of each step, summed over the timed steps, divided by the device time of
+those steps -- plus the HBM bandwidth the policy kernel achieves against
+the measured copy bandwidth of this GPU.
+
+Default workload: one 1024x1024 world, 65,536 agent slots, 50,000 founders,
+per-agent MLP 371 -> 64 -> 64 -> 9 with weights streamed as BF16 (FP32
+accumulation), rules of the mid-scale workload.  The weight stream of one
+step (~2.9 GB) is far larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl eco|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank advances its own
+independent world (seed + rank) on its own GPU: weak scaling, no collective
+on the data path; the timing is the maximum over ranks.  --impl reference
+times the CPU oracle on a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "agent-steps/sec at 65,536 agents (policy+env) and policy-kernel HBM GB/s vs peak"
+UNIT = "agent-steps/s"
+KERNELS_PER_STEP = 12  # compact, policy, 9 environment phases, finish
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="eco", choices=["eco", "reference"])
+    ap.add_argument("--workload", default="paper")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="CPU time budget of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def committed_traffic(workload_name):
+    """Per-launch DRAM bytes of the policy kernel from a committed ncu
+    summary, if one exists for this workload and the current kernel."""
+    path = os.path.join(ROOT, "profiles", "policy_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    rec = d.get(workload_name)
+    if not rec:
+        return None
+    return rec
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.lines = []
+        self.proc = None
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if device_id:
+            cmd += ["-i", device_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_sample(w, seconds, steps_cap=None):
+    """Time the CPU oracle on a bounded sample of the workload: the same MLP,
+    rules and precision on a 256x256 world with the same founder density
+    (4,096 slots, 3,125 founders)."""
+    import oracle
+    from paper_2510_18221_gb300 import workloads
+    side = 256
+    scale = (side * side) / float(w["side"] * w["side"])
+    founders = max(1, int(round(w["init_alive"] * scale)))
+    slots = max(founders, int(round(w["slots"] * scale)))
+    sw = dict(w, side=side, slots=slots, init_alive=founders,
+              name="%s sample %dx%d %d slots" % (w["name"], side, side, slots))
+    o = oracle.Oracle(sw)
+    o.reset()
+    agent_steps, n, t0 = 0, 0, time.perf_counter()
+    while True:
+        _, st, _ = o.step_once()
+        agent_steps += st["agent_steps"]
+        n += 1
+        el = time.perf_counter() - t0
+        if (steps_cap is None and el >= seconds and n >= 2) or (steps_cap is not None and n >= steps_cap):
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": agent_steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d steps of a %dx%d world, %d slots, %d founders, MLP %d-%d-%d-%d %s "
+                      "(same rules and founder density), %.1f s" %
+                      (n, side, side, slots, founders, o.D, w["hidden"], w["hidden"],
+                       w["n_actions"], w["precision"], el)}, agent_steps, el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2510_18221_gb300 import workloads
+    w = workloads.get(args.workload)
+    # warm-up steps then K timed steps of the oracle on the bounded sample
+    cpu_baseline_sample(w, 0, steps_cap=max(1, args.warmup))
+    rec, agent_steps, el = cpu_baseline_sample(w, 0, steps_cap=max(1, args.steps))
+    value = agent_steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "sample": rec["sample"]},
+            "cpu_baseline": dict(rec, value=value),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2510_18221_gb300 import eco, workloads
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = workloads.get(args.workload, seed=workloads.get(args.workload)["seed"] + rank)
+    env = eco.Env(w)
+
+    # ---- device-timed region -------------------------------------------------
+    env.reset()
+    env.step(args.warmup)            # builds the graph, autotunes the policy kernel
+    torch.cuda.synchronize()
+    s0 = env.stats()[0]
+    props = torch.cuda.get_device_properties(local)
+    dev_id = None
+    uuid = getattr(props, "uuid", None)
+    if uuid is not None:
+        dev_id = "GPU-" + str(uuid)
+    clocks = ClockSampler(dev_id) if rank == 0 else None
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(env.stream)
+    env.step_timed(args.steps)
+    t_end.record(env.stream)
+    t_end.synchronize()
+    barrier()
+    clk = clocks.stop() if clocks else None
+    ms = t_start.elapsed_time(t_end)
+    s1 = env.stats()[0]
+    policy_ms, n_timed = env.policy_timing()
+    agent_steps = s1["agent_steps"] - s0["agent_steps"]
+    births = s1["births"] - s0["births"]
+    per_agent_bytes, n_alive_now = env.policy_bytes()
+    per_agent_bytes = per_agent_bytes // max(1, n_alive_now)
+    policy_bytes = agent_steps * per_agent_bytes
+
+    # ---- end-to-end through the C-ABI: step + host read of the step's stats --
+    env.reset()
+    env.step(args.warmup)
+    torch.cuda.synchronize()
+    e0 = env.stats()[0]
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        eco.eco_step(env.h, 1)
+        tot, last = eco.eco_read_stats(env.h, env.n_envs)   # device -> host, synchronises
+    e_el = time.perf_counter() - t0
+    barrier()
+    e_agent_steps = int(tot[0][1]) - e0["agent_steps"]
+    d2h = tot.nbytes + last.nbytes
+
+    totals = torch.tensor([float(ms), float(agent_steps), float(e_el), float(e_agent_steps)],
+                          dtype=torch.float64, device="cuda")
+    if dist is not None:
+        mx = totals.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = totals.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms, e_el = float(mx[0]), float(mx[2])
+        agent_steps, e_agent_steps = int(sm[1]), int(sm[3])
+
+    peaks, peak_kind = measured_peaks()
+    achieved = policy_bytes / (policy_ms * 1e-3) / 1e9 if policy_ms > 0 else 0.0
+    traffic = committed_traffic(w["name"])
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, _, _ = cpu_baseline_sample(w, args.cpu_seconds)
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": agent_steps / (ms * 1e-3),
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 (%s weights, int32 state)" % w["precision"],
+            "data": "synthetic",
+            "config": {
+                "workload": w["name"], "grid": "%dx%d" % (w["side"], w["side"]),
+                "slots": w["slots"], "founders": w["init_alive"],
+                "mlp": "%d-%d-%d-%d" % (env.D, w["hidden"], w["hidden"], w["n_actions"]),
+                "weights": w["precision"], "parallelism": "independent worlds, one per GPU",
+                "l2": "inputs larger than L2 (%.2f GB of weights streamed per step)" %
+                      (policy_bytes / max(1, args.steps) / 1e9),
+                "window": "steps %d..%d after reset" % (args.warmup, args.warmup + args.steps),
+                "mean_alive": agent_steps / max(1, args.steps) / world,
+                "births": births,
+                "policy_variant": eco.eco_policy_variant_name(env.variants()[1]),
+            },
+            "roofline": {
+                "bound": "hbm", "kernel": "k_policy", "achieved": achieved,
+                "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                "frac": achieved / float(peaks["hbm_gbs"]),
+                "peak_kind": "%s copy bandwidth" % peak_kind,
+                "bytes_per_agent": per_agent_bytes,
+                "policy_ms_per_step": policy_ms / max(1, n_timed),
+                "policy_share_of_step": policy_ms / ms if ms > 0 else None,
+                "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                "traffic_source": traffic["source"] if traffic else None,
+            },
+            "e2e": {"value": e_agent_steps / e_el, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    env.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * eco.h -- C-ABI of the GB300 (sm_103a) ecological-simulator step library.
+ *
+ * The library runs the environment step of arXiv 2510.18221 ("The Emergence
+ * of Complex Behavior in Large-Scale Ecological Environments") on one GPU,
+ * for one or many independent environments at once.  App. E of the paper
+ * describes the same split: a population-level interface where the map
+ * state, agent states and heritable traits go in, and the actions, births,
+ * deaths and environment transitions happen inside.
+ * Every phase of the step runs in the library's own CUDA kernels:
+ *   observe (Sec. 3.2 "Sensors") -> per-agent MLP (Sec. 3.3) -> sample
+ *   (Sec. 3.3) -> turn/move with claim conflicts (Sec. 3.2 "Actions") -> eat
+ *   -> attack -> metabolism and death (Sec. 3.2 "Resources and Agent
+ *   Health") -> reproduction with Gaussian mutation (Sec. 3.2, 3.3) ->
+ *   regrowth -> statistics (App. E measurement API).
+ *
+ * Conventions
+ *   - Every function that can fail returns an int status: ECO_OK (0) or a
+ *     negative ECO_E* code.  The message of the last failure on a handle is
+ *     returned by eco_last_error().
+ *   - Device memory: the caller allocates ONE workspace of the size
+ *     eco_workspace_bytes() reports, 256-byte aligned, and keeps it alive
+ *     until eco_destroy().  The library carves every device array out of
+ *     it, allocates no other device memory, and never frees caller memory.
+ *   - Streams: all device work is enqueued on the stream given to
+ *     eco_create() (a cudaStream_t passed as void*; NULL = legacy default
+ *     stream).  eco_reset() and eco_step() are asynchronous.  eco_read_*()
+ *     and eco_write_*() synchronise that stream.
+ *   - Host buffers passed to eco_read_* / eco_write_* are caller-owned,
+ *     sized as documented per function, and are not retained.
+ *   - Environments are independent: environment e, run alone or batched
+ *     with others, produces identical results.
+ */
+#ifndef ECO_H
+#define ECO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ECO_ABI_VERSION 1
+
+/* Status codes. */
+#define ECO_OK 0
+#define ECO_EINVAL (-1)   /* bad argument or configuration                  */
+#define ECO_ENOMEM (-2)   /* workspace too small or device memory exhausted */
+#define ECO_ECUDA (-3)    /* a CUDA runtime call failed                     */
+#define ECO_ETIMEOUT (-4) /* a device-side wait ran out of its budget       */
+#define ECO_EABI (-5)     /* abi_version mismatch                           */
+
+/* Precision of the weights the policy kernel streams (Sec. 3.3 uses
+ * bfloat16 weights; FP8 e4m3 with a per-output-row FP32 scale is the
+ * second reduced form).  FP32 master weights always exist and receive the
+ * mutations; the streamed copy is re-derived from them. */
+#define ECO_FP32 0
+#define ECO_BF16 1
+#define ECO_FP8_E4M3 2
+
+/* Rule flags. */
+#define ECO_AUTO_EAT 1   /* eat automatically on the post-move cell        */
+#define ECO_ROTATE_OBS 2 /* rotate the patch so the facing is the top row  */
+#define ECO_CANCEL_ALL 4 /* the paper's rule: every contested move fails   */
+#define ECO_GREEDY 8     /* argmax of the logits instead of sampling       */
+
+/* Action codes: 0 stay, 1 north, 2 south, 3 east, 4 west, 5 attack;
+ * nine-action sets add 6 turn-left, 7 turn-right, 8 eat. */
+
+typedef struct eco_handle eco_handle;
+
+/* Configuration, copied at eco_create().  All environments share the
+ * observation, MLP shape, precision, rules and constants; each has its own
+ * grid side (even, >= 4), slot count, founder count and seed. */
+typedef struct {
+  int32_t abi_version;           /* must be ECO_ABI_VERSION                  */
+  int32_t n_envs;                /* >= 1                                     */
+  const int32_t *env_side;       /* [n_envs] grid side L (torus L x L)       */
+  const int32_t *env_slots;      /* [n_envs] agent slots                     */
+  const int32_t *env_init_alive; /* [n_envs] founders placed by eco_reset    */
+  const uint32_t *env_seed;      /* [n_envs] Philox seed                     */
+  int32_t patch_k;               /* odd patch side k: D = 3k^2 + n_scalars   */
+  int32_t n_scalars;             /* 4 or 8                                   */
+  int32_t hidden;                /* H in {32, 64, 128}                       */
+  int32_t n_actions;             /* A in {6, 9}                              */
+  int32_t precision;             /* ECO_FP32 / ECO_BF16 / ECO_FP8_E4M3       */
+  int32_t flags;                 /* ECO_AUTO_EAT | ECO_ROTATE_OBS | ...      */
+  float sigma;                   /* mutation standard deviation              */
+  float food_density;            /* initial food probability per cell        */
+  float regrow_p;                /* food regrowth probability per step       */
+  float wall_density;            /* wall probability per cell                */
+  int32_t e_init;                /* founders' energy                         */
+  int32_t e_metab;               /* energy paid per step                     */
+  int32_t e_food;                /* energy per food unit eaten               */
+  int32_t e_repro;               /* reproduction threshold; also the energy
+                                    scale of the observation scalar          */
+  int32_t attack_num, attack_den;/* transferred fraction of victim energy    */
+  int32_t policy_variant;        /* 0 = autotune at create; k > 0 = force
+                                    variant k (see eco_policy_variants)      */
+} eco_config;
+
+/* Statistics, one record per environment (App. E measurement API).
+ * Counters marked (sum) accumulate over steps in the "total" record and
+ * hold the last step's value in the "last" record; (now) values describe
+ * the state after the last step in both records. */
+enum {
+  ECO_STAT_STEP = 0,          /* (now) steps completed since reset          */
+  ECO_STAT_AGENT_STEPS,       /* (sum) agents alive when a step began       */
+  ECO_STAT_ACT0,              /* (sum) ECO_STAT_ACT0 + a: action a chosen   */
+  ECO_STAT_MOVES = ECO_STAT_ACT0 + 16, /* (sum) successful moves             */
+  ECO_STAT_MOVE_BLOCKED,      /* (sum) move into wall / occupied cell       */
+  ECO_STAT_MOVE_LOST,         /* (sum) lost a contested cell                */
+  ECO_STAT_EATEN,             /* (sum) food units eaten                     */
+  ECO_STAT_ATTACKS,           /* (sum) attack actions                       */
+  ECO_STAT_ATTACK_HITS,       /* (sum) energy transfers                     */
+  ECO_STAT_ENERGY_TRANSFERRED,/* (sum) energy moved by attacks              */
+  ECO_STAT_DEATHS,            /* (sum)                                      */
+  ECO_STAT_DEAD_ENERGY,       /* (sum) energies (<= 0) of agents that died  */
+  ECO_STAT_BIRTHS,            /* (sum)                                      */
+  ECO_STAT_FAILED_BIRTHS,     /* (sum) birth-cell winners without a slot    */
+  ECO_STAT_REGROWN,           /* (sum) cells that regrew food               */
+  ECO_STAT_ALIVE,             /* (now) alive agents                         */
+  ECO_STAT_FOOD_TOTAL,        /* (now) cells holding food                   */
+  ECO_STAT_ENERGY_TOTAL,      /* (now) summed energy of alive agents        */
+  ECO_N_STATS
+};
+
+typedef struct {
+  int64_t v[ECO_N_STATS];
+} eco_stats;
+
+/* Host view of one environment's world state (all arrays caller-owned).
+ * Cells are indexed c = y * L + x (x = column, grows east; y = row, grows
+ * south).  Any pointer may be NULL to skip that array. */
+typedef struct {
+  uint8_t *food;       /* [L*L] 0/1                                         */
+  uint8_t *wall;       /* [L*L] 0/1                                         */
+  int32_t *occ;        /* [L*L] slot on the cell or -1                      */
+  uint8_t *alive;      /* [slots] 0/1                                       */
+  int32_t *x, *y;      /* [slots]                                           */
+  uint8_t *facing;     /* [slots] 0 N, 1 E, 2 S, 3 W                        */
+  int32_t *energy;     /* [slots]                                           */
+  int32_t *parent;     /* [slots] parent slot, -1 for founders              */
+  int32_t *birth_step; /* [slots] step of birth, -1 for founders            */
+  int64_t *step;       /* [1] steps completed                               */
+} eco_state_view;
+
+/* Parameter count P and observation size D for a configuration.
+ * Parameters in "logical order" are W1[H][D], b1[H], W2[H][H], b2[H],
+ * W3[A][H], b3[A] (Sec. 3.3 MLP: tanh hidden layers, linear head). */
+int eco_param_count(const eco_config *cfg, int32_t *n_params, int32_t *obs_dim);
+
+/* Bytes of device workspace eco_create() needs for cfg.  Returns
+ * ECO_EINVAL for an invalid configuration. */
+int eco_workspace_bytes(const eco_config *cfg, size_t *bytes);
+
+/* Create a handle.  dev_workspace: caller-allocated device memory of at
+ * least the reported size (256-byte aligned); stream: cudaStream_t or
+ * NULL.  Selects the policy-kernel variant (autotuning on the workspace
+ * when cfg->policy_variant == 0).  On failure *out is NULL. */
+int eco_create(const eco_config *cfg, void *dev_workspace, size_t bytes,
+               void *stream, eco_handle **out);
+
+/* Reset every environment (Sec. 3.2, 3.3): walls and food by Bernoulli
+ * draws, founders on the K non-wall cells with the smallest placement keys
+ * (slots 0..K-1 in ascending cell order), random facings, energy e_init,
+ * weights N(0, 1/fan_in), zero biases; statistics cleared.  Asynchronous. */
+int eco_reset(eco_handle *h);
+
+/* Advance every environment by n_steps >= 0 steps.  Asynchronous; replays
+ * a CUDA graph of the step.  Returns ECO_ETIMEOUT if a previous step
+ * recorded a device-side timeout. */
+int eco_step(eco_handle *h, int32_t n_steps);
+
+/* Copy statistics of environments [0, n_envs) to host records (either
+ * pointer may be NULL).  Synchronises the stream. */
+int eco_read_stats(eco_handle *h, eco_stats *total, eco_stats *last, int32_t n_envs);
+
+/* Copy environment env's world state to / from the host.  Writing replaces
+ * the listed arrays (NULL arrays are left unchanged; food, wall and occ
+ * must be written together if any of them is written, as must alive / x /
+ * y), then re-derives the derived device tables.  Both synchronise. */
+int eco_read_state(eco_handle *h, int32_t env, eco_state_view *out);
+int eco_write_state(eco_handle *h, int32_t env, const eco_state_view *in);
+
+/* FP32 master parameters of slots [slot0, slot0 + n) of env, logical
+ * order, host array [n][P].  Writing also re-derives the streamed
+ * BF16/FP8 copy of those slots.  Both synchronise. */
+int eco_read_params(eco_handle *h, int32_t env, int32_t slot0, int32_t n, float *out);
+int eco_write_params(eco_handle *h, int32_t env, int32_t slot0, int32_t n, const float *in);
+
+/* Streamed copy of slots [slot0, slot0 + n), logical order: BF16 codes as
+ * uint16 [n][P] or e4m3 codes as uint8 [n][P] (bias positions hold the
+ * code of 0), plus for FP8 the row scales [n][2H + A] (rows of W1, W2,
+ * W3).  ECO_EINVAL for the FP32 precision.  Synchronises. */
+int eco_read_streamed(eco_handle *h, int32_t env, int32_t slot0, int32_t n,
+                      void *codes, float *row_scales);
+
+/* Logits [slots][A] (FP32) and actions [slots] of the last step's policy
+ * phase for env (dead slots hold stale values).  Synchronises. */
+int eco_read_policy_io(eco_handle *h, int32_t env, float *logits, uint8_t *actions);
+
+/* Policy-kernel variants: *count variants exist; *chosen is the one in use.
+ * eco_policy_variant_name() describes variant k (static string). */
+int eco_policy_variants(const eco_handle *h, int32_t *count, int32_t *chosen);
+const char *eco_policy_variant_name(int32_t k);
+
+/* Like eco_step, and also records a CUDA-event pair around the policy
+ * kernel of every step, on the library stream, inside the step's graph.
+ * eco_policy_timing() synchronises, then returns the summed policy-kernel
+ * time in milliseconds and the number of timed steps since its last call
+ * (at most 4096 steps are buffered; more returns ECO_EINVAL). */
+int eco_step_timed(eco_handle *h, int32_t n_steps);
+int eco_policy_timing(eco_handle *h, double *total_ms, int32_t *n_timed);
+
+/* Run only the policy phase (observe + MLP + sample) of the current state
+ * n_iters times, for timing and for the policy-parity tests; the world
+ * state does not change.  Asynchronous. */
+int eco_policy_only(eco_handle *h, int32_t n_iters);
+
+/* Algorithmic bytes the policy phase must read for the current alive
+ * population (weights of every alive agent in the streamed precision,
+ * biases and scales in FP32); synchronises. */
+int eco_policy_bytes(eco_handle *h, int64_t *bytes, int64_t *n_alive);
+
+/* Release the handle (not the workspace).  Accepts NULL. */
+void eco_destroy(eco_handle *h);
+
+/* Message of the last failure on h (or a global message when h is NULL). */
+const char *eco_last_error(const eco_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ECO_H */

@@ -1,0 +1,738 @@
+// eco_api.cu -- the C-ABI declared in include/eco.h: configuration checks,
+// the parameter-block layout, carving of the caller's workspace, the CUDA
+// graph of one step, the policy-variant autotuner, and host <-> device
+// state and parameter I/O.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/eco.h"
+#include "eco_internal.cuh"
+#include "eco_kernels.h"
+
+using namespace eco;
+
+static_assert((int)ECO_STAT_ACT0 == (int)eco::ST_ACT0, "stat enum");
+static_assert((int)ECO_STAT_ENERGY_TOTAL == (int)eco::ST_ENERGY_TOTAL, "stat enum");
+static_assert((int)ECO_N_STATS == (int)eco::N_ST, "stat enum");
+
+static char g_err[512] = "";
+
+struct eco_handle {
+  // configuration
+  int n_envs;
+  std::vector<int32_t> side, slots, init_alive;
+  std::vector<uint32_t> seed;
+  Layout L;
+  Rules R;
+  // device
+  Dev d;
+  std::vector<EnvDesc> env_host;
+  EnvDesc *env_dev;
+  uint8_t *ws;
+  size_t ws_bytes;
+  cudaStream_t stream;
+  bool own_stream;
+  EnvGrid grid;
+  // policy
+  int variant;       // chosen variant (0 = not chosen yet)
+  int forced;        // variant forced by the configuration (0 = autotune)
+  PolicyLaunch pl;
+  // step graph
+  cudaGraphExec_t graph;
+  cudaGraphNode_t ev_node[2];
+  cudaEvent_t ev_dummy[2];
+  std::vector<cudaEvent_t> ev_pool;  // pairs
+  int ev_used;
+  char err[512];
+};
+
+static int fail(eco_handle *h, int code, const char *fmt, ...) {
+  char *dst = h ? h->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  if (h) snprintf(g_err, sizeof(g_err), "%s", h->err);
+  return code;
+}
+
+#define CUDA_TRY(h, call)                                                                     \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail((h), ECO_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static int64_t pad(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// Bernoulli threshold floor(p * 2^32) (same definition as the method's).
+static uint32_t threshold_of(float p) {
+  const double v = (double)p;
+  if (!(v > 0.0)) return 0u;
+  if (v >= 1.0) return 0xFFFFFFFFu;
+  return (uint32_t)std::floor(v * 4294967296.0);
+}
+
+static int validate(const eco_config *c, char *msg, size_t n) {
+  if (!c) return snprintf(msg, n, "null config"), ECO_EINVAL;
+  if (c->abi_version != ECO_ABI_VERSION) return snprintf(msg, n, "abi_version %d != %d", c->abi_version, ECO_ABI_VERSION), ECO_EABI;
+  if (c->n_envs < 1 || c->n_envs > 4096) return snprintf(msg, n, "n_envs out of range"), ECO_EINVAL;
+  if (!c->env_side || !c->env_slots || !c->env_init_alive || !c->env_seed)
+    return snprintf(msg, n, "null per-environment array"), ECO_EINVAL;
+  if (c->patch_k < 1 || (c->patch_k & 1) == 0 || c->patch_k > 31) return snprintf(msg, n, "patch_k must be odd in [1, 31]"), ECO_EINVAL;
+  if (c->n_scalars != 4 && c->n_scalars != 8) return snprintf(msg, n, "n_scalars must be 4 or 8"), ECO_EINVAL;
+  if (c->hidden != 32 && c->hidden != 64 && c->hidden != 128) return snprintf(msg, n, "hidden must be 32, 64 or 128"), ECO_EINVAL;
+  if (c->n_actions != 6 && c->n_actions != 9) return snprintf(msg, n, "n_actions must be 6 or 9"), ECO_EINVAL;
+  if (c->precision < ECO_FP32 || c->precision > ECO_FP8_E4M3) return snprintf(msg, n, "bad precision"), ECO_EINVAL;
+  if (c->e_repro <= 0 || c->attack_den <= 0 || c->attack_num < 0 || c->e_metab < 0)
+    return snprintf(msg, n, "bad energy constants"), ECO_EINVAL;
+  if (!(c->sigma >= 0.0f) || !std::isfinite(c->sigma)) return snprintf(msg, n, "bad sigma"), ECO_EINVAL;
+  if (c->policy_variant < 0 || c->policy_variant > policy_variant_count())
+    return snprintf(msg, n, "policy_variant out of range"), ECO_EINVAL;
+  long long cells = 0, slots = 0;
+  for (int e = 0; e < c->n_envs; ++e) {
+    const int L = c->env_side[e];
+    if (L < 4 || (L & 1) || L > 16384) return snprintf(msg, n, "env %d: side must be even in [4, 16384]", e), ECO_EINVAL;
+    if (c->patch_k > L) return snprintf(msg, n, "env %d: patch larger than the grid", e), ECO_EINVAL;
+    if (c->env_slots[e] < 1) return snprintf(msg, n, "env %d: slots must be >= 1", e), ECO_EINVAL;
+    if (c->env_init_alive[e] < 0 || c->env_init_alive[e] > c->env_slots[e] || c->env_init_alive[e] > L * L)
+      return snprintf(msg, n, "env %d: init_alive out of range", e), ECO_EINVAL;
+    cells += (long long)L * L;
+    slots += c->env_slots[e];
+  }
+  if (cells > (1ll << 30) || slots > (1ll << 28)) return snprintf(msg, n, "too many cells or slots"), ECO_EINVAL;
+  return ECO_OK;
+}
+
+static Layout make_layout(const eco_config *c) {
+  Layout L;
+  L.D = 3 * c->patch_k * c->patch_k + c->n_scalars;
+  L.H = c->hidden;
+  L.A = c->n_actions;
+  L.P = L.H * L.D + L.H + L.H * L.H + L.H + L.A * L.H + L.A;
+  const int nW = L.D * L.H + L.H * L.H + L.A * L.H;
+  const int nB = 2 * L.H + L.A;
+  // FP32 masters: W1 | W2 | W3 | biases (W sections are multiples of 4 floats)
+  L.moff_w1 = 0;
+  L.moff_w2 = L.D * L.H * 4;
+  L.moff_w3 = L.moff_w2 + L.H * L.H * 4;
+  L.moff_bias = nW * 4;
+  L.mstride = pad((int64_t)(nW + nB) * 4, 128);
+  L.es = c->precision == ECO_FP32 ? 4 : (c->precision == ECO_BF16 ? 2 : 1);
+  L.off_w1 = 0;
+  L.off_w2 = L.D * L.H * L.es;
+  L.off_w3 = L.off_w2 + L.H * L.H * L.es;
+  const int wend = L.off_w3 + L.A * L.H * L.es;
+  L.off_scale = wend;
+  L.off_bias = (c->precision == ECO_FP8_E4M3) ? (int)(wend + pad(nB * 4, 16)) : wend;
+  L.stride = (c->precision == ECO_FP32) ? L.mstride : pad(L.off_bias + pad(nB * 4, 16), 128);
+  return L;
+}
+
+// Workspace carving (256-byte aligned regions).
+struct Carve {
+  size_t off = 0;
+  uint8_t *base = nullptr;
+  template <class T>
+  T *take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d, EnvDesc **env_dev) {
+  Carve k;
+  k.base = base;
+  long long cells = 0, slots = 0;
+  for (int e = 0; e < c->n_envs; ++e) {
+    cells += (long long)c->env_side[e] * c->env_side[e];
+    slots += c->env_slots[e];
+  }
+  const int E = c->n_envs;
+  Dev &D = *d;
+  memset(&D, 0, sizeof(D));
+  D.n_envs = E;
+  D.total_cells = (int)cells;
+  D.total_slots = (int)slots;
+  // weights first: the big arrays start at the workspace base
+  D.master = k.take<float>((size_t)slots * (L.mstride / 4));
+  if (c->precision == ECO_FP32)
+    D.wq = reinterpret_cast<uint8_t *>(D.master);
+  else
+    D.wq = k.take<uint8_t>((size_t)slots * L.stride);
+  *env_dev = k.take<EnvDesc>(E);
+  D.env = *env_dev;
+  D.cellf = k.take<uint8_t>(cells);
+  D.occ = k.take<int32_t>(cells);
+  D.claim_move = k.take<unsigned long long>(cells);
+  D.cnt_move = k.take<uint32_t>(cells);
+  D.claim_birth = k.take<unsigned long long>(cells);
+  D.alive = k.take<uint8_t>(slots);
+  D.pos = k.take<int32_t>(slots);
+  D.facing = k.take<uint8_t>(slots);
+  D.energy = k.take<int32_t>(slots);
+  D.parent = k.take<int32_t>(slots);
+  D.birth = k.take<int32_t>(slots);
+  D.act = k.take<uint8_t>(slots);
+  D.env_of = k.take<uint16_t>(slots);
+  D.tgt = k.take<int32_t>(slots);
+  D.gain = k.take<int32_t>(slots);
+  D.claim_att = k.take<unsigned long long>(slots);
+  D.logits = k.take<float>((size_t)slots * L.A);
+  D.alive_list = k.take<int32_t>(slots);
+  D.counters = k.take<int32_t>(CNT_N);
+  D.births = k.take<int2>(slots);
+  D.free_list = k.take<int32_t>(slots);
+  D.bflag = k.take<uint8_t>(slots);
+  D.birth_contenders = k.take<int32_t>(E);
+  D.stats_step = k.take<long long>((size_t)E * N_ST);
+  D.stats_total = k.take<long long>((size_t)E * N_ST);
+  D.stats_last = k.take<long long>((size_t)E * N_ST);
+  D.step = k.take<long long>(1);
+  D.hist = k.take<uint32_t>((size_t)E * 65536);
+  D.place_prefix = k.take<unsigned long long>(E);
+  D.place_remaining = k.take<int32_t>(E);
+  return (k.off + 255) & ~(size_t)255;
+}
+
+extern "C" int eco_param_count(const eco_config *cfg, int32_t *n_params, int32_t *obs_dim) {
+  char msg[256];
+  int rc = validate(cfg, msg, sizeof msg);
+  if (rc) return fail(nullptr, rc, "%s", msg);
+  Layout L = make_layout(cfg);
+  if (n_params) *n_params = L.P;
+  if (obs_dim) *obs_dim = L.D;
+  return ECO_OK;
+}
+
+extern "C" int eco_workspace_bytes(const eco_config *cfg, size_t *bytes) {
+  char msg[256];
+  int rc = validate(cfg, msg, sizeof msg);
+  if (rc) return fail(nullptr, rc, "%s", msg);
+  if (!bytes) return fail(nullptr, ECO_EINVAL, "null bytes");
+  Layout L = make_layout(cfg);
+  Dev d;
+  EnvDesc *ed;
+  *bytes = carve(cfg, L, nullptr, &d, &ed);
+  return ECO_OK;
+}
+
+static void destroy_graph(eco_handle *h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+}
+
+extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t bytes, void *stream,
+                          eco_handle **out) {
+  if (!out) return fail(nullptr, ECO_EINVAL, "null out");
+  *out = nullptr;
+  char msg[256];
+  int rc = validate(cfg, msg, sizeof msg);
+  if (rc) return fail(nullptr, rc, "%s", msg);
+  size_t need = 0;
+  eco_workspace_bytes(cfg, &need);
+  if (!dev_workspace || bytes < need) return fail(nullptr, ECO_ENOMEM, "workspace of %zu bytes < %zu needed", bytes, need);
+  if ((reinterpret_cast<uintptr_t>(dev_workspace) & 255) != 0) return fail(nullptr, ECO_EINVAL, "workspace not 256-byte aligned");
+
+  eco_handle *h = new eco_handle();
+  h->n_envs = cfg->n_envs;
+  h->side.assign(cfg->env_side, cfg->env_side + cfg->n_envs);
+  h->slots.assign(cfg->env_slots, cfg->env_slots + cfg->n_envs);
+  h->init_alive.assign(cfg->env_init_alive, cfg->env_init_alive + cfg->n_envs);
+  h->seed.assign(cfg->env_seed, cfg->env_seed + cfg->n_envs);
+  h->L = make_layout(cfg);
+  Rules &R = h->R;
+  R.patch_k = cfg->patch_k;
+  R.n_scalars = cfg->n_scalars;
+  R.flags = cfg->flags;
+  R.precision = cfg->precision;
+  R.sigma = cfg->sigma;
+  R.thr_food = threshold_of(cfg->food_density);
+  R.thr_regrow = threshold_of(cfg->regrow_p);
+  R.thr_wall = threshold_of(cfg->wall_density);
+  R.e_init = cfg->e_init;
+  R.e_metab = cfg->e_metab;
+  R.e_food = cfg->e_food;
+  R.e_repro = cfg->e_repro;
+  R.attack_num = cfg->attack_num;
+  R.attack_den = cfg->attack_den;
+  h->ws = reinterpret_cast<uint8_t *>(dev_workspace);
+  h->ws_bytes = bytes;
+  carve(cfg, h->L, h->ws, &h->d, &h->env_dev);
+  int so = 0, co = 0;
+  for (int e = 0; e < cfg->n_envs; ++e) {
+    EnvDesc ed;
+    ed.side = cfg->env_side[e];
+    ed.slot_off = so;
+    ed.n_slots = cfg->env_slots[e];
+    ed.cell_off = co;
+    ed.init_alive = cfg->env_init_alive[e];
+    ed.seed = cfg->env_seed[e];
+    h->env_host.push_back(ed);
+    so += ed.n_slots;
+    co += ed.side * ed.side;
+  }
+  h->own_stream = (stream == nullptr);
+  if (h->own_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete h;
+      return fail(nullptr, ECO_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+  } else {
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->grid.sms, cudaDevAttrMultiProcessorCount, dev);
+  h->grid.slot_blocks = grid_for(h->d.total_slots, 256, h->grid.sms * 8);
+  h->grid.cell_blocks = grid_for(h->d.total_cells / 4, 256, h->grid.sms * 8);
+  h->grid.birth_blocks = h->grid.sms * 2;
+  h->forced = cfg->policy_variant;
+  h->variant = 0;
+  h->graph = nullptr;
+  h->ev_used = 0;
+  h->err[0] = 0;
+  cudaError_t e = cudaMemcpyAsync(h->env_dev, h->env_host.data(), sizeof(EnvDesc) * h->n_envs,
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws, 0, need, h->stream);
+  if (e == cudaSuccess) e = launch_init_static(h->d, h->grid, h->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[1]);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    int r = fail(nullptr, ECO_ECUDA, "create: %s", cudaGetErrorString(e));
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return r;
+  }
+  if (h->forced) {
+    e = policy_prepare(h->L, h->R, h->forced, &h->pl);
+    if (e != cudaSuccess) {
+      int r = fail(nullptr, ECO_ECUDA, "policy variant %d: %s", h->forced, cudaGetErrorString(e));
+      eco_destroy(h);
+      return r;
+    }
+    h->variant = h->forced;
+  }
+  *out = h;
+  return ECO_OK;
+}
+
+extern "C" void eco_destroy(eco_handle *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  destroy_graph(h);
+  for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
+  if (h->ev_dummy[0]) cudaEventDestroy(h->ev_dummy[0]);
+  if (h->ev_dummy[1]) cudaEventDestroy(h->ev_dummy[1]);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+extern "C" const char *eco_last_error(const eco_handle *h) { return h ? h->err : g_err; }
+
+static int check_status(eco_handle *h) {
+  int32_t st = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&st, h->d.counters + CNT_STATUS, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (st & 3) return fail(h, ECO_EINVAL, "reset: fewer non-wall cells than founders (status %d)", st);
+  if (st & 4) return fail(h, ECO_ETIMEOUT, "a device-side wait ran out of its budget");
+  return ECO_OK;
+}
+
+extern "C" int eco_reset(eco_handle *h) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  CUDA_TRY(h, launch_reset(h->d, h->L, h->R, h->grid, h->stream));
+  return check_status(h);
+}
+
+// Choose the fastest policy variant on the current state (autotuner).
+static int autotune(eco_handle *h) {
+  if (h->variant) return ECO_OK;
+  CUDA_TRY(h, launch_compact(h->d, h->stream));
+  cudaEvent_t a, b;
+  CUDA_TRY(h, cudaEventCreate(&a));
+  CUDA_TRY(h, cudaEventCreate(&b));
+  float best_ms = 1e30f;
+  int best = 0;
+  for (int v = 1; v <= policy_variant_count(); ++v) {
+    PolicyLaunch pl;
+    if (policy_prepare(h->L, h->R, v, &pl) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    for (int w = 0; w < 2; ++w) CUDA_TRY(h, policy_launch(pl, h->d, h->L, h->R, h->stream));
+    CUDA_TRY(h, cudaEventRecord(a, h->stream));
+    for (int r = 0; r < 5; ++r) CUDA_TRY(h, policy_launch(pl, h->d, h->L, h->R, h->stream));
+    CUDA_TRY(h, cudaEventRecord(b, h->stream));
+    CUDA_TRY(h, cudaEventSynchronize(b));
+    float ms = 0;
+    CUDA_TRY(h, cudaEventElapsedTime(&ms, a, b));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+      h->pl = pl;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (!best) return fail(h, ECO_ECUDA, "no policy variant could be prepared");
+  h->variant = best;
+  return ECO_OK;
+}
+
+static cudaError_t enqueue_step(eco_handle *h) {
+  cudaError_t e = launch_compact(h->d, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_dummy[0], h->stream);
+  if (e == cudaSuccess) e = policy_launch(h->pl, h->d, h->L, h->R, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_dummy[1], h->stream);
+  if (e == cudaSuccess) e = launch_env_phases(h->d, h->L, h->R, h->grid, h->stream);
+  return e;
+}
+
+static int build_graph(eco_handle *h) {
+  if (h->graph) return ECO_OK;
+  int rc = autotune(h);
+  if (rc) return rc;
+  cudaGraph_t g;
+  CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = enqueue_step(h);
+  cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+  if (e != cudaSuccess) return fail(h, ECO_ECUDA, "capture: %s", cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return fail(h, ECO_ECUDA, "end capture: %s", cudaGetErrorString(e2));
+  // locate the two event-record nodes (in capture order)
+  size_t n = 0;
+  CUDA_TRY(h, cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  CUDA_TRY(h, cudaGraphGetNodes(g, nodes.data(), &n));
+  int found = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    CUDA_TRY(h, cudaGraphNodeGetType(nodes[i], &t));
+    if (t == cudaGraphNodeTypeEventRecord) {
+      cudaEvent_t ev;
+      CUDA_TRY(h, cudaGraphEventRecordNodeGetEvent(nodes[i], &ev));
+      if (ev == h->ev_dummy[0]) h->ev_node[0] = nodes[i], ++found;
+      if (ev == h->ev_dummy[1]) h->ev_node[1] = nodes[i], ++found;
+    }
+  }
+  if (found != 2) {
+    cudaGraphDestroy(g);
+    return fail(h, ECO_ECUDA, "step graph: event nodes not found");
+  }
+  cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return fail(h, ECO_ECUDA, "instantiate: %s", cudaGetErrorString(ie));
+  return ECO_OK;
+}
+
+static int step_impl(eco_handle *h, int32_t n_steps, bool timed) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  if (n_steps < 0) return fail(h, ECO_EINVAL, "n_steps < 0");
+  if (n_steps == 0) return ECO_OK;
+  int rc = build_graph(h);
+  if (rc) return rc;
+  if (timed) {
+    if (h->ev_used + n_steps > 4096) return fail(h, ECO_EINVAL, "more than 4096 timed steps buffered");
+    while ((int)h->ev_pool.size() < 2 * (h->ev_used + n_steps)) {
+      cudaEvent_t ev;
+      CUDA_TRY(h, cudaEventCreate(&ev));
+      h->ev_pool.push_back(ev);
+    }
+  }
+  for (int i = 0; i < n_steps; ++i) {
+    if (timed) {
+      CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(h->graph, h->ev_node[0], h->ev_pool[2 * h->ev_used]));
+      CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(h->graph, h->ev_node[1], h->ev_pool[2 * h->ev_used + 1]));
+      ++h->ev_used;
+    }
+    CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
+  }
+  if (timed) {
+    CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(h->graph, h->ev_node[0], h->ev_dummy[0]));
+    CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(h->graph, h->ev_node[1], h->ev_dummy[1]));
+  }
+  return ECO_OK;
+}
+
+extern "C" int eco_step(eco_handle *h, int32_t n_steps) { return step_impl(h, n_steps, false); }
+extern "C" int eco_step_timed(eco_handle *h, int32_t n_steps) { return step_impl(h, n_steps, true); }
+
+extern "C" int eco_policy_timing(eco_handle *h, double *total_ms, int32_t *n_timed) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  double tot = 0;
+  for (int i = 0; i < h->ev_used; ++i) {
+    float ms = 0;
+    CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]));
+    tot += ms;
+  }
+  if (total_ms) *total_ms = tot;
+  if (n_timed) *n_timed = h->ev_used;
+  h->ev_used = 0;
+  return ECO_OK;
+}
+
+extern "C" int eco_policy_only(eco_handle *h, int32_t n_iters) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  int rc = autotune(h);
+  if (rc) return rc;
+  CUDA_TRY(h, launch_compact(h->d, h->stream));
+  for (int i = 0; i < n_iters; ++i) CUDA_TRY(h, policy_launch(h->pl, h->d, h->L, h->R, h->stream));
+  return ECO_OK;
+}
+
+extern "C" int eco_policy_variants(const eco_handle *h, int32_t *count, int32_t *chosen) {
+  if (count) *count = policy_variant_count();
+  if (chosen) *chosen = h ? h->variant : 0;
+  return ECO_OK;
+}
+
+extern "C" const char *eco_policy_variant_name(int32_t k) { return policy_variant_name(k); }
+
+extern "C" int eco_policy_bytes(eco_handle *h, int64_t *bytes, int64_t *n_alive) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  int32_t n = 0;
+  CUDA_TRY(h, launch_compact(h->d, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(&n, h->d.counters + CNT_N_ALIVE, sizeof n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  const Layout &L = h->L;
+  const int64_t nW = (int64_t)L.D * L.H + L.H * L.H + L.A * L.H;
+  const int64_t nB = 2 * L.H + L.A;
+  int64_t per = nW * L.es + nB * 4;
+  if (h->R.precision == ECO_FP8_E4M3) per += nB * 4;  // row scales
+  if (bytes) *bytes = per * n;
+  if (n_alive) *n_alive = n;
+  return ECO_OK;
+}
+
+extern "C" int eco_read_stats(eco_handle *h, eco_stats *total, eco_stats *last, int32_t n_envs) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  if (n_envs < 0 || n_envs > h->n_envs) return fail(h, ECO_EINVAL, "n_envs out of range");
+  if (total)
+    CUDA_TRY(h, cudaMemcpyAsync(total, h->d.stats_total, sizeof(eco_stats) * n_envs, cudaMemcpyDeviceToHost, h->stream));
+  if (last)
+    CUDA_TRY(h, cudaMemcpyAsync(last, h->d.stats_last, sizeof(eco_stats) * n_envs, cudaMemcpyDeviceToHost, h->stream));
+  return check_status(h);
+}
+
+// ---------------------------------------------------------------------------
+// State and parameter I/O (host-side marshalling between the library's
+// layout and the plain views of the header).
+// ---------------------------------------------------------------------------
+
+static int check_env(eco_handle *h, int32_t env) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  if (env < 0 || env >= h->n_envs) return fail(h, ECO_EINVAL, "env %d out of range", env);
+  return ECO_OK;
+}
+
+extern "C" int eco_read_state(eco_handle *h, int32_t env, eco_state_view *out) {
+  int rc = check_env(h, env);
+  if (rc) return rc;
+  if (!out) return fail(h, ECO_EINVAL, "null view");
+  const EnvDesc &ed = h->env_host[env];
+  const int N = ed.side * ed.side, S = ed.n_slots;
+  std::vector<uint8_t> cellf(N), alive(S), facing(S);
+  std::vector<int32_t> occ(N), pos(S), energy(S), parent(S), birth(S);
+  long long step = 0;
+  cudaStream_t s = h->stream;
+  CUDA_TRY(h, cudaMemcpyAsync(cellf.data(), h->d.cellf + ed.cell_off, N, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaMemcpyAsync(occ.data(), h->d.occ + ed.cell_off, 4 * (size_t)N, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaMemcpyAsync(alive.data(), h->d.alive + ed.slot_off, S, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaMemcpyAsync(facing.data(), h->d.facing + ed.slot_off, S, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaMemcpyAsync(pos.data(), h->d.pos + ed.slot_off, 4 * (size_t)S, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaMemcpyAsync(energy.data(), h->d.energy + ed.slot_off, 4 * (size_t)S, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaMemcpyAsync(parent.data(), h->d.parent + ed.slot_off, 4 * (size_t)S, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaMemcpyAsync(birth.data(), h->d.birth + ed.slot_off, 4 * (size_t)S, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaMemcpyAsync(&step, h->d.step, sizeof step, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  for (int c = 0; c < N; ++c) {
+    if (out->food) out->food[c] = (cellf[c] & CELL_FOOD) ? 1 : 0;
+    if (out->wall) out->wall[c] = (cellf[c] & CELL_WALL) ? 1 : 0;
+    if (out->occ) out->occ[c] = occ[c] < 0 ? -1 : occ[c] - ed.slot_off;
+  }
+  for (int i = 0; i < S; ++i) {
+    if (out->alive) out->alive[i] = alive[i];
+    if (out->x) out->x[i] = pos[i] % ed.side;
+    if (out->y) out->y[i] = pos[i] / ed.side;
+    if (out->facing) out->facing[i] = facing[i];
+    if (out->energy) out->energy[i] = energy[i];
+    if (out->parent) out->parent[i] = parent[i];
+    if (out->birth_step) out->birth_step[i] = birth[i];
+  }
+  if (out->step) *out->step = step;
+  return ECO_OK;
+}
+
+extern "C" int eco_write_state(eco_handle *h, int32_t env, const eco_state_view *in) {
+  int rc = check_env(h, env);
+  if (rc) return rc;
+  if (!in) return fail(h, ECO_EINVAL, "null view");
+  const EnvDesc &ed = h->env_host[env];
+  const int N = ed.side * ed.side, S = ed.n_slots;
+  cudaStream_t s = h->stream;
+  const bool cells = in->food || in->wall || in->occ;
+  if (cells && !(in->food && in->wall && in->occ)) return fail(h, ECO_EINVAL, "food, wall and occ must be written together");
+  const bool where = in->alive || in->x || in->y;
+  if (where && !(in->alive && in->x && in->y)) return fail(h, ECO_EINVAL, "alive, x and y must be written together");
+  std::vector<uint8_t> cellf, alive;
+  std::vector<int32_t> occ, pos;
+  if (cells) {
+    cellf.resize(N);
+    occ.resize(N);
+    for (int c = 0; c < N; ++c) {
+      if (in->occ[c] < -1 || in->occ[c] >= S) return fail(h, ECO_EINVAL, "occ[%d] out of range", c);
+      cellf[c] = (uint8_t)((in->food[c] ? CELL_FOOD : 0) | (in->wall[c] ? CELL_WALL : 0) | (in->occ[c] >= 0 ? CELL_AGENT : 0));
+      occ[c] = in->occ[c] < 0 ? -1 : in->occ[c] + ed.slot_off;
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->d.cellf + ed.cell_off, cellf.data(), N, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d.occ + ed.cell_off, occ.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s));
+  }
+  if (where) {
+    alive.assign(in->alive, in->alive + S);
+    pos.resize(S);
+    for (int i = 0; i < S; ++i) {
+      if (in->x[i] < 0 || in->x[i] >= ed.side || in->y[i] < 0 || in->y[i] >= ed.side)
+        return fail(h, ECO_EINVAL, "slot %d position out of range", i);
+      pos[i] = in->y[i] * ed.side + in->x[i];
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->d.alive + ed.slot_off, alive.data(), S, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d.pos + ed.slot_off, pos.data(), 4 * (size_t)S, cudaMemcpyHostToDevice, s));
+  }
+  if (in->facing) CUDA_TRY(h, cudaMemcpyAsync(h->d.facing + ed.slot_off, in->facing, S, cudaMemcpyHostToDevice, s));
+  if (in->energy) CUDA_TRY(h, cudaMemcpyAsync(h->d.energy + ed.slot_off, in->energy, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
+  if (in->parent) CUDA_TRY(h, cudaMemcpyAsync(h->d.parent + ed.slot_off, in->parent, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
+  if (in->birth_step) CUDA_TRY(h, cudaMemcpyAsync(h->d.birth + ed.slot_off, in->birth_step, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
+  if (in->step) {
+    // all environments share one step counter
+    long long st = *in->step;
+    CUDA_TRY(h, cudaMemcpyAsync(h->d.step, &st, sizeof st, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+  }
+  CUDA_TRY(h, launch_recount(h->d, h->R, s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  return ECO_OK;
+}
+
+// Logical index of every master element of the tiled block (host copy of
+// the layout map), or -1 for padding.
+static void logical_map(const Layout &L, std::vector<int> &map) {
+  const int D = L.D, H = L.H, A = L.A;
+  const int per = (int)(L.mstride / 4);
+  map.assign(per, -1);
+  int q = 0;
+  for (int j = 0; j < D; ++j)
+    for (int o = 0; o < H; ++o) map[q++] = o * D + j;
+  for (int j = 0; j < H; ++j)
+    for (int o = 0; o < H; ++o) map[q++] = D * H + H + o * H + j;
+  for (int a = 0; a < A; ++a)
+    for (int j = 0; j < H; ++j) map[q++] = D * H + 2 * H + H * H + a * H + j;
+  for (int o = 0; o < H; ++o) map[q++] = D * H + o;
+  for (int o = 0; o < H; ++o) map[q++] = D * H + H + H * H + o;
+  for (int a = 0; a < A; ++a) map[q++] = D * H + 2 * H + H * H + A * H + a;
+}
+
+static int check_range(eco_handle *h, int32_t env, int32_t slot0, int32_t n) {
+  int rc = check_env(h, env);
+  if (rc) return rc;
+  if (slot0 < 0 || n < 0 || slot0 + n > h->env_host[env].n_slots) return fail(h, ECO_EINVAL, "slot range out of bounds");
+  return ECO_OK;
+}
+
+extern "C" int eco_read_params(eco_handle *h, int32_t env, int32_t slot0, int32_t n, float *out) {
+  int rc = check_range(h, env, slot0, n);
+  if (rc) return rc;
+  if (n == 0) return ECO_OK;
+  if (!out) return fail(h, ECO_EINVAL, "null output");
+  const Layout &L = h->L;
+  const int per = (int)(L.mstride / 4);
+  std::vector<float> buf((size_t)n * per);
+  const int g0 = h->env_host[env].slot_off + slot0;
+  CUDA_TRY(h, cudaMemcpyAsync(buf.data(), h->d.master + (size_t)g0 * per, buf.size() * 4, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  std::vector<int> map;
+  logical_map(L, map);
+  for (int i = 0; i < n; ++i)
+    for (int q = 0; q < per; ++q)
+      if (map[q] >= 0) out[(size_t)i * L.P + map[q]] = buf[(size_t)i * per + q];
+  return ECO_OK;
+}
+
+extern "C" int eco_write_params(eco_handle *h, int32_t env, int32_t slot0, int32_t n, const float *in) {
+  int rc = check_range(h, env, slot0, n);
+  if (rc) return rc;
+  if (n == 0) return ECO_OK;
+  if (!in) return fail(h, ECO_EINVAL, "null input");
+  const Layout &L = h->L;
+  const int per = (int)(L.mstride / 4);
+  std::vector<float> buf((size_t)n * per, 0.0f);
+  std::vector<int> map;
+  logical_map(L, map);
+  for (int i = 0; i < n; ++i)
+    for (int q = 0; q < per; ++q)
+      if (map[q] >= 0) buf[(size_t)i * per + q] = in[(size_t)i * L.P + map[q]];
+  const int g0 = h->env_host[env].slot_off + slot0;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d.master + (size_t)g0 * per, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, launch_requant(h->d, h->L, h->R, g0, n, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return ECO_OK;
+}
+
+extern "C" int eco_read_streamed(eco_handle *h, int32_t env, int32_t slot0, int32_t n, void *codes,
+                                 float *row_scales) {
+  int rc = check_range(h, env, slot0, n);
+  if (rc) return rc;
+  if (h->R.precision == ECO_FP32) return fail(h, ECO_EINVAL, "no streamed copy in the FP32 form");
+  if (n == 0) return ECO_OK;
+  const Layout &L = h->L;
+  std::vector<uint8_t> buf((size_t)n * L.stride);
+  const int g0 = h->env_host[env].slot_off + slot0;
+  CUDA_TRY(h, cudaMemcpyAsync(buf.data(), h->d.wq + (size_t)g0 * L.stride, buf.size(), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  std::vector<int> map;
+  logical_map(L, map);
+  const int nW = L.D * L.H + L.H * L.H + L.A * L.H;
+  const int nB = 2 * L.H + L.A;
+  for (int i = 0; i < n; ++i) {
+    const uint8_t *blk = buf.data() + (size_t)i * L.stride;
+    if (codes) {
+      if (L.es == 2) {
+        uint16_t *c = reinterpret_cast<uint16_t *>(codes) + (size_t)i * L.P;
+        for (int q = 0; q < L.P; ++q) c[q] = 0;
+        for (int q = 0; q < nW; ++q) {
+          uint16_t v;
+          memcpy(&v, blk + 2 * q, 2);
+          c[map[q]] = v;
+        }
+      } else {
+        uint8_t *c = reinterpret_cast<uint8_t *>(codes) + (size_t)i * L.P;
+        for (int q = 0; q < L.P; ++q) c[q] = 0;
+        for (int q = 0; q < nW; ++q) c[map[q]] = blk[q];
+      }
+    }
+    if (row_scales && L.es == 1) memcpy(row_scales + (size_t)i * nB, blk + L.off_scale, 4 * (size_t)nB);
+  }
+  return ECO_OK;
+}
+
+extern "C" int eco_read_policy_io(eco_handle *h, int32_t env, float *logits, uint8_t *actions) {
+  int rc = check_env(h, env);
+  if (rc) return rc;
+  const EnvDesc &ed = h->env_host[env];
+  if (logits)
+    CUDA_TRY(h, cudaMemcpyAsync(logits, h->d.logits + (size_t)ed.slot_off * h->L.A,
+                                sizeof(float) * (size_t)ed.n_slots * h->L.A, cudaMemcpyDeviceToHost, h->stream));
+  if (actions)
+    CUDA_TRY(h, cudaMemcpyAsync(actions, h->d.act + ed.slot_off, ed.n_slots, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return ECO_OK;
+}

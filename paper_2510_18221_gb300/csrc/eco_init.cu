@@ -1,0 +1,369 @@
+// eco_init.cu -- reset of every environment (Sec. 3.2: grid world with
+// randomly distributed resources and a founding population; Sec. 3.3:
+// Kaiming-style initial weights, zero biases) and re-derivation of the
+// streamed BF16 / FP8 weight copy from the FP32 masters.
+//
+// Founders: the K non-wall cells with the smallest 64-bit keys
+// (PLACE draw << 32 | local cell) -- all keys are distinct -- found by a
+// four-round radix select on 16-bit digits (one histogram pass over the
+// cells per round), then numbered in ascending cell order by a block scan.
+#include "eco_internal.cuh"
+#include "eco_kernels.h"
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+namespace eco {
+
+__device__ __forceinline__ unsigned long long place_key(const EnvDesc &ed, int local_cell) {
+  const U4 r = philox((uint32_t)(local_cell >> 2), 0u, 0u, 0u, ed.seed, S_PLACE);
+  return ((unsigned long long)word_of(r, local_cell & 3) << 32) | (unsigned long long)(uint32_t)local_cell;
+}
+
+// Walls, food, empty occupancy, cleared claims.
+__global__ void k_init_cells(Dev d, Rules R) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.total_cells; c += gridDim.x * blockDim.x) {
+    const int e = env_of_cell(d.env, d.n_envs, c);
+    const EnvDesc ed = d.env[e];
+    const int lc = c - ed.cell_off;
+    const U4 rw = philox((uint32_t)(lc >> 2), 0u, 0u, 0u, ed.seed, S_WALL);
+    const bool wall = word_of(rw, lc & 3) < R.thr_wall;
+    const U4 rf = philox((uint32_t)(lc >> 2), 0u, 0u, 0u, ed.seed, S_FOOD_INIT);
+    const bool food = !wall && word_of(rf, lc & 3) < R.thr_food;
+    d.cellf[c] = (uint8_t)((wall ? CELL_WALL : 0u) | (food ? CELL_FOOD : 0u));
+    d.occ[c] = -1;
+    d.claim_move[c] = 0ull;
+    d.cnt_move[c] = 0u;
+    d.claim_birth[c] = 0ull;
+  }
+}
+
+// Per-slot agent fields (founders get alive / facing / energy here; their
+// cells come from the placement below).
+__global__ void k_init_agents(Dev d, Rules R) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.total_slots; s += gridDim.x * blockDim.x) {
+    int e = 0;
+    while (e + 1 < d.n_envs && d.env[e + 1].slot_off <= s) ++e;
+    const EnvDesc ed = d.env[e];
+    const int ls = s - ed.slot_off;
+    const bool founder = ls < ed.init_alive;
+    d.env_of[s] = (uint16_t)e;
+    d.alive[s] = founder ? 1 : 0;
+    d.pos[s] = 0;
+    uint8_t f = 0;
+    if (founder) {
+      const U4 r = philox((uint32_t)(ls >> 2), 0u, 0u, 0u, ed.seed, S_FACING_INIT);
+      f = (uint8_t)(word_of(r, ls & 3) >> 30);
+    }
+    d.facing[s] = f;
+    d.energy[s] = founder ? R.e_init : 0;
+    d.parent[s] = -1;
+    d.birth[s] = -1;
+    d.act[s] = 0;
+    d.tgt[s] = -1;
+    d.gain[s] = 0;
+    d.claim_att[s] = 0ull;
+  }
+}
+
+// Radix-select round: histogram of the 16-bit digit at `shift` among the
+// non-wall cells whose higher digits equal the prefix found so far.
+__global__ void k_place_hist(Dev d, int shift) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.total_cells; c += gridDim.x * blockDim.x) {
+    if (d.cellf[c] & CELL_WALL) continue;
+    const int e = env_of_cell(d.env, d.n_envs, c);
+    const EnvDesc ed = d.env[e];
+    if (ed.init_alive == 0) continue;
+    const unsigned long long key = place_key(ed, c - ed.cell_off);
+    if (shift < 48 && (key >> (shift + 16)) != d.place_prefix[e]) continue;
+    atomicAdd(&d.hist[(size_t)e * 65536 + ((key >> shift) & 0xFFFFull)], 1u);
+  }
+}
+
+// One CTA per environment: find the bin holding the remaining-th smallest
+// key, extend the prefix, clear the histogram.  A missing bin (fewer than K
+// non-wall cells) sets the status word.
+__global__ void __launch_bounds__(1024) k_place_find(Dev d) {
+  __shared__ int sh[33];
+  __shared__ int found_bin, found_before;
+  const int e = blockIdx.x;
+  uint32_t *h = d.hist + (size_t)e * 65536;
+  const int remaining = d.place_remaining[e];
+  if (d.env[e].init_alive == 0) return;
+  const int per = 65536 / blockDim.x;  // 64 bins per thread
+  const int beg = threadIdx.x * per;
+  int cnt = 0;
+  for (int i = 0; i < per; ++i) cnt += (int)h[beg + i];
+  int total;
+  int before = block_exclusive_scan(cnt, &total, sh);
+  if (threadIdx.x == 0) {
+    found_bin = -1;
+    found_before = 0;
+  }
+  __syncthreads();
+  if (before < remaining && before + cnt >= remaining) {
+    int run = before;
+    for (int i = 0; i < per; ++i) {
+      const int c = (int)h[beg + i];
+      if (run + c >= remaining) {
+        found_bin = beg + i;
+        found_before = run;
+        break;
+      }
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < per; ++i) h[beg + i] = 0u;
+  if (threadIdx.x == 0) {
+    if (found_bin < 0) {
+      atomicOr(&d.counters[CNT_STATUS], 1);
+    } else {
+      d.place_prefix[e] = (d.place_prefix[e] << 16) | (unsigned long long)found_bin;
+      d.place_remaining[e] = remaining - found_before;
+    }
+  }
+}
+
+// One CTA per environment: founders are the non-wall cells with key <= the
+// selected threshold; slot = rank in ascending cell order.
+__global__ void __launch_bounds__(1024) k_place_assign(Dev d) {
+  __shared__ int sh[33];
+  const int e = blockIdx.x;
+  const EnvDesc ed = d.env[e];
+  if (ed.init_alive == 0) return;
+  const unsigned long long thr = d.place_prefix[e];
+  const int n = ed.side * ed.side;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int beg = min(n, (int)threadIdx.x * per), end = min(n, beg + per);
+  int cnt = 0;
+  for (int c = beg; c < end; ++c)
+    if (!(d.cellf[ed.cell_off + c] & CELL_WALL) && place_key(ed, c) <= thr) ++cnt;
+  int total;
+  int off = block_exclusive_scan(cnt, &total, sh);
+  for (int c = beg; c < end; ++c) {
+    const int gc = ed.cell_off + c;
+    if (!(d.cellf[gc] & CELL_WALL) && place_key(ed, c) <= thr) {
+      // the guard only matters when the select failed (status already set)
+      if (off < ed.init_alive) {
+        const int slot = ed.slot_off + off;
+        d.pos[slot] = c;
+        d.occ[gc] = slot;
+        d.cellf[gc] |= (uint8_t)CELL_AGENT;
+      }
+      ++off;
+    }
+  }
+  if (threadIdx.x == 0 && total != ed.init_alive) atomicOr(&d.counters[CNT_STATUS], 2);
+}
+
+// Logical parameter index of master element q (see eco_env.cu).
+__device__ __forceinline__ int master_logical_i(const Layout &L, int q) {
+  const int D = L.D, H = L.H, A = L.A;
+  const int n1 = D * H, n2 = H * H, n3 = A * H;
+  if (q < n1) {
+    const int j = q / H, o = q - j * H;
+    return o * D + j;
+  }
+  q -= n1;
+  if (q < n2) {
+    const int j = q / H, o = q - j * H;
+    return D * H + H + o * H + j;
+  }
+  q -= n2;
+  if (q < n3) return D * H + 2 * H + H * H + q;
+  return -1;  // biases and padding
+}
+
+// Founders' weights: N(0,1) / sqrt(fan_in) from stream W_INIT at counter
+// (local slot, p / 4), biases zero; every other slot all zero.
+__global__ void k_init_params(Dev d, Layout L) {
+  const int64_t per_slot = L.mstride / 4;
+  const int nW1 = L.D * L.H, nW = L.D * L.H + L.H * L.H + L.A * L.H;
+  const int64_t total = (int64_t)d.total_slots * per_slot;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(i / per_slot);
+    const int q = (int)(i - (int64_t)s * per_slot);
+    const EnvDesc ed = d.env[d.env_of[s]];
+    const int ls = s - ed.slot_off;
+    float w = 0.0f;
+    if (ls < ed.init_alive && q < nW) {
+      const int p = master_logical_i(L, q);
+      const U4 r = philox((uint32_t)ls, (uint32_t)(p >> 2), 0u, 0u, ed.seed, S_W_INIT);
+      const float fan = (q < nW1) ? (float)L.D : (float)L.H;
+      w = __fdiv_rn(normal_of(r, p & 3), sqrtf(fan));
+    }
+    d.master[i] = w;
+  }
+}
+
+// Streamed copy of slots [slot0, slot0 + n): BF16 elementwise (RNE), FP8 per
+// output row (scale = max|w| / 448, satfinite RNE codes), biases FP32.
+__global__ void k_requant_bf16(Dev d, Layout L, int slot0, int n) {
+  const int nW = L.D * L.H + L.H * L.H + L.A * L.H;
+  const int nB = 2 * L.H + L.A;
+  const int per = nW + nB;
+  const int64_t total = (int64_t)n * per;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int s = slot0 + (int)(i / per);
+    const int q = (int)(i % per);
+    const float *m = d.master + (int64_t)s * (L.mstride / 4);
+    uint8_t *blk = d.wq + (int64_t)s * L.stride;
+    if (q < nW) {
+      reinterpret_cast<__nv_bfloat16 *>(blk)[q] = __float2bfloat16_rn(m[q]);
+    } else {
+      reinterpret_cast<float *>(blk + L.off_bias)[q - nW] = m[L.moff_bias / 4 + (q - nW)];
+    }
+  }
+}
+
+__global__ void k_requant_fp8(Dev d, Layout L, int slot0, int n) {
+  const int H = L.H, A = L.A, rows = 2 * H + A;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)n * rows;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < warps;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int s = slot0 + (int)(w / rows);
+    const int row = (int)(w % rows);
+    const float *m = d.master + (int64_t)s * (L.mstride / 4);
+    uint8_t *blk = d.wq + (int64_t)s * L.stride;
+    int base, stride, cnt;
+    if (row < H) { base = row; stride = H; cnt = L.D; }
+    else if (row < 2 * H) { base = L.D * H + (row - H); stride = H; cnt = H; }
+    else { base = L.D * H + H * H + (row - 2 * H) * H; stride = 1; cnt = H; }
+    float mx = 0.0f;
+    for (int j = lane; j < cnt; j += 32) mx = fmaxf(mx, fabsf(m[base + j * stride]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+    float sc = __fdiv_rn(mx, 448.0f);
+    if (sc == 0.0f) sc = 1.0f;
+    for (int j = lane; j < cnt; j += 32) {
+      const int idx = base + j * stride;
+      blk[idx] = (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(m[idx], sc), __NV_SATFINITE, __NV_E4M3);
+    }
+    if (lane == 0) {
+      reinterpret_cast<float *>(blk + L.off_scale)[row] = sc;
+      reinterpret_cast<float *>(blk + L.off_bias)[row] = m[L.moff_bias / 4 + row];
+    }
+  }
+}
+
+// Initial statistics: alive = K, food count, energy = K * e_init, step 0.
+__global__ void __launch_bounds__(1024) k_init_stats(Dev d, Rules R) {
+  __shared__ int sh[33];
+  const int e = blockIdx.x;
+  const EnvDesc ed = d.env[e];
+  const int n = ed.side * ed.side;
+  int cnt = 0;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) cnt += (d.cellf[ed.cell_off + c] & CELL_FOOD) ? 1 : 0;
+  int total;
+  block_exclusive_scan(cnt, &total, sh);
+  for (int k = threadIdx.x; k < N_ST; k += blockDim.x) {
+    long long v = 0;
+    if (k == ST_ALIVE) v = ed.init_alive;
+    else if (k == ST_FOOD_TOTAL) v = total;
+    else if (k == ST_ENERGY_TOTAL) v = (long long)ed.init_alive * R.e_init;
+    d.stats_total[e * N_ST + k] = v;
+    d.stats_last[e * N_ST + k] = v;
+    d.stats_step[e * N_ST + k] = 0;
+  }
+  if (threadIdx.x == 0) {
+    d.birth_contenders[e] = 0;
+    d.place_prefix[e] = 0ull;
+    d.place_remaining[e] = ed.init_alive;
+  }
+}
+
+__global__ void k_init_static(Dev d) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.total_slots; s += gridDim.x * blockDim.x) {
+    int e = 0;
+    while (e + 1 < d.n_envs && d.env[e + 1].slot_off <= s) ++e;
+    d.env_of[s] = (uint16_t)e;
+  }
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.total_cells; c += gridDim.x * blockDim.x)
+    d.occ[c] = -1;
+}
+
+// One CTA per environment: alive count, food count and energy sum of the
+// current state become the "now" statistics; the step counter is copied.
+__global__ void __launch_bounds__(1024) k_recount(Dev d) {
+  __shared__ int sh[33];
+  const int e = blockIdx.x;
+  const EnvDesc ed = d.env[e];
+  const int n = ed.side * ed.side;
+  int food = 0, alive = 0, energy = 0;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) food += (d.cellf[ed.cell_off + c] & CELL_FOOD) ? 1 : 0;
+  for (int s = threadIdx.x; s < ed.n_slots; s += blockDim.x) {
+    const int g = ed.slot_off + s;
+    if (d.alive[g]) {
+      ++alive;
+      energy += d.energy[g];
+    }
+  }
+  int ft, at, et;
+  block_exclusive_scan(food, &ft, sh);
+  block_exclusive_scan(alive, &at, sh);
+  block_exclusive_scan(energy, &et, sh);
+  if (threadIdx.x == 0) {
+    const long long t = d.step[0];
+    long long *tot = d.stats_total + e * N_ST, *last = d.stats_last + e * N_ST;
+    tot[ST_ALIVE] = last[ST_ALIVE] = at;
+    tot[ST_FOOD_TOTAL] = last[ST_FOOD_TOTAL] = ft;
+    tot[ST_ENERGY_TOTAL] = last[ST_ENERGY_TOTAL] = et;
+    tot[ST_STEP] = last[ST_STEP] = t;
+  }
+}
+
+cudaError_t launch_init_static(const Dev &d, const EnvGrid &g, cudaStream_t s) {
+  const long long n = d.total_slots > d.total_cells ? d.total_slots : d.total_cells;
+  k_init_static<<<grid_for(n, 256, g.sms * 16), 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recount(const Dev &d, const Rules &R, cudaStream_t s) {
+  (void)R;
+  k_recount<<<d.n_envs, 1024, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_requant(const Dev &d, const Layout &L, const Rules &R, int slot0, int n,
+                           cudaStream_t s) {
+  if (R.precision == PREC_FP32 || n <= 0) return cudaSuccess;
+  if (R.precision == PREC_BF16) {
+    const long long work = (long long)n * (L.D * L.H + L.H * L.H + L.A * L.H + 2 * L.H + L.A);
+    k_requant_bf16<<<grid_for(work, 256, 152 * 32), 256, 0, s>>>(d, L, slot0, n);
+  } else {
+    const long long work = (long long)n * (2 * L.H + L.A) * 32;
+    k_requant_fp8<<<grid_for(work, 256, 152 * 32), 256, 0, s>>>(d, L, slot0, n);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset(const Dev &d, const Layout &L, const Rules &R, const EnvGrid &g,
+                         cudaStream_t s) {
+  cudaError_t err;
+  const int T = 256;
+  const int cb = grid_for(d.total_cells, T, g.sms * 16);
+  const int sb = grid_for(d.total_slots, T, g.sms * 16);
+  if ((err = cudaMemsetAsync(d.counters, 0, sizeof(int32_t) * CNT_N, s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(d.step, 0, sizeof(long long), s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(d.hist, 0, sizeof(uint32_t) * 65536 * (size_t)d.n_envs, s)) != cudaSuccess)
+    return err;
+  k_init_cells<<<cb, T, 0, s>>>(d, R);
+  k_init_agents<<<sb, T, 0, s>>>(d, R);
+  k_init_stats<<<d.n_envs, 1024, 0, s>>>(d, R);  // also zeroes the placement prefix
+  for (int round = 0; round < 4; ++round) {
+    const int shift = 48 - 16 * round;
+    k_place_hist<<<cb, T, 0, s>>>(d, shift);
+    k_place_find<<<d.n_envs, 1024, 0, s>>>(d);
+  }
+  k_place_assign<<<d.n_envs, 1024, 0, s>>>(d);
+  const long long pw = (long long)d.total_slots * (L.mstride / 4);
+  k_init_params<<<grid_for(pw, T, g.sms * 64), T, 0, s>>>(d, L);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  return launch_requant(d, L, R, 0, d.total_slots, s);
+}
+
+}  // namespace eco

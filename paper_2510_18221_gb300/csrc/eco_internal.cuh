@@ -1,0 +1,325 @@
+// eco_internal.cuh -- device-side data layout and helpers shared by the
+// library's translation units (not part of the C-ABI).
+//
+// Layout in HBM (one workspace, carved at create):
+//   per cell (all environments concatenated): cellf u8 (bit0 food, bit1
+//     wall, bit2 agent), occ i32 (global slot or -1), claim_move u64,
+//     cnt_move u32, claim_birth u64;
+//   per slot (all environments concatenated): alive u8, pos i32 (env-local
+//     cell y*L+x), facing u8, energy i32, parent i32 (env-local), birth i32,
+//     act u8, env u16, tgt i32, gain i32, claim_att u64, logits f32[A];
+//   weights: FP32 masters [slot][mstride] and, for BF16/FP8, the streamed
+//     copy [slot][stride], both in the kernel's tiled block layout below.
+//
+// Block layout of one agent's parameters (Sec. 3.3 MLP D -> H -> H -> A),
+// element size es (4 FP32, 2 BF16, 1 FP8), E = 16 / es elements per 16-byte
+// unit:
+//   W1: D x H elements, input-major: element (j, o) at j*H + o.  A 16-byte
+//       unit holds E consecutive outputs o of one input j, so one warp load
+//       of 32 units is 512 contiguous bytes and each lane keeps a fixed
+//       group of E outputs.
+//   W2: H x H elements, input-major, the same way.
+//   W3: A x H elements, output-major: element (a, j) at a*H + j.
+//   [FP8 only] row scales: s1[H], s2[H], s3[A] (FP32), padded to 16 bytes.
+//   biases: b1[H], b2[H], b3[A] (FP32), padded to 16 bytes.
+//   The block stride is padded to 128 bytes (whole cache lines).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace eco {
+
+enum : uint32_t {
+  CELL_FOOD = 1u,
+  CELL_WALL = 2u,
+  CELL_AGENT = 4u,
+};
+
+enum : uint32_t {
+  S_WALL = 1,
+  S_FOOD_INIT = 2,
+  S_PLACE = 3,
+  S_FACING_INIT = 4,
+  S_W_INIT = 5,
+  S_SAMPLE = 6,
+  S_CLAIM_MOVE = 7,
+  S_CLAIM_ATTACK = 8,
+  S_CLAIM_BIRTH = 9,
+  S_MUTATE = 10,
+  S_REGROW = 11,
+};
+
+enum : int {
+  ACT_STAY = 0,
+  ACT_N = 1,
+  ACT_S = 2,
+  ACT_E = 3,
+  ACT_W = 4,
+  ACT_ATTACK = 5,
+  ACT_LEFT = 6,
+  ACT_RIGHT = 7,
+  ACT_EAT = 8,
+};
+
+enum : int {
+  PREC_FP32 = 0,
+  PREC_BF16 = 1,
+  PREC_FP8 = 2,
+};
+
+enum : int {
+  F_AUTO_EAT = 1,
+  F_ROTATE_OBS = 2,
+  F_CANCEL_ALL = 4,
+  F_GREEDY = 8,
+};
+
+// Statistic indices (same meaning and order as the public enum).
+enum : int {
+  ST_STEP = 0,
+  ST_AGENT_STEPS,
+  ST_ACT0,
+  ST_MOVES = ST_ACT0 + 16,
+  ST_MOVE_BLOCKED,
+  ST_MOVE_LOST,
+  ST_EATEN,
+  ST_ATTACKS,
+  ST_ATTACK_HITS,
+  ST_ENERGY_TRANSFERRED,
+  ST_DEATHS,
+  ST_DEAD_ENERGY,
+  ST_BIRTHS,
+  ST_FAILED_BIRTHS,
+  ST_REGROWN,
+  ST_ALIVE,
+  ST_FOOD_TOTAL,
+  ST_ENERGY_TOTAL,
+  N_ST
+};
+
+struct EnvDesc {
+  int32_t side;
+  int32_t slot_off;   // first global slot of the environment
+  int32_t n_slots;
+  int32_t cell_off;   // first global cell of the environment
+  int32_t init_alive;
+  uint32_t seed;
+};
+
+struct Layout {
+  int D, H, A, P;     // observation size, hidden, actions, parameter count
+  int es;             // bytes per streamed weight element
+  int64_t stride;     // bytes per slot, streamed copy
+  int off_w1, off_w2, off_w3, off_scale, off_bias;  // byte offsets, streamed
+  int64_t mstride;    // bytes per slot, FP32 masters
+  int moff_w1, moff_w2, moff_w3, moff_bias;          // byte offsets, masters
+};
+
+struct Rules {
+  int patch_k, n_scalars, flags, precision;
+  float sigma;
+  uint32_t thr_food, thr_regrow, thr_wall;
+  int e_init, e_metab, e_food, e_repro, attack_num, attack_den;
+};
+
+// Device pointers (all inside the caller's workspace).
+struct Dev {
+  const EnvDesc *env;   // [n_envs]
+  int n_envs;
+  int total_slots;
+  int total_cells;
+  uint8_t *cellf;
+  int32_t *occ;
+  unsigned long long *claim_move;
+  uint32_t *cnt_move;
+  unsigned long long *claim_birth;
+  uint8_t *alive;
+  int32_t *pos;
+  uint8_t *facing;
+  int32_t *energy;
+  int32_t *parent;
+  int32_t *birth;
+  uint8_t *act;
+  uint16_t *env_of;
+  int32_t *tgt;
+  int32_t *gain;
+  unsigned long long *claim_att;
+  float *logits;
+  int32_t *alive_list;
+  int32_t *counters;    // [0] n_alive, [1] n_births, [2] status, [3..] spare
+  int2 *births;         // (parent global, child global)
+  int32_t *free_list;   // per env: slot_off + rank
+  int32_t *birth_contenders;  // [n_envs]
+  long long *stats_step;   // [n_envs][N_ST] this step
+  long long *stats_total;  // [n_envs][N_ST]
+  long long *stats_last;   // [n_envs][N_ST]
+  long long *step;         // [1] current step t (all environments)
+  float *master;           // [total_slots][mstride / 4]
+  uint8_t *wq;             // [total_slots][stride] streamed copy (or == master)
+  uint32_t *hist;          // [n_envs][65536] placement radix select
+  unsigned long long *place_prefix;  // [n_envs] (prefix, remaining)
+  int32_t *place_remaining; // [n_envs] placement radix select
+  uint8_t *bflag;          // [total_slots] birth pass flags
+};
+
+enum : int {
+  CNT_N_ALIVE = 0,
+  CNT_N_BIRTHS = 1,
+  CNT_STATUS = 2,
+  CNT_N = 8,
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Ten rounds; each round
+// multiplies words 0 and 2 by the two round constants, forms the new words
+// from the high/low halves xor the other words and the key, then bumps the
+// key by the Weyl constants.
+// ---------------------------------------------------------------------------
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t a0 = 0xD2511F53u * c0;
+    const uint32_t h0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t a2 = 0xCD9E8D57u * c2;
+    const uint32_t h2 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = h2 ^ c1 ^ k0;
+    const uint32_t n2 = h0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = a2;
+    c2 = n2;
+    c3 = a0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ uint32_t word_of(const U4 &r, int i) {
+  return i == 0 ? r.x : (i == 1 ? r.y : (i == 2 ? r.z : r.w));
+}
+
+// Uniform in (0,1): ((r >> 8) | 1) * 2^-24, exact in binary32.
+__device__ __forceinline__ float uniform01(uint32_t r) {
+  return __uint2float_rn((r >> 8) | 1u) * 5.9604644775390625e-8f;
+}
+
+// Standard normal number i (0..3) of a Philox block by Box-Muller on the
+// pairs (u0,u1) and (u2,u3).  Uses the CUDA math library's logf, sqrtf and
+// sincospif.
+__device__ __forceinline__ float normal_of(const U4 &r, int i) {
+  const float ua = uniform01(i < 2 ? r.x : r.z);
+  const float ub = uniform01(i < 2 ? r.y : r.w);
+  const float rad = sqrtf(-2.0f * logf(ua));
+  float s, c;
+  sincospif(2.0f * ub, &s, &c);
+  return rad * ((i & 1) ? s : c);
+}
+
+// All four normals of a block.
+__device__ __forceinline__ void normals4(const U4 &r, float n[4]) {
+  const float u0 = uniform01(r.x), u1 = uniform01(r.y);
+  const float u2 = uniform01(r.z), u3 = uniform01(r.w);
+  const float ra = sqrtf(-2.0f * logf(u0));
+  const float rb = sqrtf(-2.0f * logf(u2));
+  float s0, c0, s1, c1;
+  sincospif(2.0f * u1, &s0, &c0);
+  sincospif(2.0f * u3, &s1, &c1);
+  n[0] = ra * c0;
+  n[1] = ra * s0;
+  n[2] = rb * c1;
+  n[3] = rb * s1;
+}
+
+// Direction vectors N E S W.
+__device__ __forceinline__ int dir_dx(int d) { return d == 1 ? 1 : (d == 3 ? -1 : 0); }
+__device__ __forceinline__ int dir_dy(int d) { return d == 0 ? -1 : (d == 2 ? 1 : 0); }
+
+__device__ __forceinline__ int wrapi(int v, int L) {
+  v %= L;
+  return v < 0 ? v + L : v;
+}
+
+// Env-local cell one step from local cell c in direction d.
+__device__ __forceinline__ int step_cell(int c, int d, int L) {
+  const int x = c % L, y = c / L;
+  return wrapi(y + dir_dy(d), L) * L + wrapi(x + dir_dx(d), L);
+}
+
+// Claim key: the larger wins; the draw first, then the lower env-local slot.
+__device__ __forceinline__ unsigned long long claim_key(uint32_t draw, int local_slot) {
+  return ((unsigned long long)draw << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)local_slot);
+}
+
+__device__ __forceinline__ int claim_local_slot(unsigned long long key) {
+  return (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
+}
+
+// Warp-aggregated add of v to stats[env][idx]: lanes with the same
+// (env, idx) combine before one 64-bit atomic.  Integer adds commute, so
+// totals do not depend on thread order.  The per-warp partial sum must fit
+// in 32 bits (every counter here does).
+__device__ __forceinline__ void stat_add(long long *stats, int env, int idx, int v) {
+  const unsigned active = __activemask();
+  const int key = env * N_ST + idx;
+  const unsigned peers = __match_any_sync(active, key);
+  const int tot = __reduce_add_sync(peers, v);
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1 && tot != 0)
+    atomicAdd((unsigned long long *)&stats[key], (unsigned long long)(long long)tot);
+}
+
+// Find the environment of a global cell (environments are sorted by cell
+// offset; a short binary search).
+__device__ __forceinline__ int env_of_cell(const EnvDesc *env, int n_envs, int cell) {
+  int lo = 0, hi = n_envs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (env[mid].cell_off <= cell)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan of one int per thread (blockDim.x multiple of 32).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int block_exclusive_scan(int v, int *total, int *sh /* >= 33 ints */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int o = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+    if (lane >= off) incl += o;
+  }
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < nwarps ? sh[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int o = __shfl_up_sync(0xFFFFFFFFu, wi, off);
+      if (lane >= off) wi += o;
+    }
+    if (lane < nwarps) sh[lane] = wi - w;
+    if (lane == 31) sh[32] = wi;
+  }
+  __syncthreads();
+  const int excl = sh[warp] + incl - v;
+  *total = sh[32];
+  __syncthreads();
+  return excl;
+}
+
+// Launch helpers (host).
+int grid_for(long long n, int threads, int max_blocks);
+
+}  // namespace eco

@@ -1,0 +1,44 @@
+// eco_kernels.h -- host-side launchers of the library's kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "eco_internal.cuh"
+
+namespace eco {
+
+// Policy phase (eco_policy.cu).
+struct PolicyLaunch {
+  void *fn;
+  int threads, blocks;
+  size_t smem;
+  int xs_floats;
+};
+int policy_variant_count();
+const char *policy_variant_name(int k);
+cudaError_t policy_prepare(const Layout &L, const Rules &R, int variant, PolicyLaunch *pl);
+cudaError_t policy_launch(const PolicyLaunch &pl, const Dev &d, const Layout &L, const Rules &R,
+                          cudaStream_t s);
+
+// Environment phases (eco_env.cu).
+struct EnvGrid {
+  int sms;          // SM count
+  int slot_blocks;  // blocks of 256 threads for per-agent phases
+  int cell_blocks;  // blocks of 256 threads for per-cell phases
+  int birth_blocks; // CTAs of the mutation kernel
+};
+cudaError_t launch_compact(const Dev &d, cudaStream_t s);
+cudaError_t launch_env_phases(const Dev &d, const Layout &L, const Rules &R, const EnvGrid &g,
+                              cudaStream_t s);
+
+// Reset and parameter maintenance (eco_init.cu).
+cudaError_t launch_reset(const Dev &d, const Layout &L, const Rules &R, const EnvGrid &g,
+                         cudaStream_t s);
+// Static per-slot tables (environment of every slot) at create.
+cudaError_t launch_init_static(const Dev &d, const EnvGrid &g, cudaStream_t s);
+// Recompute the "now" statistics (alive, food, energy, step) from the state.
+cudaError_t launch_recount(const Dev &d, const Rules &R, cudaStream_t s);
+cudaError_t launch_requant(const Dev &d, const Layout &L, const Rules &R, int slot0, int n,
+                           cudaStream_t s);
+
+}  // namespace eco

@@ -1,0 +1,386 @@
+// eco_policy.cu -- the policy phase of the step: observation gather
+// (Sec. 3.2 "Sensors"), per-agent MLP D -> H -> H -> A with tanh hidden
+// layers (Sec. 3.3), and Gumbel-max sampling of the action (Sec. 3.3:
+// actions are sampled from a softmax over the logits).
+//
+// Every agent owns its weights, so the work is a batch of independent
+// matrix-vector products bound by HBM reads of the weights (about 57 KB per
+// agent in BF16 at 371 -> 64 -> 64 -> 9), not a dense contraction: tensor
+// cores do not apply.  The kernel is warp-per-agent:
+//   * the warp gathers the agent's k x k x 3 patch and scalars into its own
+//     shared-memory row (one byte per cell: food / wall / agent bits);
+//   * each lane streams 16-byte units of the agent's weight block with
+//     non-allocating loads, UNROLL units in flight per lane; a warp load is
+//     512 contiguous bytes;
+//   * in the input-major layout a lane's units always hold the same group of
+//     E outputs, so the lane accumulates E partial sums in FP32 and a
+//     butterfly over lanes with the same group finishes each output;
+//   * the head (A rows, output-major) reduces over small lane groups, and a
+//     warp argmax of logit + Gumbel picks the action (ties to the lowest
+//     action index).
+// All floating-point reductions run in a fixed order, so results are
+// bit-reproducible from run to run.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "eco_internal.cuh"
+#include "eco_kernels.h"
+
+namespace eco {
+
+__device__ __forceinline__ uint4 ldg_stream(const uint4 *p) {
+  uint4 r;
+  asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p));
+  return r;
+}
+
+template <int PREC>
+struct Unit;
+
+template <>
+struct Unit<PREC_FP32> {
+  static constexpr int E = 4;
+  __device__ __forceinline__ static void fma(float *acc, const uint4 &v, float x) {
+    acc[0] = fmaf(__uint_as_float(v.x), x, acc[0]);
+    acc[1] = fmaf(__uint_as_float(v.y), x, acc[1]);
+    acc[2] = fmaf(__uint_as_float(v.z), x, acc[2]);
+    acc[3] = fmaf(__uint_as_float(v.w), x, acc[3]);
+  }
+  __device__ __forceinline__ static float dot(const uint4 &v, const float *h) {
+    const float4 a = *reinterpret_cast<const float4 *>(h);
+    float s = __uint_as_float(v.x) * a.x;
+    s = fmaf(__uint_as_float(v.y), a.y, s);
+    s = fmaf(__uint_as_float(v.z), a.z, s);
+    s = fmaf(__uint_as_float(v.w), a.w, s);
+    return s;
+  }
+};
+
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+template <>
+struct Unit<PREC_BF16> {
+  static constexpr int E = 8;
+  __device__ __forceinline__ static void fma(float *acc, const uint4 &v, float x) {
+    acc[0] = fmaf(bf_lo(v.x), x, acc[0]);
+    acc[1] = fmaf(bf_hi(v.x), x, acc[1]);
+    acc[2] = fmaf(bf_lo(v.y), x, acc[2]);
+    acc[3] = fmaf(bf_hi(v.y), x, acc[3]);
+    acc[4] = fmaf(bf_lo(v.z), x, acc[4]);
+    acc[5] = fmaf(bf_hi(v.z), x, acc[5]);
+    acc[6] = fmaf(bf_lo(v.w), x, acc[6]);
+    acc[7] = fmaf(bf_hi(v.w), x, acc[7]);
+  }
+  __device__ __forceinline__ static float dot(const uint4 &v, const float *h) {
+    const float4 a = *reinterpret_cast<const float4 *>(h);
+    const float4 b = *reinterpret_cast<const float4 *>(h + 4);
+    float s = bf_lo(v.x) * a.x;
+    s = fmaf(bf_hi(v.x), a.y, s);
+    s = fmaf(bf_lo(v.y), a.z, s);
+    s = fmaf(bf_hi(v.y), a.w, s);
+    s = fmaf(bf_lo(v.z), b.x, s);
+    s = fmaf(bf_hi(v.z), b.y, s);
+    s = fmaf(bf_lo(v.w), b.z, s);
+    s = fmaf(bf_hi(v.w), b.w, s);
+    return s;
+  }
+};
+
+// Two e4m3 codes (low byte = first element) to two floats, exactly.
+__device__ __forceinline__ float2 e4m3x2(uint32_t two) {
+  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(two & 0xFFFFu), __NV_E4M3);
+  return __half22float2(*reinterpret_cast<const __half2 *>(&h));
+}
+
+template <>
+struct Unit<PREC_FP8> {
+  static constexpr int E = 16;
+  __device__ __forceinline__ static void fma4(float *acc, uint32_t w, float x) {
+    const float2 a = e4m3x2(w), b = e4m3x2(w >> 16);
+    acc[0] = fmaf(a.x, x, acc[0]);
+    acc[1] = fmaf(a.y, x, acc[1]);
+    acc[2] = fmaf(b.x, x, acc[2]);
+    acc[3] = fmaf(b.y, x, acc[3]);
+  }
+  __device__ __forceinline__ static void fma(float *acc, const uint4 &v, float x) {
+    fma4(acc + 0, v.x, x);
+    fma4(acc + 4, v.y, x);
+    fma4(acc + 8, v.z, x);
+    fma4(acc + 12, v.w, x);
+  }
+  __device__ __forceinline__ static float dot4(uint32_t w, const float *h, float s) {
+    const float2 a = e4m3x2(w), b = e4m3x2(w >> 16);
+    const float4 x = *reinterpret_cast<const float4 *>(h);
+    s = fmaf(a.x, x.x, s);
+    s = fmaf(a.y, x.y, s);
+    s = fmaf(b.x, x.z, s);
+    s = fmaf(b.y, x.w, s);
+    return s;
+  }
+  __device__ __forceinline__ static float dot(const uint4 &v, const float *h) {
+    float s = 0.0f;
+    s = dot4(v.x, h, s);
+    s = dot4(v.y, h + 4, s);
+    s = dot4(v.z, h + 8, s);
+    s = dot4(v.w, h + 12, s);
+    return s;
+  }
+};
+
+template <int N>
+struct Log2 {
+  static constexpr int v = 1 + Log2<N / 2>::v;
+};
+template <>
+struct Log2<1> {
+  static constexpr int v = 0;
+};
+
+// One input-major layer: out[o] = tanh(s_o * sum_j W[j][o] x[j] + b_o) for
+// o in [0, H), written to shared memory by lanes 0 .. H/E - 1.
+template <int PREC, int H, int UNROLL>
+__device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int n_in,
+                                               const float *__restrict__ x,
+                                               const float *__restrict__ bias,
+                                               const float *__restrict__ scale,
+                                               float *__restrict__ out, int lane) {
+  constexpr int E = Unit<PREC>::E;
+  constexpr int UPJ = H / E;  // units per input
+  constexpr int LG = Log2<UPJ>::v;
+  static_assert((1 << LG) == UPJ && UPJ <= 32, "H / E must be a power of two <= 32");
+  float acc[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) acc[e] = 0.0f;
+  const int U = n_in * UPJ;
+  int u = lane;
+  for (; u + 32 * (UNROLL - 1) < U; u += 32 * UNROLL) {
+    uint4 v[UNROLL];
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) v[k] = ldg_stream(w + u + 32 * k);
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) Unit<PREC>::fma(acc, v[k], x[(u + 32 * k) >> LG]);
+  }
+  for (; u < U; u += 32) {
+    const uint4 v = ldg_stream(w + u);
+    Unit<PREC>::fma(acc, v, x[u >> LG]);
+  }
+#pragma unroll
+  for (int off = UPJ; off < 32; off <<= 1) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[e] += __shfl_xor_sync(0xFFFFFFFFu, acc[e], off);
+  }
+  if (lane < UPJ) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int o = lane * E + e;
+      const float s = (PREC == PREC_FP8) ? __ldg(scale + o) : 1.0f;
+      out[o] = tanhf(fmaf(acc[e], s, __ldg(bias + o)));
+    }
+  }
+}
+
+template <int PREC, int H, int WARPS, int UNROLL>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_policy(Dev d, Layout L, Rules R, int xs_floats) {
+  constexpr int E = Unit<PREC>::E;
+  constexpr int UPJ = H / E;
+  constexpr int LG = Log2<UPJ>::v;
+  extern __shared__ __align__(16) float smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  float *xs = smem + warp * (xs_floats + H + 16);
+  float *hs = xs + xs_floats;
+  float *ls = hs + H;
+
+  const int n_alive = d.counters[CNT_N_ALIVE];
+  const uint32_t t = (uint32_t)d.step[0];
+  const int k = R.patch_k, RR = k >> 1, kk = k * k;
+  const bool rotate = (R.flags & F_ROTATE_OBS) != 0;
+  const bool greedy = (R.flags & F_GREEDY) != 0;
+
+  for (int i = blockIdx.x * WARPS + warp; i < n_alive; i += gridDim.x * WARPS) {
+    const int slot = d.alive_list[i];
+    const EnvDesc ed = d.env[d.env_of[slot]];
+    const int side = ed.side;
+    const int pos = d.pos[slot];
+    const int px = pos % side, py = pos / side;
+    const int f = d.facing[slot];
+    const int rt = (f + 1) & 3;
+    const uint8_t *cellf = d.cellf + ed.cell_off;
+
+    // -- observation: k x k x 3 patch (row, column, channel), then scalars
+    for (int c = lane; c < kk; c += 32) {
+      const int r = c / k, col = c - r * k;
+      int dx, dy;
+      if (rotate) {
+        const int fw = RR - r, ri = col - RR;
+        dx = fw * dir_dx(f) + ri * dir_dx(rt);
+        dy = fw * dir_dy(f) + ri * dir_dy(rt);
+      } else {
+        dx = col - RR;
+        dy = r - RR;
+      }
+      const int cx = wrapi(px + dx, side), cy = wrapi(py + dy, side);
+      const uint32_t cf = cellf[cy * side + cx];
+      xs[3 * c + 0] = (cf & CELL_FOOD) ? 1.0f : 0.0f;
+      xs[3 * c + 1] = (cf & CELL_AGENT) ? 1.0f : 0.0f;
+      xs[3 * c + 2] = (cf & CELL_WALL) ? 1.0f : 0.0f;
+    }
+    if (lane < R.n_scalars) {
+      float v = 0.0f;
+      if (lane == 0)
+        v = (float)d.energy[slot] / (float)R.e_repro;
+      else if (R.n_scalars >= 8 && lane == 1 + f)
+        v = 1.0f;
+      xs[3 * kk + lane] = v;
+    }
+    __syncwarp();
+
+    const uint8_t *blk = d.wq + (int64_t)slot * L.stride;
+    const uint4 *wb = reinterpret_cast<const uint4 *>(blk);
+    const float *bias = reinterpret_cast<const float *>(blk + L.off_bias);
+    const float *scale = reinterpret_cast<const float *>(blk + L.off_scale);
+
+    // -- layer 1: h1 = tanh(W1 x + b1) -> hs
+    layer_in_major<PREC, H, UNROLL>(wb + L.off_w1 / 16, L.D, xs, bias, scale, hs, lane);
+    __syncwarp();
+    // -- layer 2: h2 = tanh(W2 h1 + b2) -> xs
+    layer_in_major<PREC, H, UNROLL>(wb + L.off_w2 / 16, H, hs, bias + H, scale + H, xs, lane);
+    __syncwarp();
+
+    // -- head: logits = W3 h2 + b3 (output-major rows of H / E units)
+    const uint4 *w3 = wb + L.off_w3 / 16;
+    const int U3 = L.A * UPJ;
+    for (int base = 0; base < U3; base += 32) {
+      const int u = base + lane;
+      float part = 0.0f;
+      if (u < U3) part = Unit<PREC>::dot(ldg_stream(w3 + u), xs + (u & (UPJ - 1)) * E);
+#pragma unroll
+      for (int off = 1; off < UPJ; off <<= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, off);
+      if (u < U3 && (lane & (UPJ - 1)) == 0) {
+        const int a = u >> LG;
+        const float s = (PREC == PREC_FP8) ? __ldg(scale + 2 * H + a) : 1.0f;
+        ls[a] = fmaf(part, s, __ldg(bias + 2 * H + a));
+      }
+    }
+    __syncwarp();
+
+    // -- sample: argmax_a (logit_a + Gumbel_a), ties to the lowest a
+    float score = -INFINITY;
+    int best = lane;
+    if (lane < L.A) {
+      const float lg = ls[lane];
+      d.logits[(int64_t)slot * L.A + lane] = lg;
+      score = lg;
+      if (!greedy) {
+        const U4 r = philox(t, (uint32_t)(slot - ed.slot_off), (uint32_t)(lane >> 2), 0u, ed.seed,
+                            S_SAMPLE);
+        const float u = uniform01(word_of(r, lane & 3));
+        score = lg + (-logf(-logf(u)));
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float os = __shfl_xor_sync(0xFFFFFFFFu, score, off);
+      const int oa = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+      if (os > score || (os == score && oa < best)) {
+        score = os;
+        best = oa;
+      }
+    }
+    if (lane == 0) d.act[slot] = (uint8_t)best;
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Variants and launch
+// ---------------------------------------------------------------------------
+
+typedef void (*PolicyFn)(Dev, Layout, Rules, int);
+
+struct VariantDesc {
+  const char *name;
+  int warps, unroll;
+};
+
+static const VariantDesc kVariants[] = {
+    {"warp-per-agent, 4 warps/CTA, 8 units in flight per lane", 4, 8},
+    {"warp-per-agent, 8 warps/CTA, 8 units in flight per lane", 8, 8},
+    {"warp-per-agent, 8 warps/CTA, 4 units in flight per lane", 8, 4},
+    {"warp-per-agent, 16 warps/CTA, 4 units in flight per lane", 16, 4},
+};
+static const int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+int policy_variant_count() { return kNumVariants; }
+const char *policy_variant_name(int k) {
+  if (k < 1 || k > kNumVariants) return "invalid";
+  return kVariants[k - 1].name;
+}
+
+template <int PREC, int H>
+static PolicyFn pick_fn(int variant) {
+  switch (variant) {
+    case 1: return k_policy<PREC, H, 4, 8>;
+    case 2: return k_policy<PREC, H, 8, 8>;
+    case 3: return k_policy<PREC, H, 8, 4>;
+    default: return k_policy<PREC, H, 16, 4>;
+  }
+}
+
+static PolicyFn pick(int prec, int H, int variant) {
+  if (prec == PREC_FP32) {
+    if (H == 32) return pick_fn<PREC_FP32, 32>(variant);
+    if (H == 64) return pick_fn<PREC_FP32, 64>(variant);
+    if (H == 128) return pick_fn<PREC_FP32, 128>(variant);
+  } else if (prec == PREC_BF16) {
+    if (H == 32) return pick_fn<PREC_BF16, 32>(variant);
+    if (H == 64) return pick_fn<PREC_BF16, 64>(variant);
+    if (H == 128) return pick_fn<PREC_BF16, 128>(variant);
+  } else {
+    if (H == 32) return pick_fn<PREC_FP8, 32>(variant);
+    if (H == 64) return pick_fn<PREC_FP8, 64>(variant);
+    if (H == 128) return pick_fn<PREC_FP8, 128>(variant);
+  }
+  return nullptr;
+}
+
+int policy_xs_floats(const Layout &L) { return (L.D + 3) & ~3; }
+
+cudaError_t policy_prepare(const Layout &L, const Rules &R, int variant, PolicyLaunch *pl) {
+  PolicyFn fn = pick(R.precision, L.H, variant);
+  if (!fn) return cudaErrorInvalidValue;
+  const int warps = kVariants[variant - 1].warps;
+  const int xs = policy_xs_floats(L);
+  const size_t smem = (size_t)warps * (xs + L.H + 16) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, warps * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  pl->fn = (void *)fn;
+  pl->threads = warps * 32;
+  pl->blocks = sms * per_sm;  // one full wave of resident CTAs on every SM
+  pl->smem = smem;
+  pl->xs_floats = xs;
+  return cudaSuccess;
+}
+
+cudaError_t policy_launch(const PolicyLaunch &pl, const Dev &d, const Layout &L, const Rules &R,
+                          cudaStream_t s) {
+  PolicyFn fn = (PolicyFn)pl.fn;
+  fn<<<pl.blocks, pl.threads, pl.smem, s>>>(d, L, R, pl.xs_floats);
+  return cudaGetLastError();
+}
+
+}  // namespace eco
