@@ -45,6 +45,7 @@ struct eco_handle {
   PolicyLaunch pl;
   // step graph
   cudaGraphExec_t graph;
+  cudaGraph_t graph_src;  // kept alive: its node handles address the exec's nodes
   cudaGraphNode_t ev_node[2];
   cudaEvent_t ev_dummy[2];
   std::vector<cudaEvent_t> ev_pool;  // pairs
@@ -226,7 +227,9 @@ extern "C" int eco_workspace_bytes(const eco_config *cfg, size_t *bytes) {
 
 static void destroy_graph(eco_handle *h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->graph_src) cudaGraphDestroy(h->graph_src);
   h->graph = nullptr;
+  h->graph_src = nullptr;
 }
 
 extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t bytes, void *stream,
@@ -298,11 +301,14 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
   h->forced = cfg->policy_variant;
   h->variant = 0;
   h->graph = nullptr;
+  h->graph_src = nullptr;
   h->ev_used = 0;
   h->err[0] = 0;
-  cudaError_t e = cudaMemcpyAsync(h->env_dev, h->env_host.data(), sizeof(EnvDesc) * h->n_envs,
-                                  cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws, 0, need, h->stream);
+  // zero the whole workspace first, then install the environment table
+  cudaError_t e = cudaMemsetAsync(h->ws, 0, need, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->env_dev, h->env_host.data(), sizeof(EnvDesc) * h->n_envs,
+                        cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = launch_init_static(h->d, h->grid, h->stream);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[1]);
@@ -391,9 +397,10 @@ static int autotune(eco_handle *h) {
 
 static cudaError_t enqueue_step(eco_handle *h) {
   cudaError_t e = launch_compact(h->d, h->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(h->ev_dummy[0], h->stream);
+  // "external" records become event-record nodes of the captured graph
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(h->ev_dummy[0], h->stream, cudaEventRecordExternal);
   if (e == cudaSuccess) e = policy_launch(h->pl, h->d, h->L, h->R, h->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(h->ev_dummy[1], h->stream);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(h->ev_dummy[1], h->stream, cudaEventRecordExternal);
   if (e == cudaSuccess) e = launch_env_phases(h->d, h->L, h->R, h->grid, h->stream);
   return e;
 }
@@ -429,8 +436,12 @@ static int build_graph(eco_handle *h) {
     return fail(h, ECO_ECUDA, "step graph: event nodes not found");
   }
   cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
-  cudaGraphDestroy(g);
-  if (ie != cudaSuccess) return fail(h, ECO_ECUDA, "instantiate: %s", cudaGetErrorString(ie));
+  if (ie != cudaSuccess) {
+    cudaGraphDestroy(g);
+    h->graph = nullptr;
+    return fail(h, ECO_ECUDA, "instantiate: %s", cudaGetErrorString(ie));
+  }
+  h->graph_src = g;
   return ECO_OK;
 }
 

@@ -58,10 +58,12 @@ def get(name: str, **overrides) -> dict:
     return w
 
 
-def scaled(name: str, side: int, slots: int, init_alive: int, **overrides) -> dict:
+def scaled(base: str, side: int, slots: int, init_alive: int, **overrides) -> dict:
     """A named workload's rules and MLP on a different grid / population."""
-    return get(name, side=side, slots=slots, init_alive=init_alive,
-               name="%s-%dx%d-%dslots" % (name, side, side, slots), **overrides)
+    w = get(base, side=side, slots=slots, init_alive=init_alive)
+    w["name"] = "%s-%dx%d-%dslots" % (base, side, side, slots)
+    w.update(overrides)
+    return w
 
 
 def batched(n_envs: int = 64, seed: int = 0, base_seed: int = 0,
