@@ -224,6 +224,49 @@ int eco_policy_only(eco_handle *h, int32_t n_iters);
  * biases and scales in FP32); synchronises. */
 int eco_policy_bytes(eco_handle *h, int64_t *bytes, int64_t *n_alive);
 
+/* Movement-claim resolution for one world, allocating nothing.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code running where every byte of
+ * device memory is owned by a host framework's own pool, loops that must
+ * not call cudaMalloc because it can synchronise the whole device, and
+ * callers that cannot hold a workspace for the lifetime of a handle.  It
+ * needs no handle and no workspace: its scratch (one 64-bit claim per
+ * cell) is a fixed file-scope device array of ECO_NOALLOC_MAX_CELLS
+ * entries (8 MiB), which every GPU that loads the library holds until the
+ * process exits.
+ *
+ * Rule (the movement phase of eco_step for one world): agent i at cell
+ * pos[i] (y * side + x) with action act[i] and facing facing_in[i]; a move
+ * action (1 N, 2 S, 3 E, 4 W) faces its direction and claims the
+ * neighbouring cell unless blocked[cell] is nonzero (a wall, or an agent
+ * there when the step began); among claimants of one cell the highest
+ * Philox draw of stream CLAIM_MOVE at counter (step, i, 0, 0) under key
+ * (seed, 7) wins, ties to the lower i; actions 6 / 7 turn left / right.
+ * Outputs: facing_out[i], pos_out[i] (the new cell, or pos[i]) and
+ * moved[i] (0/1).
+ *
+ * All array arguments are device pointers the caller allocates: pos,
+ * pos_out int32[n_agents]; act, facing_in, facing_out, moved
+ * uint8[n_agents]; blocked uint8[side * side].  Work is enqueued on
+ * stream (cudaStream_t or NULL) and is asynchronous.
+ * Returns ECO_EINVAL if side is odd or < 4, if side * side exceeds
+ * ECO_NOALLOC_MAX_CELLS, or for a null array with n_agents > 0;
+ * ECO_ECUDA if a CUDA call fails.  It calls no cudaMalloc / cudaFree.
+ *
+ * The first call on each device looks up the scratch array's device
+ * address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call on a device shares the
+ * one scratch array (each call clears the cells it uses before claiming),
+ * so calls whose work overlaps on the GPU -- on different streams, or from
+ * different threads -- race and give wrong results; serialise them. */
+#define ECO_NOALLOC_MAX_CELLS (1 << 20)
+int eco_move_claims_noalloc(int32_t side, int32_t n_agents, const int32_t *pos,
+                            const uint8_t *act, const uint8_t *facing_in,
+                            const uint8_t *blocked, uint32_t seed, uint32_t step,
+                            uint8_t *facing_out, int32_t *pos_out, uint8_t *moved,
+                            void *stream);
+
 /* Release the handle (not the workspace).  Accepts NULL. */
 void eco_destroy(eco_handle *h);
 

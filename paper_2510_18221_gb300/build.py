@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeco.so")
-SOURCES = ["eco_api.cu", "eco_policy.cu", "eco_env.cu", "eco_init.cu"]
+SOURCES = ["eco_api.cu", "eco_policy.cu", "eco_env.cu", "eco_init.cu", "eco_noalloc.cu"]
 HEADERS = ["eco_internal.cuh", "eco_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

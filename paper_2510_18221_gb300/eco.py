@@ -104,6 +104,9 @@ def lib() -> ctypes.CDLL:
         L.eco_policy_variant_name.restype = ctypes.c_char_p
         L.eco_policy_only.argtypes = [H, ctypes.c_int32]
         L.eco_policy_bytes.argtypes = [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        L.eco_move_claims_noalloc.argtypes = [
+            ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32,
+            _vp, _vp, _vp, _vp]
         L.eco_destroy.argtypes = [H]
         L.eco_destroy.restype = None
         L.eco_last_error.argtypes = [H]
@@ -193,6 +196,18 @@ def eco_policy_variant_name(k: int) -> str:
 
 def eco_destroy(h) -> None:
     lib().eco_destroy(h)
+
+
+def eco_move_claims_noalloc(side: int, n_agents: int, pos: int, act: int, facing_in: int,
+                            blocked: int, seed: int, step: int, facing_out: int, pos_out: int,
+                            moved: int, stream: int) -> None:
+    """Movement-claim resolution with no device allocation (all array
+    arguments are device pointers owned by the caller; see include/eco.h
+    for who needs it and its limits)."""
+    _check(lib().eco_move_claims_noalloc(
+        int(side), int(n_agents), _vp(pos), _vp(act), _vp(facing_in), _vp(blocked),
+        int(seed) & 0xFFFFFFFF, int(step) & 0xFFFFFFFF, _vp(facing_out), _vp(pos_out),
+        _vp(moved), _vp(stream)))
 
 
 # ---------------------------------------------------------------------------
