@@ -34,7 +34,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "agent-steps/sec at 65,536 agents (policy+env) and policy-kernel HBM GB/s vs peak"
 UNIT = "agent-steps/s"
-KERNELS_PER_STEP = 12  # compact, policy, 9 environment phases, finish
+# compact, policy (+ move claims), move+eat, attack claim, attack gain,
+# metabolism+death, birth claim, birth assign, mutate, regrow, finish
+KERNELS_PER_STEP = 11
 
 
 def parse():
@@ -128,12 +130,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline_sample(w, seconds, steps_cap=None):
+def cpu_baseline_sample(w, seconds, window, steps_cap=None):
     """Time the CPU oracle on a bounded sample of the workload: the same MLP,
     rules and precision on a 256x256 world with the same founder density
-    (4,096 slots, 3,125 founders)."""
+    (4,096 slots, 3,125 founders), stepping through the same post-reset
+    window (w0, w1) as the GPU measurement; the world is reset (untimed)
+    whenever the window is exhausted, until `seconds` of stepping (or
+    `steps_cap` timed steps) have been spent."""
     import oracle
-    from paper_2510_18221_gb300 import workloads
     side = 256
     scale = (side * side) / float(w["side"] * w["side"])
     founders = max(1, int(round(w["init_alive"] * scale)))
@@ -141,20 +145,28 @@ def cpu_baseline_sample(w, seconds, steps_cap=None):
     sw = dict(w, side=side, slots=slots, init_alive=founders,
               name="%s sample %dx%d %d slots" % (w["name"], side, side, slots))
     o = oracle.Oracle(sw)
-    o.reset()
-    agent_steps, n, t0 = 0, 0, time.perf_counter()
+    w0, w1 = window
+    agent_steps, n, el = 0, 0, 0.0
     while True:
-        _, st, _ = o.step_once()
-        agent_steps += st["agent_steps"]
-        n += 1
-        el = time.perf_counter() - t0
-        if (steps_cap is None and el >= seconds and n >= 2) or (steps_cap is not None and n >= steps_cap):
-            break
+        o.reset()
+        for _ in range(w0):
+            o.step_once()
+        for _ in range(w0, w1):
+            t0 = time.perf_counter()
+            _, st, _ = o.step_once()
+            el += time.perf_counter() - t0
+            agent_steps += st["agent_steps"]
+            n += 1
+            if (steps_cap is None and el >= seconds and n >= 2) or (steps_cap is not None and n >= steps_cap):
+                break
+        else:
+            continue
+        break
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": agent_steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d steps of a %dx%d world, %d slots, %d founders, MLP %d-%d-%d-%d %s "
-                      "(same rules and founder density), %.1f s" %
-                      (n, side, side, slots, founders, o.D, w["hidden"], w["hidden"],
+            "sample": "%d timed steps (within steps %d..%d after reset) of a %dx%d world, %d slots, "
+                      "%d founders, MLP %d-%d-%d-%d %s (same rules and founder density), %.1f s" %
+                      (n, w0, w1, side, side, slots, founders, o.D, w["hidden"], w["hidden"],
                        w["n_actions"], w["precision"], el)}, agent_steps, el
 
 
@@ -163,9 +175,9 @@ def run_reference(args, rank, world):
         return
     from paper_2510_18221_gb300 import workloads
     w = workloads.get(args.workload)
-    # warm-up steps then K timed steps of the oracle on the bounded sample
-    cpu_baseline_sample(w, 0, steps_cap=max(1, args.warmup))
-    rec, agent_steps, el = cpu_baseline_sample(w, 0, steps_cap=max(1, args.steps))
+    # K timed oracle steps on the bounded sample, after W untimed ones
+    window = (args.warmup, args.warmup + args.steps)
+    rec, agent_steps, el = cpu_baseline_sample(w, 0, window, steps_cap=max(1, args.steps))
     value = agent_steps / el
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -263,7 +275,7 @@ def main():
     traffic = committed_traffic(w["name"])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, _, _ = cpu_baseline_sample(w, args.cpu_seconds)
+        cpu, _, _ = cpu_baseline_sample(w, args.cpu_seconds, (args.warmup, args.warmup + args.steps))
     if rank == 0:
         line = {
             "metric": METRIC,
@@ -298,7 +310,8 @@ def main():
                 "bytes_per_agent": per_agent_bytes,
                 "policy_ms_per_step": policy_ms / max(1, n_timed),
                 "policy_share_of_step": policy_ms / ms if ms > 0 else None,
-                "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                "traffic": (traffic["dram_bytes_per_agent"] * agent_steps / max(1, args.steps * world))
+                           if traffic else None,
                 "traffic_source": traffic["source"] if traffic else None,
             },
             "e2e": {"value": e_agent_steps / e_el, "unit": UNIT, "h2d_bytes_per_step": 0,

@@ -193,6 +193,7 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.free_list = k.take<int32_t>(slots);
   D.bflag = k.take<uint8_t>(slots);
   D.birth_contenders = k.take<int32_t>(E);
+  D.contenders = k.take<int32_t>(slots);
   D.stats_step = k.take<long long>((size_t)E * N_ST);
   D.stats_total = k.take<long long>((size_t)E * N_ST);
   D.stats_last = k.take<long long>((size_t)E * N_ST);
@@ -310,6 +311,7 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
     e = cudaMemcpyAsync(h->env_dev, h->env_host.data(), sizeof(EnvDesc) * h->n_envs,
                         cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = launch_init_static(h->d, h->grid, h->stream);
+  if (e == cudaSuccess) e = env_prepare(h->L);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[1]);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -375,9 +377,9 @@ static int autotune(eco_handle *h) {
       cudaGetLastError();
       continue;
     }
-    for (int w = 0; w < 2; ++w) CUDA_TRY(h, policy_launch(pl, h->d, h->L, h->R, h->stream));
+    for (int w = 0; w < 2; ++w) CUDA_TRY(h, policy_launch(pl, h->d, h->L, h->R, h->stream, false));
     CUDA_TRY(h, cudaEventRecord(a, h->stream));
-    for (int r = 0; r < 5; ++r) CUDA_TRY(h, policy_launch(pl, h->d, h->L, h->R, h->stream));
+    for (int r = 0; r < 5; ++r) CUDA_TRY(h, policy_launch(pl, h->d, h->L, h->R, h->stream, false));
     CUDA_TRY(h, cudaEventRecord(b, h->stream));
     CUDA_TRY(h, cudaEventSynchronize(b));
     float ms = 0;
@@ -399,7 +401,7 @@ static cudaError_t enqueue_step(eco_handle *h) {
   cudaError_t e = launch_compact(h->d, h->stream);
   // "external" records become event-record nodes of the captured graph
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(h->ev_dummy[0], h->stream, cudaEventRecordExternal);
-  if (e == cudaSuccess) e = policy_launch(h->pl, h->d, h->L, h->R, h->stream);
+  if (e == cudaSuccess) e = policy_launch(h->pl, h->d, h->L, h->R, h->stream, true);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(h->ev_dummy[1], h->stream, cudaEventRecordExternal);
   if (e == cudaSuccess) e = launch_env_phases(h->d, h->L, h->R, h->grid, h->stream);
   return e;
@@ -497,7 +499,7 @@ extern "C" int eco_policy_only(eco_handle *h, int32_t n_iters) {
   int rc = autotune(h);
   if (rc) return rc;
   CUDA_TRY(h, launch_compact(h->d, h->stream));
-  for (int i = 0; i < n_iters; ++i) CUDA_TRY(h, policy_launch(h->pl, h->d, h->L, h->R, h->stream));
+  for (int i = 0; i < n_iters; ++i) CUDA_TRY(h, policy_launch(h->pl, h->d, h->L, h->R, h->stream, false));
   return ECO_OK;
 }
 

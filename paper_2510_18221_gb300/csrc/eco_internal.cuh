@@ -150,7 +150,8 @@ struct Dev {
   int32_t *counters;    // [0] n_alive, [1] n_births, [2] status, [3..] spare
   int2 *births;         // (parent global, child global)
   int32_t *free_list;   // per env: slot_off + rank
-  int32_t *birth_contenders;  // [n_envs]
+  int32_t *birth_contenders;  // [n_envs] count of this step's birth claimants
+  int32_t *contenders;        // per env: slot_off + k -> k-th claimant (global slot)
   long long *stats_step;   // [n_envs][N_ST] this step
   long long *stats_total;  // [n_envs][N_ST]
   long long *stats_last;   // [n_envs][N_ST]

@@ -17,8 +17,10 @@ struct PolicyLaunch {
 int policy_variant_count();
 const char *policy_variant_name(int k);
 cudaError_t policy_prepare(const Layout &L, const Rules &R, int variant, PolicyLaunch *pl);
+// apply_moves: also apply facing / turns and file move claims (the step);
+// false leaves the world state untouched (timing, parity of the policy).
 cudaError_t policy_launch(const PolicyLaunch &pl, const Dev &d, const Layout &L, const Rules &R,
-                          cudaStream_t s);
+                          cudaStream_t s, bool apply_moves);
 
 // Environment phases (eco_env.cu).
 struct EnvGrid {
@@ -28,6 +30,7 @@ struct EnvGrid {
   int birth_blocks; // CTAs of the mutation kernel
 };
 cudaError_t launch_compact(const Dev &d, cudaStream_t s);
+cudaError_t env_prepare(const Layout &L);
 cudaError_t launch_env_phases(const Dev &d, const Layout &L, const Rules &R, const EnvGrid &g,
                               cudaStream_t s);
 

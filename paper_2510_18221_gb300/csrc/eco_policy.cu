@@ -185,7 +185,7 @@ __device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int 
 
 template <int PREC, int H, int WARPS, int UNROLL>
 __global__ void __launch_bounds__(WARPS * 32)
-    k_policy(Dev d, Layout L, Rules R, int xs_floats) {
+    k_policy(Dev d, Layout L, Rules R, int xs_floats, int apply_moves) {
   constexpr int E = Unit<PREC>::E;
   constexpr int UPJ = H / E;
   constexpr int LG = Log2<UPJ>::v;
@@ -202,9 +202,24 @@ __global__ void __launch_bounds__(WARPS * 32)
   const bool rotate = (R.flags & F_ROTATE_OBS) != 0;
   const bool greedy = (R.flags & F_GREEDY) != 0;
 
+  // Per-warp counters, flushed when the environment changes: lane a < 16
+  // counts action a, lane 16 counts moves blocked by a wall or an agent.
+  int cnt = 0, e_cur = -1;
+  auto flush = [&]() {
+    if (e_cur >= 0 && cnt && lane <= 16)
+      atomicAdd((unsigned long long *)&d.stats_step[e_cur * N_ST + (lane < 16 ? ST_ACT0 + lane : ST_MOVE_BLOCKED)],
+                (unsigned long long)cnt);
+    cnt = 0;
+  };
+
   for (int i = blockIdx.x * WARPS + warp; i < n_alive; i += gridDim.x * WARPS) {
     const int slot = d.alive_list[i];
-    const EnvDesc ed = d.env[d.env_of[slot]];
+    const int env = d.env_of[slot];
+    if (env != e_cur) {
+      flush();
+      e_cur = env;
+    }
+    const EnvDesc ed = d.env[env];
     const int side = ed.side;
     const int pos = d.pos[slot];
     const int px = pos % side, py = pos / side;
@@ -292,16 +307,48 @@ __global__ void __launch_bounds__(WARPS * 32)
         best = oa;
       }
     }
+    if (apply_moves) {
+      // A6 (part 1), fused: facing and turns, and the move claim on a cell
+      // that is neither a wall nor occupied now, at the start of the step
+      // (no cell changes while the policy phase runs).
+      int blk = 0;
+      if (lane == 0) {
+        int nf = f, tc = -1;
+        if (best >= ACT_N && best <= ACT_W) {
+          nf = (best == ACT_N) ? 0 : (best == ACT_S) ? 2 : (best == ACT_E) ? 1 : 3;
+          const int c = step_cell(pos, nf, side);
+          if (cellf[c] & (CELL_WALL | CELL_AGENT)) {
+            blk = 1;
+          } else {
+            const int local = slot - ed.slot_off;
+            const U4 r = philox(t, (uint32_t)local, 0u, 0u, ed.seed, S_CLAIM_MOVE);
+            atomicMax(&d.claim_move[ed.cell_off + c], claim_key(r.x, local));
+            if (R.flags & F_CANCEL_ALL) atomicAdd(&d.cnt_move[ed.cell_off + c], 1u);
+            tc = c;
+          }
+        } else if (best == ACT_LEFT) {
+          nf = (f + 3) & 3;
+        } else if (best == ACT_RIGHT) {
+          nf = (f + 1) & 3;
+        }
+        d.facing[slot] = (uint8_t)nf;
+        d.tgt[slot] = tc;
+      }
+      blk = __shfl_sync(0xFFFFFFFFu, blk, 0);
+      if (lane == best) ++cnt;
+      if (lane == 16 && blk) ++cnt;
+    }
     if (lane == 0) d.act[slot] = (uint8_t)best;
     __syncwarp();
   }
+  flush();
 }
 
 // ---------------------------------------------------------------------------
 // Variants and launch
 // ---------------------------------------------------------------------------
 
-typedef void (*PolicyFn)(Dev, Layout, Rules, int);
+typedef void (*PolicyFn)(Dev, Layout, Rules, int, int);
 
 struct VariantDesc {
   const char *name;
@@ -377,9 +424,9 @@ cudaError_t policy_prepare(const Layout &L, const Rules &R, int variant, PolicyL
 }
 
 cudaError_t policy_launch(const PolicyLaunch &pl, const Dev &d, const Layout &L, const Rules &R,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool apply_moves) {
   PolicyFn fn = (PolicyFn)pl.fn;
-  fn<<<pl.blocks, pl.threads, pl.smem, s>>>(d, L, R, pl.xs_floats);
+  fn<<<pl.blocks, pl.threads, pl.smem, s>>>(d, L, R, pl.xs_floats, apply_moves ? 1 : 0);
   return cudaGetLastError();
 }
 
