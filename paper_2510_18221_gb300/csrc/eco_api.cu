@@ -188,6 +188,7 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.claim_att = k.take<unsigned long long>(slots);
   D.logits = k.take<float>((size_t)slots * L.A);
   D.alive_list = k.take<int32_t>(slots);
+  D.tile_counts = k.take<int32_t>(compact_tiles((int)slots));
   D.counters = k.take<int32_t>(CNT_N);
   D.births = k.take<int2>(slots);
   D.free_list = k.take<int32_t>(slots);

@@ -11,8 +11,8 @@
 // two parents onto one birth cell) are resolved by a 64-bit atomicMax of
 // (Philox draw << 32 | ~local slot): the highest draw wins, equal draws go
 // to the lower slot.  A maximum does not depend on the order of the
-// atomics, every other atomic is an integer add, and no phase depends on
-// the order of the alive list, so all integer state is bit-identical from
+// atomics, every other atomic is an integer add, and no phase's result
+// depends on the order of the alive list, so all integer state is bit-identical from
 // run to run and equal to the plain sequential rule.
 #include "eco_internal.cuh"
 #include "eco_kernels.h"
@@ -29,42 +29,54 @@ int grid_for(long long n, int threads, int max_blocks) {
   return (int)b;
 }
 
-// A0: list of alive slots (Sec. 3.1: the population function names the
-// alive agents).  Each thread looks at 16 consecutive slots; a warp appends
-// its alive slots with one atomic.  The list's order is irrelevant to every
-// later phase.  The counter is zeroed by the memset launched just before.
-__global__ void k_compact(Dev d) {
+// A0: list of alive slots in ascending slot order (Sec. 3.1: the population
+// function names the alive agents).  Two kernels over tiles of kCompactTile
+// slots: each tile counts its alive slots; then each tile adds up the
+// counts of the tiles before it (a few dozen numbers) and writes its slots.
+// Slot order keeps the warps of the policy kernel streaming neighbouring
+// weight blocks at the same time.
+constexpr int kCompactTile = 4096;  // 256 threads x 16 slots
+
+__device__ __forceinline__ uint32_t alive_mask16(const Dev &d, int s0) {
   const int S = d.total_slots;
-  const int lane = threadIdx.x & 31;
-  const int chunks = (S + 15) >> 4;
-  for (int base = blockIdx.x * blockDim.x; base < chunks; base += gridDim.x * blockDim.x) {
-    const int ch = base + threadIdx.x;
-    uint32_t mask = 0;
-    if (ch < chunks) {
-      const int s0 = ch << 4;
-      for (int k = 0; k < 16; ++k) {
-        const int s = s0 + k;
-        if (s < S && d.alive[s]) mask |= 1u << k;
-      }
-    }
-    const int cnt = __popc(mask);
-    int incl = cnt;
+  uint32_t mask = 0;
+  if (s0 + 16 <= S) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(d.alive + s0);  // 16-byte aligned
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int o = __shfl_up_sync(0xFFFFFFFFu, incl, off);
-      if (lane >= off) incl += o;
-    }
-    const int warp_total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    int wbase = 0;
-    if (lane == 31 && warp_total) wbase = atomicAdd(&d.counters[CNT_N_ALIVE], warp_total);
-    wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
-    int at = wbase + incl - cnt;
-    while (mask) {
-      const int k = __ffs(mask) - 1;
-      d.alive_list[at++] = (ch << 4) + k;
-      mask &= mask - 1;
-    }
+    for (int k = 0; k < 16; ++k)
+      if ((w[k >> 2] >> ((k & 3) * 8)) & 0xFFu) mask |= 1u << k;
+  } else {
+    for (int k = 0; k < 16 && s0 + k < S; ++k)
+      if (d.alive[s0 + k]) mask |= 1u << k;
   }
+  return mask;
+}
+
+__global__ void __launch_bounds__(256) k_compact_count(Dev d) {
+  __shared__ int sh[33];
+  const uint32_t mask = alive_mask16(d, blockIdx.x * kCompactTile + threadIdx.x * 16);
+  int total;
+  block_exclusive_scan(__popc(mask), &total, sh);
+  if (threadIdx.x == 0) d.tile_counts[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(256) k_compact_scatter(Dev d) {
+  __shared__ int sh[33];
+  int before = 0;
+  for (int k = threadIdx.x; k < (int)blockIdx.x; k += blockDim.x) before += d.tile_counts[k];
+  int base;
+  block_exclusive_scan(before, &base, sh);  // base = sum over the earlier tiles
+  const int s0 = blockIdx.x * kCompactTile + threadIdx.x * 16;
+  uint32_t mask = alive_mask16(d, s0);
+  int total;
+  int at = base + block_exclusive_scan(__popc(mask), &total, sh);
+  while (mask) {
+    const int k = __ffs(mask) - 1;
+    d.alive_list[at++] = s0 + k;
+    mask &= mask - 1;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) d.counters[CNT_N_ALIVE] = base + total;
 }
 
 // A6 (part 2) + A7: winners move (only the winner of a cell writes it, and
@@ -584,11 +596,12 @@ __global__ void k_finish(Dev d, Rules R) {
   }
 }
 
+int compact_tiles(int total_slots) { return (total_slots + kCompactTile - 1) / kCompactTile; }
+
 cudaError_t launch_compact(const Dev &d, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(d.counters + CNT_N_ALIVE, 0, sizeof(int32_t), s);
-  if (e != cudaSuccess) return e;
-  const int chunks = (d.total_slots + 15) / 16;
-  k_compact<<<grid_for(chunks, 256, 152 * 8), 256, 0, s>>>(d);
+  const int tiles = compact_tiles(d.total_slots);
+  k_compact_count<<<tiles, 256, 0, s>>>(d);
+  k_compact_scatter<<<tiles, 256, 0, s>>>(d);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ struct EnvGrid {
   int cell_blocks;  // blocks of 256 threads for per-cell phases
   int birth_blocks; // CTAs of the mutation kernel
 };
+int compact_tiles(int total_slots);
 cudaError_t launch_compact(const Dev &d, cudaStream_t s);
 cudaError_t env_prepare(const Layout &L);
 cudaError_t launch_env_phases(const Dev &d, const Layout &L, const Rules &R, const EnvGrid &g,

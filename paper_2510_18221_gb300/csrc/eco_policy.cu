@@ -183,8 +183,10 @@ __device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int 
   }
 }
 
+// The weight stream is latency-bound per warp: the register budget is capped
+// so that about 40 warps stay resident per SM.
 template <int PREC, int H, int WARPS, int UNROLL>
-__global__ void __launch_bounds__(WARPS * 32)
+__global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
     k_policy(Dev d, Layout L, Rules R, int xs_floats, int apply_moves) {
   constexpr int E = Unit<PREC>::E;
   constexpr int UPJ = H / E;
@@ -219,6 +221,10 @@ __global__ void __launch_bounds__(WARPS * 32)
       flush();
       e_cur = env;
     }
+    // -- observation: k x k x 3 patch (row, column, channel), then scalars.
+    // Its locals end with this scope so that they do not stay live (in
+    // registers) through the weight stream below.
+    {
     const EnvDesc ed = d.env[env];
     const int side = ed.side;
     const int pos = d.pos[slot];
@@ -226,8 +232,6 @@ __global__ void __launch_bounds__(WARPS * 32)
     const int f = d.facing[slot];
     const int rt = (f + 1) & 3;
     const uint8_t *cellf = d.cellf + ed.cell_off;
-
-    // -- observation: k x k x 3 patch (row, column, channel), then scalars
     for (int c = lane; c < kk; c += 32) {
       const int r = c / k, col = c - r * k;
       int dx, dy;
@@ -252,6 +256,7 @@ __global__ void __launch_bounds__(WARPS * 32)
       else if (R.n_scalars >= 8 && lane == 1 + f)
         v = 1.0f;
       xs[3 * kk + lane] = v;
+    }
     }
     __syncwarp();
 
@@ -292,6 +297,7 @@ __global__ void __launch_bounds__(WARPS * 32)
       d.logits[(int64_t)slot * L.A + lane] = lg;
       score = lg;
       if (!greedy) {
+        const EnvDesc ed = d.env[env];
         const U4 r = philox(t, (uint32_t)(slot - ed.slot_off), (uint32_t)(lane >> 2), 0u, ed.seed,
                             S_SAMPLE);
         const float u = uniform01(word_of(r, lane & 3));
@@ -313,6 +319,11 @@ __global__ void __launch_bounds__(WARPS * 32)
       // (no cell changes while the policy phase runs).
       int blk = 0;
       if (lane == 0) {
+        const EnvDesc ed = d.env[env];
+        const int side = ed.side;
+        const int pos = d.pos[slot];
+        const int f = d.facing[slot];
+        const uint8_t *cellf = d.cellf + ed.cell_off;
         int nf = f, tc = -1;
         if (best >= ACT_N && best <= ACT_W) {
           nf = (best == ACT_N) ? 0 : (best == ACT_S) ? 2 : (best == ACT_E) ? 1 : 3;
