@@ -49,7 +49,25 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="CPU time budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "fp8"],
+                    help="override the workload's streamed weight precision")
     return ap.parse_args()
+
+
+def make_workloads(args, rank):
+    """The worlds one rank advances: one named workload, or the 64 uneven
+    worlds of the batched workload (seeds offset per rank)."""
+    from paper_2510_18221_gb300 import workloads
+    if args.workload == "batched":
+        envs = workloads.batched(64, seed=0, base_seed=1000 * rank,
+                                 precision=args.precision or "bf16")
+    else:
+        base = workloads.get(args.workload)
+        envs = [workloads.get(args.workload, seed=base["seed"] + rank)]
+        if args.precision:
+            envs[0]["precision"] = args.precision
+            envs[0]["name"] = envs[0]["name"].rsplit("-", 1)[0] + "-" + args.precision
+    return envs
 
 
 def measured_peaks():
@@ -213,14 +231,18 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = workloads.get(args.workload, seed=workloads.get(args.workload)["seed"] + rank)
-    env = eco.Env(w)
+    envs = make_workloads(args, rank)
+    w = envs[0]
+    env = eco.Env(envs)
+
+    def agent_steps_of(stats):
+        return sum(s["agent_steps"] for s in stats)
 
     # ---- device-timed region -------------------------------------------------
     env.reset()
     env.step(args.warmup)            # builds the graph, autotunes the policy kernel
     torch.cuda.synchronize()
-    s0 = env.stats()[0]
+    s0 = env.stats()
     props = torch.cuda.get_device_properties(local)
     dev_id = None
     uuid = getattr(props, "uuid", None)
@@ -237,10 +259,10 @@ def main():
     barrier()
     clk = clocks.stop() if clocks else None
     ms = t_start.elapsed_time(t_end)
-    s1 = env.stats()[0]
+    s1 = env.stats()
     policy_ms, n_timed = env.policy_timing()
-    agent_steps = s1["agent_steps"] - s0["agent_steps"]
-    births = s1["births"] - s0["births"]
+    agent_steps = agent_steps_of(s1) - agent_steps_of(s0)
+    births = sum(s["births"] for s in s1) - sum(s["births"] for s in s0)
     per_agent_bytes, n_alive_now = env.policy_bytes()
     per_agent_bytes = per_agent_bytes // max(1, n_alive_now)
     policy_bytes = agent_steps * per_agent_bytes
@@ -249,7 +271,7 @@ def main():
     env.reset()
     env.step(args.warmup)
     torch.cuda.synchronize()
-    e0 = env.stats()[0]
+    e0 = env.stats()
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -257,8 +279,40 @@ def main():
         tot, last = eco.eco_read_stats(env.h, env.n_envs)   # device -> host, synchronises
     e_el = time.perf_counter() - t0
     barrier()
-    e_agent_steps = int(tot[0][1]) - e0["agent_steps"]
+    e_agent_steps = int(tot[:, 1].sum()) - agent_steps_of(e0)
     d2h = tot.nbytes + last.nbytes
+    variant_name = eco.eco_policy_variant_name(env.variants()[1])
+    env.close()
+    del env
+    torch.cuda.empty_cache()
+
+    # ---- batched only: the same worlds as separate handles, stepped one
+    #      after another on one stream (64 sequential single-world launches)
+    sequential = None
+    if args.workload == "batched":
+        shared = torch.cuda.Stream()
+        singles = [eco.Env(e, stream=shared) for e in envs]
+        for s in singles:
+            s.reset()
+            s.step(args.warmup)
+        torch.cuda.synchronize()
+        q0 = sum(agent_steps_of(s.stats()) for s in singles)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(shared)
+        for _ in range(args.steps):
+            for s in singles:
+                eco.eco_step(s.h, 1)
+        b.record(shared)
+        b.synchronize()
+        q1 = sum(agent_steps_of(s.stats()) for s in singles)
+        qms = a.elapsed_time(b)
+        sequential = {"value": (q1 - q0) / (qms * 1e-3), "unit": UNIT, "ms_per_step": qms / args.steps,
+                      "how": "%d handles, one world each, eco_step(h, 1) in turn on one stream" % len(singles)}
+        for s in singles:
+            s.close()
+        del singles
+        torch.cuda.empty_cache()
 
     totals = torch.tensor([float(ms), float(agent_steps), float(e_el), float(e_agent_steps)],
                           dtype=torch.float64, device="cuda")
@@ -291,16 +345,22 @@ def main():
             "dtype": "f32 (%s weights, int32 state)" % w["precision"],
             "data": "synthetic",
             "config": {
-                "workload": w["name"], "grid": "%dx%d" % (w["side"], w["side"]),
-                "slots": w["slots"], "founders": w["init_alive"],
-                "mlp": "%d-%d-%d-%d" % (env.D, w["hidden"], w["hidden"], w["n_actions"]),
+                "workload": ("batched: %d worlds (sides %s), %d slots, %d founders" % (
+                    len(envs), "/".join(str(s) for s in sorted({e["side"] for e in envs})),
+                    sum(e["slots"] for e in envs), sum(e["init_alive"] for e in envs)))
+                if args.workload == "batched" else w["name"],
+                "grid": "%dx%d" % (w["side"], w["side"]) if len(envs) == 1 else "mixed",
+                "slots": sum(e["slots"] for e in envs),
+                "founders": sum(e["init_alive"] for e in envs),
+                "mlp": "%d-%d-%d-%d" % (3 * w["patch_k"] ** 2 + w["n_scalars"], w["hidden"],
+                                        w["hidden"], w["n_actions"]),
                 "weights": w["precision"], "parallelism": "independent worlds, one per GPU",
                 "l2": "inputs larger than L2 (%.2f GB of weights streamed per step)" %
                       (policy_bytes / max(1, args.steps) / 1e9),
                 "window": "steps %d..%d after reset" % (args.warmup, args.warmup + args.steps),
                 "mean_alive": agent_steps / max(1, args.steps) / world,
                 "births": births,
-                "policy_variant": eco.eco_policy_variant_name(env.variants()[1]),
+                "policy_variant": variant_name,
             },
             "roofline": {
                 "bound": "hbm", "kernel": "k_policy", "achieved": achieved,
@@ -320,8 +380,9 @@ def main():
             "clocks": clk,
             "cpu_baseline": cpu,
         }
+        if sequential is not None:
+            line["sequential_single_world_launches"] = sequential
         print(json.dumps(line), flush=True)
-    env.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -51,9 +51,9 @@ LARGE = dict(MID, name="large-2048x2048-262144slots-683-128-128-9-fp8",
 WORKLOADS = {"small": SMALL, "mid": MID, "paper": PAPER, "large": LARGE}
 
 
-def get(name: str, **overrides) -> dict:
+def get(key: str, **overrides) -> dict:
     """A copy of a named workload with fields overridden."""
-    w = copy.deepcopy(WORKLOADS[name])
+    w = copy.deepcopy(WORKLOADS[key])
     w.update(overrides)
     return w
 

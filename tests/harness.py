@@ -45,9 +45,10 @@ def runs(slots):
     return out
 
 
-def push_params(env, orc, slots, e=0):
+def push_params(env, orc, slots, e=0, chunk=4096):
     for a, b in runs(slots):
-        env.write_params(e, a, orc.master[a:b])
+        for c in range(a, b, chunk):
+            env.write_params(e, c, orc.master[c:min(b, c + chunk)])
 
 
 def compare_state(gs, orc, where=""):
@@ -112,16 +113,32 @@ def check_policy(env, orc, pol, alive0, e=0, where=""):
     return err, act, diff
 
 
-def lockstep(env, orc, steps, e=0, where=""):
-    """Advance both sides `steps` steps in lock-step; returns a report."""
+def lockstep(env, orc, steps, e=0, where="", vs_master=False):
+    """Advance both sides `steps` steps in lock-step; returns a report.
+
+    With vs_master, every step also evaluates the oracle on the FP32 master
+    parameters (the unquantised policy) and records how far the GPU's
+    logits are from it and how often the GPU's action agrees with it
+    (quantisation error: reported, not bounded)."""
     rep = {"steps": 0, "ambiguous": 0, "births": 0, "max_logit_err": 0.0, "max_param_err": 0.0}
+    if vs_master:
+        rep.update({"agents": 0, "agree": 0, "master_err_max": 0.0, "master_err_sum": 0.0})
     for t in range(steps):
         tag = "%s step %d" % (where, int(orc.step[0]))
         alive0 = orc.alive.astype(bool).copy()
         pol = orc.policy(tol=GAP_TOL)
+        ref = orc.policy(use_master=True, tol=GAP_TOL) if vs_master else None
         env.step(1)
         err, act, diff = check_policy(env, orc, pol, alive0, e, tag)
         rep["max_logit_err"] = max(rep["max_logit_err"], err)
+        if vs_master and alive0.any():
+            lg, _ = env.read_policy_io(e)
+            r = ref["logits"][alive0]
+            rel = np.abs(lg[alive0].astype(np.float64) - r).max(axis=1) / np.maximum(1.0, np.abs(r).max(axis=1))
+            rep["master_err_max"] = max(rep["master_err_max"], float(rel.max()))
+            rep["master_err_sum"] += float(rel.sum())
+            rep["agents"] += int(alive0.sum())
+            rep["agree"] += int((act[alive0] == ref["action"][alive0]).sum())
         last = env.stats("last")[e]
         gs = env.read_state(e)
         if diff.any():

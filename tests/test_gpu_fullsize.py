@@ -1,0 +1,101 @@
+"""Full-size parity and long-run checks on the GPU.
+
+* The paper-scale workload (1024x1024 torus, 65,536 slots, 50,000 founders,
+  371 -> 64 -> 64 -> 9 BF16), in the launch configuration bench.py times
+  (autotuned policy variant), in lock-step with the oracle.
+* The mid workload (512x512, 16,384 slots, FP32) in lock-step for 200 steps.
+* A 1000-step GPU run at paper scale, checked every 50 steps against
+  properties that hold at any size: the statistics equal a recount of the
+  state, one agent per cell, the occupancy map equals the agents'
+  positions, no agent on a wall, every alive energy positive.
+* Opt-in (ECO_LONG=1): 1000-step lock-steps of the mid workload (seeds 0-3)
+  and of the paper-scale workload.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_18221_gb300 import workloads
+from tests import harness
+
+pytestmark = pytest.mark.gpu
+LONG = os.environ.get("ECO_LONG") == "1"
+
+
+def _pair(w):
+    from paper_2510_18221_gb300 import eco
+    return eco.Env(w), oracle.Oracle(w)
+
+
+def _lockstep(w, steps, sample=None):
+    env, orc = _pair(w)
+    try:
+        harness.start_pair(env, orc, sample=sample)
+        rep = harness.lockstep(env, orc, steps, where=w["name"])
+    finally:
+        env.close()
+    return rep
+
+
+def test_paper_workload_lockstep():
+    rep = _lockstep(workloads.get("paper"), 4, sample=512)
+    assert rep["steps"] == 4
+    print("paper-scale lock-step:", rep)
+
+
+def test_mid_workload_200_steps():
+    rep = _lockstep(workloads.get("mid"), 200, sample=256)
+    assert rep["steps"] == 200
+    print("mid lock-step:", rep)
+
+
+def check_state_properties(env, e, w, st):
+    s = env.read_state(e)
+    L = w["side"]
+    alive = np.flatnonzero(s["alive"])
+    cells = s["y"][alive] * L + s["x"][alive]
+    assert len(np.unique(cells)) == len(alive)
+    assert np.array_equal(s["occ"][cells], alive)
+    assert int((s["occ"] >= 0).sum()) == len(alive)
+    assert not s["wall"][cells].any()
+    assert (s["energy"][alive] > 0).all()
+    assert st["alive"] == len(alive)
+    assert st["food_total"] == int(s["food"].sum())
+    assert st["energy_total"] == int(s["energy"][alive].astype(np.int64).sum())
+    assert not (s["food"] & s["wall"]).any()
+    kids = alive[s["parent"][alive] >= 0]
+    assert (s["birth_step"][kids] >= 0).all()
+
+
+def test_paper_workload_1000_steps_properties():
+    from paper_2510_18221_gb300 import eco
+    w = workloads.get("paper")
+    env = eco.Env(w)
+    env.reset()
+    prev = env.stats()[0]
+    births = 0
+    for k in range(20):
+        env.step(50)
+        st = env.stats()[0]
+        assert st["step"] == 50 * (k + 1)
+        assert st["alive"] == prev["alive"] + (st["births"] - prev["births"]) - (st["deaths"] - prev["deaths"])
+        births = st["births"]
+        check_state_properties(env, 0, w, st)
+        prev = st
+    env.close()
+    assert births > 0
+
+
+@pytest.mark.skipif(not LONG, reason="long lock-step runs only with ECO_LONG=1")
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_long_mid_1000_steps(seed):
+    rep = _lockstep(workloads.get("mid", seed=seed), 1000, sample=128)
+    print("mid seed %d 1000-step lock-step:" % seed, rep)
+
+
+@pytest.mark.skipif(not LONG, reason="long lock-step runs only with ECO_LONG=1")
+def test_long_paper_1000_steps():
+    rep = _lockstep(workloads.get("paper"), 1000, sample=128)
+    print("paper-scale 1000-step lock-step:", rep)
