@@ -54,6 +54,18 @@ def parse():
     return ap.parse_args()
 
 
+def reduce_over_ranks(dist, times, counts, device="cpu"):
+    """Whole-job figures across ranks: the maximum of each time (the job
+    ends when the slowest rank ends) and the sum of each count (agent-steps
+    of every rank's world).  Returns the times, then the counts."""
+    import torch
+    t = torch.tensor([float(v) for v in times], dtype=torch.float64, device=device)
+    c = torch.tensor([float(v) for v in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return [float(v) for v in t.tolist()] + [int(v) for v in c.tolist()]
+
+
 def make_workloads(args, rank):
     """The worlds one rank advances: one named workload, or the 64 uneven
     worlds of the batched workload (seeds offset per rank)."""
@@ -314,15 +326,9 @@ def main():
         del singles
         torch.cuda.empty_cache()
 
-    totals = torch.tensor([float(ms), float(agent_steps), float(e_el), float(e_agent_steps)],
-                          dtype=torch.float64, device="cuda")
     if dist is not None:
-        mx = totals.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = totals.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms, e_el = float(mx[0]), float(mx[2])
-        agent_steps, e_agent_steps = int(sm[1]), int(sm[3])
+        ms, e_el, agent_steps, e_agent_steps = reduce_over_ranks(
+            dist, [ms, e_el], [agent_steps, e_agent_steps], device="cuda")
 
     peaks, peak_kind = measured_peaks()
     achieved = policy_bytes / (policy_ms * 1e-3) / 1e9 if policy_ms > 0 else 0.0

@@ -88,6 +88,29 @@ def test_paper_workload_1000_steps_properties():
     assert births > 0
 
 
+def test_large_workload_fullsize_properties():
+    """2048x2048, 262,144 slots, 200,000 founders, 683 -> 128 -> 128 -> 9 FP8
+    (138.6 GB workspace): the reset state's founders and 20 steps checked
+    against the recount properties; the oracle pins this MLP and precision
+    at a reduced size in test_gpu_parity."""
+    import torch
+    from paper_2510_18221_gb300 import eco
+    w = workloads.get("large")
+    free, _ = torch.cuda.mem_get_info()
+    if free < 150e9:
+        pytest.skip("needs ~140 GB of free device memory")
+    env = eco.Env(w)
+    env.reset()
+    st = env.stats()[0]
+    assert st["alive"] == 200000
+    check_state_properties(env, 0, w, st)
+    env.step(20)
+    st = env.stats()[0]
+    assert st["step"] == 20 and st["agent_steps"] > 20 * 190000
+    check_state_properties(env, 0, w, st)
+    env.close()
+
+
 @pytest.mark.skipif(not LONG, reason="long lock-step runs only with ECO_LONG=1")
 @pytest.mark.parametrize("seed", [0, 1, 2, 3])
 def test_long_mid_1000_steps(seed):
