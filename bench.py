@@ -34,9 +34,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "agent-steps/sec at 65,536 agents (policy+env) and policy-kernel HBM GB/s vs peak"
 UNIT = "agent-steps/s"
-# compact, policy (+ move claims), move+eat, attack claim, attack gain,
-# metabolism+death, birth claim, birth assign, mutate, regrow, finish
-KERNELS_PER_STEP = 11
+# Kernels per step: the policy kernel (with the move claims) plus either one
+# persistent kernel for every environment phase, or one kernel per phase:
+# move+eat, attack claim, attack gain, metabolism+death, birth claim, birth
+# assign, mutate, regrow, finish, and the two passes of the alive list.
+KERNELS_PER_STEP = {0: 2, 1: 12}
 
 
 def parse():
@@ -294,6 +296,7 @@ def main():
     e_agent_steps = int(tot[:, 1].sum()) - agent_steps_of(e0)
     d2h = tot.nbytes + last.nbytes
     variant_name = eco.eco_policy_variant_name(env.variants()[1])
+    launch_mode, launch_blocks = env.launch_mode()
     env.close()
     del env
     torch.cuda.empty_cache()
@@ -367,6 +370,8 @@ def main():
                 "mean_alive": agent_steps / max(1, args.steps) / world,
                 "births": births,
                 "policy_variant": variant_name,
+                "env_phases": ("one persistent cooperative kernel, %d CTAs" % launch_blocks
+                               if launch_mode == 0 else "one kernel per phase"),
             },
             "roofline": {
                 "bound": "hbm", "kernel": "k_policy", "achieved": achieved,
@@ -382,7 +387,7 @@ def main():
             },
             "e2e": {"value": e_agent_steps / e_el, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "gpu_launches": KERNELS_PER_STEP[launch_mode] * args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

@@ -98,6 +98,10 @@ typedef struct {
   int32_t attack_num, attack_den;/* transferred fraction of victim energy    */
   int32_t policy_variant;        /* 0 = autotune at create; k > 0 = force
                                     variant k (see eco_policy_variants)      */
+  int32_t launch_mode;           /* environment phases: 0 = one persistent
+                                    cooperative kernel when the device
+                                    supports it, 1 = one kernel per phase
+                                    (identical results)                     */
 } eco_config;
 
 /* Statistics, one record per environment (App. E measurement API).
@@ -205,6 +209,12 @@ int eco_read_policy_io(eco_handle *h, int32_t env, float *logits, uint8_t *actio
  * eco_policy_variant_name() describes variant k (static string). */
 int eco_policy_variants(const eco_handle *h, int32_t *count, int32_t *chosen);
 const char *eco_policy_variant_name(int32_t k);
+
+/* Launch form of the environment phases in use: *mode 0 = one persistent
+ * cooperative kernel of *blocks CTAs, 1 = one kernel per phase.  Decided at
+ * the first eco_step (falls back to 1 when the device or the graph capture
+ * does not support the cooperative form). */
+int eco_launch_mode(const eco_handle *h, int32_t *mode, int32_t *blocks);
 
 /* Like eco_step, and also records a CUDA-event pair around the policy
  * kernel of every step, on the library stream, inside the step's graph.

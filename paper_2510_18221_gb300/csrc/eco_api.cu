@@ -93,6 +93,7 @@ static int validate(const eco_config *c, char *msg, size_t n) {
   if (c->e_repro <= 0 || c->attack_den <= 0 || c->attack_num < 0 || c->e_metab < 0)
     return snprintf(msg, n, "bad energy constants"), ECO_EINVAL;
   if (!(c->sigma >= 0.0f) || !std::isfinite(c->sigma)) return snprintf(msg, n, "bad sigma"), ECO_EINVAL;
+  if (c->launch_mode < 0 || c->launch_mode > 1) return snprintf(msg, n, "launch_mode must be 0 or 1"), ECO_EINVAL;
   if (c->policy_variant < 0 || c->policy_variant > policy_variant_count())
     return snprintf(msg, n, "policy_variant out of range"), ECO_EINVAL;
   long long cells = 0, slots = 0;
@@ -189,6 +190,7 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.logits = k.take<float>((size_t)slots * L.A);
   D.alive_list = k.take<int32_t>(slots);
   D.tile_counts = k.take<int32_t>(compact_tiles((int)slots));
+  D.barrier = k.take<unsigned>(2);
   D.counters = k.take<int32_t>(CNT_N);
   D.births = k.take<int2>(slots);
   D.free_list = k.take<int32_t>(slots);
@@ -300,6 +302,8 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
   h->grid.slot_blocks = grid_for(h->d.total_slots, 256, h->grid.sms * 8);
   h->grid.cell_blocks = grid_for(h->d.total_cells / 4, 256, h->grid.sms * 8);
   h->grid.birth_blocks = h->grid.sms * 2;
+  h->grid.persistent_blocks = 0;
+  h->grid.use_persistent = cfg->launch_mode == 0;
   h->forced = cfg->policy_variant;
   h->variant = 0;
   h->graph = nullptr;
@@ -312,7 +316,7 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
     e = cudaMemcpyAsync(h->env_dev, h->env_host.data(), sizeof(EnvDesc) * h->n_envs,
                         cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = launch_init_static(h->d, h->grid, h->stream);
-  if (e == cudaSuccess) e = env_prepare(h->L);
+  if (e == cudaSuccess) e = env_prepare(h->L, &h->grid);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[1]);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -359,7 +363,10 @@ static int check_status(eco_handle *h) {
 
 extern "C" int eco_reset(eco_handle *h) {
   if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  // also clears the status word and the persistent form's barrier
+  CUDA_TRY(h, cudaMemsetAsync(h->d.barrier, 0, 2 * sizeof(unsigned), h->stream));
   CUDA_TRY(h, launch_reset(h->d, h->L, h->R, h->grid, h->stream));
+  CUDA_TRY(h, launch_compact(h->d, h->stream));
   return check_status(h);
 }
 
@@ -398,10 +405,12 @@ static int autotune(eco_handle *h) {
   return ECO_OK;
 }
 
+// One step: the alive list was built by the previous step (or by reset /
+// write_state), so the step is the policy kernel and the environment
+// phases, which end by building the next step's alive list.
 static cudaError_t enqueue_step(eco_handle *h) {
-  cudaError_t e = launch_compact(h->d, h->stream);
   // "external" records become event-record nodes of the captured graph
-  if (e == cudaSuccess) e = cudaEventRecordWithFlags(h->ev_dummy[0], h->stream, cudaEventRecordExternal);
+  cudaError_t e = cudaEventRecordWithFlags(h->ev_dummy[0], h->stream, cudaEventRecordExternal);
   if (e == cudaSuccess) e = policy_launch(h->pl, h->d, h->L, h->R, h->stream, true);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(h->ev_dummy[1], h->stream, cudaEventRecordExternal);
   if (e == cudaSuccess) e = launch_env_phases(h->d, h->L, h->R, h->grid, h->stream);
@@ -412,12 +421,24 @@ static int build_graph(eco_handle *h) {
   if (h->graph) return ECO_OK;
   int rc = autotune(h);
   if (rc) return rc;
-  cudaGraph_t g;
-  CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = enqueue_step(h);
-  cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
-  if (e != cudaSuccess) return fail(h, ECO_ECUDA, "capture: %s", cudaGetErrorString(e));
-  if (e2 != cudaSuccess) return fail(h, ECO_ECUDA, "end capture: %s", cudaGetErrorString(e2));
+  cudaGraph_t g = nullptr;
+  for (;;) {
+    CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_step(h);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e == cudaSuccess && e2 == cudaSuccess) break;
+    if (e2 == cudaSuccess && g) cudaGraphDestroy(g);
+    g = nullptr;
+    cudaGetLastError();
+    if (h->grid.use_persistent && h->grid.persistent_blocks > 0) {
+      // the persistent form could not be captured: fall back to one
+      // kernel per phase (identical results)
+      h->grid.use_persistent = 0;
+      continue;
+    }
+    if (e != cudaSuccess) return fail(h, ECO_ECUDA, "capture: %s", cudaGetErrorString(e));
+    return fail(h, ECO_ECUDA, "end capture: %s", cudaGetErrorString(e2));
+  }
   // locate the two event-record nodes (in capture order)
   size_t n = 0;
   CUDA_TRY(h, cudaGraphGetNodes(g, nullptr, &n));
@@ -511,6 +532,14 @@ extern "C" int eco_policy_variants(const eco_handle *h, int32_t *count, int32_t 
 }
 
 extern "C" const char *eco_policy_variant_name(int32_t k) { return policy_variant_name(k); }
+
+extern "C" int eco_launch_mode(const eco_handle *h, int32_t *mode, int32_t *blocks) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  const bool pers = h->grid.use_persistent && h->grid.persistent_blocks > 0;
+  if (mode) *mode = pers ? 0 : 1;
+  if (blocks) *blocks = pers ? h->grid.persistent_blocks : 0;
+  return ECO_OK;
+}
 
 extern "C" int eco_policy_bytes(eco_handle *h, int64_t *bytes, int64_t *n_alive) {
   if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
@@ -633,6 +662,7 @@ extern "C" int eco_write_state(eco_handle *h, int32_t env, const eco_state_view 
     CUDA_TRY(h, cudaStreamSynchronize(s));
   }
   CUDA_TRY(h, launch_recount(h->d, h->R, s));
+  CUDA_TRY(h, launch_compact(h->d, s));
   CUDA_TRY(h, cudaStreamSynchronize(s));
   return ECO_OK;
 }

@@ -2,21 +2,28 @@
 // "Resources and Agent Health"; Sec. 3.3 mutation), for every environment
 // of the batch at once.
 //
-// Phase order: alive compaction -> policy (+ facing, turns and move claims,
-// fused into its epilogue) -> move apply + eat -> attack claims -> attack
+// Phase order: policy (+ facing, turns and move claims, fused into its
+// epilogue; eco_policy.cu) -> move apply + eat -> attack claims -> attack
 // gains -> metabolism + death -> birth claims -> slot assignment ->
-// mutation of the children -> regrowth -> statistics.
+// mutation of the children + regrowth -> statistics + the alive list of the
+// next step.
+//
+// Two launch forms run the same phase functions: one persistent kernel
+// (cooperative launch; phases separated by grid barriers whose waits are
+// bounded, so a stuck barrier sets the status word and every CTA exits), and
+// one kernel per phase.  Both give bit-identical results.
 //
 // Conflicts (two movers into one free cell, two attackers on one victim,
 // two parents onto one birth cell) are resolved by a 64-bit atomicMax of
 // (Philox draw << 32 | ~local slot): the highest draw wins, equal draws go
 // to the lower slot.  A maximum does not depend on the order of the
 // atomics, every other atomic is an integer add, and no phase's result
-// depends on the order of the alive list, so all integer state is bit-identical from
-// run to run and equal to the plain sequential rule.
+// depends on the order in which agents are visited, so all integer state
+// is bit-identical from run to run and equal to the plain sequential rule.
 #include "eco_internal.cuh"
 #include "eco_kernels.h"
 
+#include <cuda/atomic>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -29,13 +36,20 @@ int grid_for(long long n, int threads, int max_blocks) {
   return (int)b;
 }
 
+// ---------------------------------------------------------------------------
 // A0: list of alive slots in ascending slot order (Sec. 3.1: the population
-// function names the alive agents).  Two kernels over tiles of kCompactTile
+// function names the alive agents).  Two passes over tiles of kCompactTile
 // slots: each tile counts its alive slots; then each tile adds up the
 // counts of the tiles before it (a few dozen numbers) and writes its slots.
 // Slot order keeps the warps of the policy kernel streaming neighbouring
-// weight blocks at the same time.
+// weight blocks at the same time.  Block-level: the first 256 threads of a
+// CTA of any size >= 256 cover a tile.
+// ---------------------------------------------------------------------------
 constexpr int kCompactTile = 4096;  // 256 threads x 16 slots
+
+__host__ __device__ int compact_tiles(int total_slots) {
+  return (total_slots + kCompactTile - 1) / kCompactTile;
+}
 
 __device__ __forceinline__ uint32_t alive_mask16(const Dev &d, int s0) {
   const int S = d.total_slots;
@@ -53,39 +67,48 @@ __device__ __forceinline__ uint32_t alive_mask16(const Dev &d, int s0) {
   return mask;
 }
 
-__global__ void __launch_bounds__(256) k_compact_count(Dev d) {
-  __shared__ int sh[33];
-  const uint32_t mask = alive_mask16(d, blockIdx.x * kCompactTile + threadIdx.x * 16);
-  int total;
-  block_exclusive_scan(__popc(mask), &total, sh);
-  if (threadIdx.x == 0) d.tile_counts[blockIdx.x] = total;
+__device__ void ph_compact_count(const Dev &d, int b0, int bs, int *sh) {
+  const int tiles = compact_tiles(d.total_slots);
+  for (int tile = b0; tile < tiles; tile += bs) {
+    const uint32_t mask =
+        threadIdx.x < kCompactTile / 16 ? alive_mask16(d, tile * kCompactTile + threadIdx.x * 16) : 0u;
+    int total;
+    block_exclusive_scan(__popc(mask), &total, sh);
+    if (threadIdx.x == 0) d.tile_counts[tile] = total;
+  }
 }
 
-__global__ void __launch_bounds__(256) k_compact_scatter(Dev d) {
-  __shared__ int sh[33];
-  int before = 0;
-  for (int k = threadIdx.x; k < (int)blockIdx.x; k += blockDim.x) before += d.tile_counts[k];
-  int base;
-  block_exclusive_scan(before, &base, sh);  // base = sum over the earlier tiles
-  const int s0 = blockIdx.x * kCompactTile + threadIdx.x * 16;
-  uint32_t mask = alive_mask16(d, s0);
-  int total;
-  int at = base + block_exclusive_scan(__popc(mask), &total, sh);
-  while (mask) {
-    const int k = __ffs(mask) - 1;
-    d.alive_list[at++] = s0 + k;
-    mask &= mask - 1;
+__device__ void ph_compact_scatter(const Dev &d, int b0, int bs, int *sh) {
+  const int tiles = compact_tiles(d.total_slots);
+  for (int tile = b0; tile < tiles; tile += bs) {
+    int before = 0;
+    for (int k = threadIdx.x; k < tile; k += blockDim.x) before += d.tile_counts[k];
+    int base;
+    block_exclusive_scan(before, &base, sh);  // base = sum over the earlier tiles
+    const int s0 = tile * kCompactTile + threadIdx.x * 16;
+    uint32_t mask = threadIdx.x < kCompactTile / 16 ? alive_mask16(d, s0) : 0u;
+    int total;
+    int at = base + block_exclusive_scan(__popc(mask), &total, sh);
+    while (mask) {
+      const int k = __ffs(mask) - 1;
+      d.alive_list[at++] = s0 + k;
+      mask &= mask - 1;
+    }
+    if (tile == tiles - 1 && threadIdx.x == 0) d.counters[CNT_N_ALIVE] = base + total;
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) d.counters[CNT_N_ALIVE] = base + total;
 }
+
+// ---------------------------------------------------------------------------
+// Per-agent phases (grid-stride over the alive list).
+// ---------------------------------------------------------------------------
 
 // A6 (part 2) + A7: winners move (only the winner of a cell writes it, and
 // a winner's old cell was occupied when the step began, so nobody moves
 // into it); then every agent eats the food of its post-move cell, when the
 // rules say it eats.  Nobody else can be on that cell.
-__global__ void k_move_apply_eat(Dev d, Rules R, int n_actions) {
+__device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, int g0, int gs) {
   const int n = d.counters[CNT_N_ALIVE];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = g0; i < n; i += gs) {
     const int slot = d.alive_list[i];
     const int e = d.env_of[slot];
     const EnvDesc ed = d.env[e];
@@ -123,10 +146,10 @@ __global__ void k_move_apply_eat(Dev d, Rules R, int n_actions) {
 
 // A8 (part 1): clear this step's move claims; attackers claim the agent on
 // the faced cell (post-move occupancy).
-__global__ void k_attack_claim(Dev d, Rules R) {
+__device__ void ph_attack_claim(const Dev &d, const Rules &R, int g0, int gs) {
   const int n = d.counters[CNT_N_ALIVE];
   const uint32_t t = (uint32_t)d.step[0];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = g0; i < n; i += gs) {
     const int slot = d.alive_list[i];
     const int e = d.env_of[slot];
     const EnvDesc ed = d.env[e];
@@ -152,9 +175,9 @@ __global__ void k_attack_claim(Dev d, Rules R) {
 
 // A8 (part 2): the winning attacker of each victim takes floor(e * num /
 // den) of the victim's post-eat energy (read here, written only later).
-__global__ void k_attack_gain(Dev d, Rules R) {
+__device__ void ph_attack_gain(const Dev &d, const Rules &R, int g0, int gs) {
   const int n = d.counters[CNT_N_ALIVE];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = g0; i < n; i += gs) {
     const int slot = d.alive_list[i];
     const int v = d.tgt[slot];
     int g = 0;
@@ -172,9 +195,9 @@ __global__ void k_attack_gain(Dev d, Rules R) {
 }
 
 // A8 (part 3) + A9: apply the transfer, pay metabolism, die at e <= 0.
-__global__ void k_metab_death(Dev d, Rules R) {
+__device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs) {
   const int n = d.counters[CNT_N_ALIVE];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = g0; i < n; i += gs) {
     const int slot = d.alive_list[i];
     int en = d.energy[slot];
     const unsigned long long ca = d.claim_att[slot];
@@ -197,10 +220,10 @@ __global__ void k_metab_death(Dev d, Rules R) {
 
 // A10 (part 1): agents with e >= e_repro claim the free non-wall cell
 // behind them and join their environment's contender list.
-__global__ void k_birth_claim(Dev d, Rules R) {
+__device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs) {
   const int n = d.counters[CNT_N_ALIVE];
   const uint32_t t = (uint32_t)d.step[0];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = g0; i < n; i += gs) {
     const int slot = d.alive_list[i];
     int bt = -1;
     if (d.alive[slot] && d.energy[slot] >= R.e_repro) {
@@ -221,7 +244,23 @@ __global__ void k_birth_claim(Dev d, Rules R) {
   }
 }
 
-// Give winner p (global slot) the child slot c (global) behind it.
+// ---------------------------------------------------------------------------
+// A10 (part 2): slot assignment, one CTA per environment.  Cell winners in
+// ascending slot order take the free slots in ascending order; the child
+// gets floor(e/2) of the parent's energy, the parent's facing, and the cell
+// behind.  Winners (at most kBirthCap per step) are sorted in shared memory
+// and only the first n_winners free slots are searched for; more
+// contenders than kBirthCap fall back to a full scan of the slots.
+// ---------------------------------------------------------------------------
+constexpr int kBirthCap = 2048;
+
+struct BirthSmem {
+  int sh[33];
+  int win[kBirthCap];
+  int free_[kBirthCap];
+  int nwin;
+};
+
 __device__ __forceinline__ void make_child(const Dev &d, const EnvDesc &ed, int p, int c, int bt,
                                            uint32_t t) {
   const int en = d.energy[p];
@@ -239,25 +278,13 @@ __device__ __forceinline__ void make_child(const Dev &d, const EnvDesc &ed, int 
   d.births[b] = make_int2(p, c);
 }
 
-// A10 (part 2): one CTA per environment.  Cell winners in ascending slot
-// order take the free slots in ascending order; the child gets floor(e/2)
-// of the parent's energy, the parent's facing, and the cell behind.
-// Winners (at most kBirthCap per step) are sorted in shared memory; only
-// the first n_winners free slots are searched for.  More contenders than
-// kBirthCap fall back to a full scan of the environment's slots.
-constexpr int kBirthCap = 2048;
-
-__global__ void __launch_bounds__(1024) k_birth_assign(Dev d) {
-  __shared__ int sh[33];
-  __shared__ int s_win[kBirthCap];
-  __shared__ int s_free[kBirthCap];
-  __shared__ int s_nwin, s_nfree;
-  const int e = blockIdx.x;
+__device__ void birth_assign_env(const Dev &d, int e, BirthSmem &S) {
   const int nc = d.birth_contenders[e];
   if (nc == 0) return;  // uniform across the CTA
   const EnvDesc ed = d.env[e];
   const uint32_t t = (uint32_t)d.step[0];
   const int tid = threadIdx.x, nt = blockDim.x;
+  int born = 0, failed = 0;
 
   if (nc <= kBirthCap) {
     int p2 = 1;
@@ -269,20 +296,19 @@ __global__ void __launch_bounds__(1024) k_birth_assign(Dev d) {
         const int bt = d.tgt[g];
         if (claim_local_slot(d.claim_birth[ed.cell_off + bt]) == g - ed.slot_off) v = g;
       }
-      s_win[i] = v;
+      S.win[i] = v;
     }
     __syncthreads();
-    // bitonic sort of s_win[0, p2) ascending
-    for (int k = 2; k <= p2; k <<= 1) {
+    for (int k = 2; k <= p2; k <<= 1) {  // bitonic sort, ascending
       for (int j = k >> 1; j > 0; j >>= 1) {
         for (int i = tid; i < p2; i += nt) {
           const int l = i ^ j;
           if (l > i) {
-            const int a = s_win[i], b = s_win[l];
+            const int a = S.win[i], b = S.win[l];
             const bool up = (i & k) == 0;
             if ((a > b) == up) {
-              s_win[i] = b;
-              s_win[l] = a;
+              S.win[i] = b;
+              S.win[l] = a;
             }
           }
         }
@@ -291,93 +317,100 @@ __global__ void __launch_bounds__(1024) k_birth_assign(Dev d) {
     }
     if (tid == 0) {
       int nw = 0;
-      while (nw < p2 && s_win[nw] != 0x7FFFFFFF) ++nw;
-      s_nwin = nw;
+      while (nw < p2 && S.win[nw] != 0x7FFFFFFF) ++nw;
+      S.nwin = nw;
     }
     __syncthreads();
-    const int nwin = s_nwin;
-    // the first nwin free slots, 16 slots per thread per pass
-    int found = 0;
-    for (int base = 0; base < ed.n_slots && found < nwin; base += nt * 16) {
-      const int s0 = base + tid * 16;
-      uint32_t mask = 0;
-      for (int k = 0; k < 16; ++k) {
-        const int s = s0 + k;
-        if (s < ed.n_slots && !d.alive[ed.slot_off + s]) mask |= 1u << k;
+    const int nwin = S.nwin;
+    int found = 0;  // the first nwin free slots, 64 slots per thread per pass
+    for (int base = 0; base < ed.n_slots && found < nwin; base += nt * 64) {
+      const int s0 = base + tid * 64;
+      unsigned long long mask = 0ull;
+      const uint8_t *al = d.alive + ed.slot_off + s0;
+      if (s0 + 64 <= ed.n_slots && ((reinterpret_cast<uintptr_t>(al) & 15) == 0)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint4 v = reinterpret_cast<const uint4 *>(al)[q];
+          const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            if (!((w4[k >> 2] >> ((k & 3) * 8)) & 0xFFu)) mask |= 1ull << (q * 16 + k);
+        }
+      } else {
+        for (int k = 0; k < 64; ++k)
+          if (s0 + k < ed.n_slots && !al[k]) mask |= 1ull << k;
       }
       int total;
-      int r = found + block_exclusive_scan(__popc(mask), &total, sh);
+      int r = found + block_exclusive_scan(__popcll(mask), &total, S.sh);
       while (mask && r < nwin) {
-        const int k = __ffs(mask) - 1;
-        s_free[r++] = s0 + k;
+        const int k = __ffsll(mask) - 1;
+        S.free_[r++] = s0 + k;
         mask &= mask - 1;
       }
       found += total;
       __syncthreads();
     }
     const int nfree = found < nwin ? found : nwin;
-    int born = 0, failed = 0;
     for (int i = tid; i < nwin; i += nt) {
-      const int p = s_win[i];
+      const int p = S.win[i];
       const int bt = d.tgt[p];
       d.claim_birth[ed.cell_off + bt] = 0ull;
       if (i < nfree) {
-        make_child(d, ed, p, ed.slot_off + s_free[i], bt, t);
+        make_child(d, ed, p, ed.slot_off + S.free_[i], bt, t);
         ++born;
       } else {
         ++failed;
       }
     }
-    if (born) atomicAdd((unsigned long long *)&d.stats_step[e * N_ST + ST_BIRTHS], (unsigned long long)born);
-    if (failed)
-      atomicAdd((unsigned long long *)&d.stats_step[e * N_ST + ST_FAILED_BIRTHS], (unsigned long long)failed);
-    return;
-  }
-
-  // Fallback: full scan over the environment's slots (more than kBirthCap
-  // contenders this step).
-  const int n = ed.n_slots;
-  const int per = (n + nt - 1) / nt;
-  const int beg = min(n, tid * per), end = min(n, beg + per);
-  int nfree = 0, nwin = 0;
-  for (int s = beg; s < end; ++s) {
-    const int g = ed.slot_off + s;
-    uint8_t fl = 0;
-    if (!d.alive[g]) {
-      fl = 1;
-      ++nfree;
-    } else {
-      const int bt = d.tgt[g];
-      if (bt >= 0 && claim_local_slot(d.claim_birth[ed.cell_off + bt]) == s) {
-        fl = 2;
-        ++nwin;
+  } else {
+    // full scan over the environment's slots
+    const int n = ed.n_slots;
+    const int per = (n + nt - 1) / nt;
+    const int beg = min(n, tid * per), end = min(n, beg + per);
+    int nfree = 0, nwin = 0;
+    for (int s = beg; s < end; ++s) {
+      const int g = ed.slot_off + s;
+      uint8_t fl = 0;
+      if (!d.alive[g]) {
+        fl = 1;
+        ++nfree;
+      } else {
+        const int bt = d.tgt[g];
+        if (bt >= 0 && claim_local_slot(d.claim_birth[ed.cell_off + bt]) == s) {
+          fl = 2;
+          ++nwin;
+        }
       }
+      d.bflag[g] = fl;
     }
-    d.bflag[g] = fl;
-  }
-  int free_total, win_total;
-  int free_off = block_exclusive_scan(nfree, &free_total, sh);
-  int win_off = block_exclusive_scan(nwin, &win_total, sh);
-  for (int s = beg; s < end; ++s)
-    if (d.bflag[ed.slot_off + s] == 1) d.free_list[ed.slot_off + free_off++] = s;
-  __syncthreads();
-  int failed = 0, born = 0;
-  for (int s = beg; s < end; ++s) {
-    const int p = ed.slot_off + s;
-    if (d.bflag[p] != 2) continue;
-    const int r = win_off++;
-    const int bt = d.tgt[p];
-    d.claim_birth[ed.cell_off + bt] = 0ull;
-    if (r >= free_total) {
-      ++failed;
-      continue;
+    int free_total, win_total;
+    int free_off = block_exclusive_scan(nfree, &free_total, S.sh);
+    int win_off = block_exclusive_scan(nwin, &win_total, S.sh);
+    for (int s = beg; s < end; ++s)
+      if (d.bflag[ed.slot_off + s] == 1) d.free_list[ed.slot_off + free_off++] = s;
+    __syncthreads();
+    for (int s = beg; s < end; ++s) {
+      const int p = ed.slot_off + s;
+      if (d.bflag[p] != 2) continue;
+      const int r = win_off++;
+      const int bt = d.tgt[p];
+      d.claim_birth[ed.cell_off + bt] = 0ull;
+      if (r >= free_total) {
+        ++failed;
+        continue;
+      }
+      make_child(d, ed, p, ed.slot_off + d.free_list[ed.slot_off + r], bt, t);
+      ++born;
     }
-    make_child(d, ed, p, ed.slot_off + d.free_list[ed.slot_off + r], bt, t);
-    ++born;
   }
   if (born) atomicAdd((unsigned long long *)&d.stats_step[e * N_ST + ST_BIRTHS], (unsigned long long)born);
   if (failed)
     atomicAdd((unsigned long long *)&d.stats_step[e * N_ST + ST_FAILED_BIRTHS], (unsigned long long)failed);
+  __syncthreads();  // S is reused by the next environment of this CTA
+}
+
+__device__ void ph_birth_assign(const Dev &d, int b0, int bs, BirthSmem &S) {
+  for (int e = b0; e < d.n_envs; e += bs) birth_assign_env(d, e, S);
 }
 
 // ---------------------------------------------------------------------------
@@ -391,7 +424,7 @@ __global__ void __launch_bounds__(1024) k_birth_assign(Dev d) {
 // normals in logical order (one Philox block per four parameters) into
 // shared memory, then walks the master in its physical (input-major) order
 // so global reads and writes are contiguous; FP8 row scales come from the
-// tile's complete rows.
+// tile's complete rows.  Block-level (any multiple of 32 threads).
 // ---------------------------------------------------------------------------
 constexpr int kMutRows = 16;
 
@@ -399,9 +432,8 @@ __device__ __forceinline__ uint8_t e4m3_sat(float v) {
   return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
 }
 
-__global__ void __launch_bounds__(256) k_mutate(Dev d, Layout L, Rules R) {
-  extern __shared__ __align__(16) float msm[];
-  __shared__ float s_scale[kMutRows + 16];
+__device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0, int bs, float *msm,
+                          float *s_scale) {
   const int D = L.D, H = L.H, A = L.A;
   const int nb = d.counters[CNT_N_BIRTHS];
   const int tiles = H / kMutRows;
@@ -411,7 +443,7 @@ __global__ void __launch_bounds__(256) k_mutate(Dev d, Layout L, Rules R) {
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int64_t mper = L.mstride / 4;
 
-  for (int w = blockIdx.x; w < nb * items; w += gridDim.x) {
+  for (int w = b0; w < nb * items; w += bs) {
     const int b = w / items, it = w - b * items;
     const int2 pc = d.births[b];
     const EnvDesc ed = d.env[d.env_of[pc.y]];
@@ -528,10 +560,10 @@ size_t mutate_smem_bytes(const Layout &L) {
 
 // A12: regrowth of food on non-wall food-less cells; four cells per thread
 // share one Philox block (counter (step, local cell / 4)).
-__global__ void k_regrow(Dev d, Rules R) {
+__device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs) {
   const int groups = d.total_cells >> 2;
   const uint32_t t = (uint32_t)d.step[0];
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {
+  for (int g = g0; g < groups; g += gs) {
     const int c0 = g << 2;
     const int e = env_of_cell(d.env, d.n_envs, c0);
     const EnvDesc ed = d.env[e];
@@ -552,9 +584,9 @@ __global__ void k_regrow(Dev d, Rules R) {
 }
 
 // A13: fold this step's counters into the per-environment records and
-// advance the step counter.  Agent-steps and attacks come from the action
-// histogram the policy kernel counted.
-__global__ void k_finish(Dev d, Rules R) {
+// advance the step counter (one CTA).  Agent-steps and attacks come from the
+// action histogram the policy kernel counted.
+__device__ void ph_finish(const Dev &d, const Rules &R) {
   const long long t = d.step[0];
   for (int i = threadIdx.x; i < d.n_envs; i += blockDim.x) {
     long long *st = d.stats_step + i * N_ST;
@@ -596,8 +628,107 @@ __global__ void k_finish(Dev d, Rules R) {
   }
 }
 
-int compact_tiles(int total_slots) { return (total_slots + kCompactTile - 1) / kCompactTile; }
+// ---------------------------------------------------------------------------
+// One kernel per phase.
+// ---------------------------------------------------------------------------
+#define GRID_ARGS blockIdx.x *blockDim.x + threadIdx.x, gridDim.x *blockDim.x
 
+__global__ void __launch_bounds__(256) k_compact_count(Dev d) {
+  __shared__ int sh[33];
+  ph_compact_count(d, blockIdx.x, gridDim.x, sh);
+}
+__global__ void __launch_bounds__(256) k_compact_scatter(Dev d) {
+  __shared__ int sh[33];
+  ph_compact_scatter(d, blockIdx.x, gridDim.x, sh);
+}
+__global__ void k_move_apply_eat(Dev d, Rules R, int A) { ph_move_apply_eat(d, R, A, GRID_ARGS); }
+__global__ void k_attack_claim(Dev d, Rules R) { ph_attack_claim(d, R, GRID_ARGS); }
+__global__ void k_attack_gain(Dev d, Rules R) { ph_attack_gain(d, R, GRID_ARGS); }
+__global__ void k_metab_death(Dev d, Rules R) { ph_metab_death(d, R, GRID_ARGS); }
+__global__ void k_birth_claim(Dev d, Rules R) { ph_birth_claim(d, R, GRID_ARGS); }
+__global__ void __launch_bounds__(1024) k_birth_assign(Dev d) {
+  __shared__ BirthSmem S;
+  ph_birth_assign(d, blockIdx.x, gridDim.x, S);
+}
+__global__ void __launch_bounds__(256) k_mutate(Dev d, Layout L, Rules R) {
+  extern __shared__ __align__(16) float msm[];
+  __shared__ float s_scale[kMutRows];
+  ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale);
+}
+__global__ void k_regrow(Dev d, Rules R) { ph_regrow(d, R, GRID_ARGS); }
+__global__ void k_finish(Dev d, Rules R) { ph_finish(d, R); }
+
+// ---------------------------------------------------------------------------
+// The persistent form: all phases in one cooperative launch.
+// ---------------------------------------------------------------------------
+constexpr unsigned kBarrierSpinLimit = 40u * 1000u * 1000u;  // x >= 64 ns: > 2.5 s
+constexpr int kStatusTimeout = 4;
+
+// Grid-wide barrier for a co-resident (cooperative) grid: sense reversal
+// on a generation counter.  The wait is bounded: when it runs out, the
+// status word records a timeout and every CTA leaves the kernel at its next
+// barrier.  Returns false when the kernel must stop.
+__device__ bool grid_sync(const Dev &d, unsigned nblocks, int *s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(d.barrier[1]);
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(d.barrier[0]);
+    cuda::atomic_ref<int, cuda::thread_scope_device> status(d.counters[CNT_STATUS]);
+    const unsigned g = gen.load(cuda::memory_order_acquire);
+    __threadfence();
+    int ok = 1;
+    if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == nblocks - 1) {
+      cnt.store(0u, cuda::memory_order_relaxed);
+      gen.fetch_add(1u, cuda::memory_order_release);
+    } else {
+      unsigned it = 0;
+      while (gen.load(cuda::memory_order_acquire) == g) {
+        if (++it > kBarrierSpinLimit) {
+          status.fetch_or(kStatusTimeout, cuda::memory_order_relaxed);
+          ok = 0;
+          break;
+        }
+        if (it > 2048) __nanosleep(64);  // spin first: most waits are short
+      }
+    }
+    __threadfence();
+    if (status.load(cuda::memory_order_relaxed) & kStatusTimeout) ok = 0;
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+__global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rules R) {
+  extern __shared__ __align__(16) float msm[];
+  __shared__ BirthSmem S;
+  __shared__ float s_scale[kMutRows];
+  __shared__ int s_flag;
+  const unsigned nb = gridDim.x;
+  const int g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  ph_move_apply_eat(d, R, L.A, g0, gs);
+  if (!grid_sync(d, nb, &s_flag)) return;
+  ph_attack_claim(d, R, g0, gs);
+  if (!grid_sync(d, nb, &s_flag)) return;
+  ph_attack_gain(d, R, g0, gs);
+  if (!grid_sync(d, nb, &s_flag)) return;
+  ph_metab_death(d, R, g0, gs);
+  if (!grid_sync(d, nb, &s_flag)) return;
+  ph_birth_claim(d, R, g0, gs);
+  if (!grid_sync(d, nb, &s_flag)) return;
+  ph_birth_assign(d, blockIdx.x, gridDim.x, S);
+  if (!grid_sync(d, nb, &s_flag)) return;
+  ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale);
+  ph_regrow(d, R, g0, gs);
+  ph_compact_count(d, blockIdx.x, gridDim.x, S.sh);
+  if (!grid_sync(d, nb, &s_flag)) return;
+  ph_compact_scatter(d, blockIdx.x, gridDim.x, S.sh);
+  if (blockIdx.x == gridDim.x - 1) ph_finish(d, R);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
 cudaError_t launch_compact(const Dev &d, cudaStream_t s) {
   const int tiles = compact_tiles(d.total_slots);
   k_compact_count<<<tiles, 256, 0, s>>>(d);
@@ -605,14 +736,43 @@ cudaError_t launch_compact(const Dev &d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t env_prepare(const Layout &L) {
+cudaError_t env_prepare(const Layout &L, EnvGrid *g) {
   const size_t smem = mutate_smem_bytes(L);
-  return cudaFuncSetAttribute((const void *)k_mutate, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  cudaError_t e = cudaFuncSetAttribute((const void *)k_mutate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute((const void *)k_env_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, coop = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_env_persistent, 1024,
+                                                         smem)) != cudaSuccess)
+    return e;
+  // one CTA per SM: fewer arrivals on the barrier counter
+  g->persistent_blocks = (coop && per_sm >= 1) ? g->sms : 0;
+  return cudaSuccess;
 }
 
+// The step's phases after the policy kernel, ending with the alive list of
+// the next step.
 cudaError_t launch_env_phases(const Dev &d, const Layout &L, const Rules &R, const EnvGrid &g,
                               cudaStream_t s) {
+  const size_t msmem = mutate_smem_bytes(L);
+  if (g.persistent_blocks > 0 && g.use_persistent) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g.persistent_blocks);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = msmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_env_persistent, d, L, R);
+  }
   const int T = 256;
   k_move_apply_eat<<<g.slot_blocks, T, 0, s>>>(d, R, L.A);
   k_attack_claim<<<g.slot_blocks, T, 0, s>>>(d, R);
@@ -620,10 +780,12 @@ cudaError_t launch_env_phases(const Dev &d, const Layout &L, const Rules &R, con
   k_metab_death<<<g.slot_blocks, T, 0, s>>>(d, R);
   k_birth_claim<<<g.slot_blocks, T, 0, s>>>(d, R);
   k_birth_assign<<<d.n_envs, 1024, 0, s>>>(d);
-  k_mutate<<<g.birth_blocks, 256, mutate_smem_bytes(L), s>>>(d, L, R);
+  k_mutate<<<g.birth_blocks, 256, msmem, s>>>(d, L, R);
   k_regrow<<<g.cell_blocks, T, 0, s>>>(d, R);
   k_finish<<<1, 1024, 0, s>>>(d, R);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_compact(d, s);
 }
 
 }  // namespace eco

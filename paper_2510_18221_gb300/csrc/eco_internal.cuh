@@ -148,6 +148,7 @@ struct Dev {
   float *logits;
   int32_t *alive_list;
   int32_t *tile_counts;  // [compact tiles] alive slots per tile of 4096
+  unsigned *barrier;     // [2] grid barrier of the persistent form: count, generation
   int32_t *counters;    // [0] n_alive, [1] n_births, [2] status, [3..] spare
   int2 *births;         // (parent global, child global)
   int32_t *free_list;   // per env: slot_off + rank

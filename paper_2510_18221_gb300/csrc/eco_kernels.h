@@ -24,14 +24,18 @@ cudaError_t policy_launch(const PolicyLaunch &pl, const Dev &d, const Layout &L,
 
 // Environment phases (eco_env.cu).
 struct EnvGrid {
-  int sms;          // SM count
-  int slot_blocks;  // blocks of 256 threads for per-agent phases
-  int cell_blocks;  // blocks of 256 threads for per-cell phases
-  int birth_blocks; // CTAs of the mutation kernel
+  int sms;                // SM count
+  int slot_blocks;        // blocks of 256 threads for per-agent phases
+  int cell_blocks;        // blocks of 256 threads for per-cell phases
+  int birth_blocks;       // CTAs of the mutation kernel
+  int persistent_blocks;  // co-resident CTAs of the persistent form (0: unavailable)
+  int use_persistent;     // run the environment phases as one persistent kernel
 };
-int compact_tiles(int total_slots);
+__host__ __device__ int compact_tiles(int total_slots);
+// Alive list of the current state (ascending slots) and its count.
 cudaError_t launch_compact(const Dev &d, cudaStream_t s);
-cudaError_t env_prepare(const Layout &L);
+// Shared-memory attributes and the persistent form's grid size.
+cudaError_t env_prepare(const Layout &L, EnvGrid *g);
 cudaError_t launch_env_phases(const Dev &d, const Layout &L, const Rules &R, const EnvGrid &g,
                               cudaStream_t s);
 

@@ -53,7 +53,7 @@ class eco_config(ctypes.Structure):
         ("e_init", ctypes.c_int32), ("e_metab", ctypes.c_int32),
         ("e_food", ctypes.c_int32), ("e_repro", ctypes.c_int32),
         ("attack_num", ctypes.c_int32), ("attack_den", ctypes.c_int32),
-        ("policy_variant", ctypes.c_int32),
+        ("policy_variant", ctypes.c_int32), ("launch_mode", ctypes.c_int32),
     ]
 
 
@@ -103,6 +103,7 @@ def lib() -> ctypes.CDLL:
         L.eco_policy_variant_name.argtypes = [ctypes.c_int32]
         L.eco_policy_variant_name.restype = ctypes.c_char_p
         L.eco_policy_only.argtypes = [H, ctypes.c_int32]
+        L.eco_launch_mode.argtypes = [H, _i32p, _i32p]
         L.eco_policy_bytes.argtypes = [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.eco_move_claims_noalloc.argtypes = [
             ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32,
@@ -190,6 +191,12 @@ def eco_policy_variants(h):
     return c.value, ch.value
 
 
+def eco_launch_mode(h):
+    m, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().eco_launch_mode(h, ctypes.byref(m), ctypes.byref(b)), h)
+    return m.value, b.value
+
+
 def eco_policy_variant_name(k: int) -> str:
     return lib().eco_policy_variant_name(int(k)).decode()
 
@@ -219,7 +226,7 @@ _SHARED = ("patch_k", "n_scalars", "hidden", "n_actions", "precision", "flags", 
            "e_repro", "attack_num", "attack_den")
 
 
-def make_config(envs: Sequence[dict], policy_variant: int = 0):
+def make_config(envs: Sequence[dict], policy_variant: int = 0, launch_mode: int = 0):
     """An eco_config for environments sharing rules and MLP shape (the
     per-environment arrays are returned too, to keep them alive)."""
     envs = list(envs)
@@ -244,19 +251,19 @@ def make_config(envs: Sequence[dict], policy_variant: int = 0):
         sigma=w0["sigma"], food_density=w0["food_density"], regrow_p=w0["regrow_p"],
         wall_density=w0["wall_density"], e_init=w0["e_init"], e_metab=w0["e_metab"],
         e_food=w0["e_food"], e_repro=w0["e_repro"], attack_num=w0["attack_num"],
-        attack_den=w0["attack_den"], policy_variant=policy_variant)
+        attack_den=w0["attack_den"], policy_variant=policy_variant, launch_mode=launch_mode)
     return cfg, (side, slots, alive, seed)
 
 
 class Env:
     """One or more environments advanced together on the current GPU."""
 
-    def __init__(self, envs, policy_variant: int = 0, stream=None):
+    def __init__(self, envs, policy_variant: int = 0, stream=None, launch_mode: int = 0):
         import torch
         if isinstance(envs, dict):
             envs = [envs]
         self.envs = list(envs)
-        self.cfg, self._keep = make_config(self.envs, policy_variant)
+        self.cfg, self._keep = make_config(self.envs, policy_variant, launch_mode)
         self.P, self.D = eco_param_count(self.cfg)
         self.A = self.cfg.n_actions
         self.H = self.cfg.hidden
@@ -299,6 +306,10 @@ class Env:
 
     def policy_bytes(self):
         return eco_policy_bytes(self.h)
+
+    def launch_mode(self):
+        """(0 persistent / 1 one kernel per phase, persistent CTAs)."""
+        return eco_launch_mode(self.h)
 
     def variants(self):
         return eco_policy_variants(self.h)

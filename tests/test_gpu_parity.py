@@ -156,3 +156,37 @@ def test_batched_equals_single_and_oracle():
     batch2.close()
     for s in singles:
         s.close()
+
+
+def test_launch_forms_bit_identical():
+    """The persistent cooperative kernel and one kernel per phase run the
+    same phase functions: every array and statistic must match."""
+    from paper_2510_18221_gb300 import eco
+    envs = [workloads.scaled("mid", s, n, k, seed=40 + i, precision="bf16", e_init=185)
+            for i, (s, n, k) in enumerate([(64, 600, 500), (128, 2048, 1500), (32, 300, 250)])]
+    a = eco.Env(envs, launch_mode=0)
+    b = eco.Env(envs, launch_mode=1)
+    a.reset()
+    b.reset()
+    a.step(1)
+    b.step(1)
+    assert b.launch_mode()[0] == 1
+    assert a.launch_mode()[0] == 0 and a.launch_mode()[1] > 0   # GB300 supports the persistent form
+    for t in range(6):
+        a.step(5)
+        b.step(5)
+        for e in range(len(envs)):
+            sa, sb = a.read_state(e), b.read_state(e)
+            for k in harness.STATE_KEYS:
+                assert np.array_equal(sa[k], sb[k]), (t, e, k)
+            assert a.stats()[e] == b.stats()[e]
+            assert np.array_equal(a.read_params(e), b.read_params(e))
+    assert sum(s["births"] for s in a.stats()) > 0
+    a.close()
+    b.close()
+
+
+def test_per_phase_launch_form_lockstep():
+    w = workloads.scaled("mid", 128, 2048, 1500, precision="fp8", e_init=190)
+    rep = _run(w, 15, launch_mode=1)
+    assert rep["births"] > 10
