@@ -34,6 +34,8 @@ FP32, BF16, FP8 = 0, 1, 2
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp8": FP8}
 
 AUTO_EAT, ROTATE_OBS, CANCEL_ALL, GREEDY = 1, 2, 4, 8
+PLAIN, PAPER_FORM = 0, 1
+POLICY_FORMS = {"plain": PLAIN, "paper": PAPER_FORM}
 FLAG_NAMES = {"auto_eat": AUTO_EAT, "rotate_obs": ROTATE_OBS,
               "cancel_all": CANCEL_ALL, "greedy": GREEDY}
 
@@ -66,6 +68,7 @@ class Config(ctypes.Structure):
         ("e_init", ctypes.c_int32), ("e_metab", ctypes.c_int32),
         ("e_food", ctypes.c_int32), ("e_repro", ctypes.c_int32),
         ("attack_num", ctypes.c_int32), ("attack_den", ctypes.c_int32),
+        ("policy_form", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
     ]
 
 
@@ -114,6 +117,7 @@ def lib():
             L.orc_fp8_row_scale.restype = ctypes.c_float
             cfgp = ctypes.POINTER(Config)
             stp = ctypes.POINTER(State)
+            L.orc_param_count_shape.argtypes = [ctypes.c_int] * 7
             L.orc_obs_dim.argtypes = [cfgp]
             L.orc_n_params.argtypes = [cfgp]
             L.orc_reset.argtypes = [cfgp, stp]
@@ -161,6 +165,13 @@ def normals4(words):
     return [float(v) for v in n]
 
 
+def param_count_shape(D, H, A, L, ns, out_bias, temp) -> int:
+    """Parameter count of a policy with D inputs, ns sensors (one input
+    bias each), L hidden H -> H layers, A actions, an optional head bias
+    and an optional temperature parameter."""
+    return int(lib().orc_param_count_shape(D, H, A, L, ns, int(out_bias), int(temp)))
+
+
 def threshold(p: float) -> int:
     return int(lib().orc_threshold(float(p)))
 
@@ -205,7 +216,10 @@ def make_config(cfg: dict) -> Config:
         food_density=cfg["food_density"], regrow_p=cfg["regrow_p"],
         wall_density=cfg["wall_density"], e_init=cfg["e_init"],
         e_metab=cfg["e_metab"], e_food=cfg["e_food"], e_repro=cfg["e_repro"],
-        attack_num=cfg["attack_num"], attack_den=cfg["attack_den"])
+        attack_num=cfg["attack_num"], attack_den=cfg["attack_den"],
+        policy_form=POLICY_FORMS[cfg.get("policy_form", "plain")]
+        if isinstance(cfg.get("policy_form", "plain"), str) else int(cfg["policy_form"]),
+        n_hidden=cfg.get("n_hidden", 1))
 
 
 class Oracle:

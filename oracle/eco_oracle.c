@@ -101,7 +101,15 @@ typedef struct {
   float regrow_p;      /* per-step Bernoulli regrowth probability        */
   float wall_density;  /* Bernoulli wall probability                     */
   int32_t e_init, e_metab, e_food, e_repro, attack_num, attack_den;
+  int32_t policy_form; /* ORC_PLAIN or ORC_PAPER_FORM (see the layout below) */
+  int32_t n_hidden;    /* paper form: hidden H -> H layers (plain form: 1)  */
 } orc_config;
+
+enum {
+  ORC_PLAIN = 0,      /* tanh MLP D -> H -> H -> A with biases everywhere   */
+  ORC_PAPER_FORM = 1  /* Sec. 3.3: per-sensor input linears summed, ReLU,
+                         L hidden layers, unbiased head, temperature       */
+};
 
 typedef struct {
   uint8_t *food;       /* [L*L] 0/1                                      */
@@ -139,28 +147,86 @@ typedef struct {
 
 /* ------------------------------------------------------------------------ */
 /* Parameter layout (logical order).  Sec. 3.3: a per-agent MLP.             */
-/* W1 [H][D] row-major, b1 [H], W2 [H][H], b2 [H], W3 [A][H], b3 [A].        */
+/*   W_in [H][D] row-major, then one bias vector [H] per sensor (the        */
+/*   paper's separate per-sensor input linears, whose outputs are summed:   */
+/*   the weights of all sensors together form W_in), then L hidden layers   */
+/*   W_l [H][H], b_l [H], then the head W_out [A][H], its bias b_out [A]     */
+/*   (plain form only), then the log-temperature tau (paper form only).     */
+/* Plain form: one sensor, L = 1, tanh, biased head, no temperature         */
+/* (= W1, b1, W2, b2, W3, b3).  Paper form: sensors vision / internal       */
+/* (+ compass with 8 scalars), L = n_hidden, ReLU, unbiased head, tau.      */
 /* ------------------------------------------------------------------------ */
 
 int orc_obs_dim(const orc_config *c) {
   return 3 * c->patch_k * c->patch_k + c->n_scalars;
 }
 
-int orc_n_params(const orc_config *c) {
-  int D = orc_obs_dim(c), H = c->hidden, A = c->n_actions;
-  return H * D + H + H * H + H + A * H + A;
+typedef struct {
+  int D, H, A, L;       /* inputs, hidden width, actions, hidden layers     */
+  int ns;               /* sensors, each with its own input bias            */
+  int relu, out_bias, temp;
+  int oWin, obin, oWh, oWout, obout, otau, P;
+} orc_shape;
+
+/* Parameter count for explicit shape numbers (the paper's table of network
+ * sizes is written in these terms). */
+int orc_param_count_shape(int D, int H, int A, int L, int ns, int out_bias, int temp) {
+  return H * D + ns * H + L * (H * H + H) + A * H + (out_bias ? A : 0) + (temp ? 1 : 0);
 }
 
-/* Offsets of the six parameter blocks. */
-static void param_offsets(const orc_config *c, int *oW1, int *ob1, int *oW2,
-                          int *ob2, int *oW3, int *ob3) {
-  int D = orc_obs_dim(c), H = c->hidden, A = c->n_actions;
-  *oW1 = 0;
-  *ob1 = H * D;
-  *oW2 = *ob1 + H;
-  *ob2 = *oW2 + H * H;
-  *oW3 = *ob2 + H;
-  *ob3 = *oW3 + A * H;
+static void shape_of(const orc_config *c, orc_shape *s) {
+  s->D = orc_obs_dim(c);
+  s->H = c->hidden;
+  s->A = c->n_actions;
+  if (c->policy_form == ORC_PAPER_FORM) {
+    s->L = c->n_hidden;
+    s->ns = c->n_scalars >= 8 ? 3 : 2;
+    s->relu = 1;
+    s->out_bias = 0;
+    s->temp = 1;
+  } else {
+    s->L = 1;
+    s->ns = 1;
+    s->relu = 0;
+    s->out_bias = 1;
+    s->temp = 0;
+  }
+  s->oWin = 0;
+  s->obin = s->H * s->D;
+  s->oWh = s->obin + s->ns * s->H; /* layer l: W at oWh + l*(H*H+H), b after */
+  s->oWout = s->oWh + s->L * (s->H * s->H + s->H);
+  s->obout = s->oWout + s->A * s->H;
+  s->otau = s->obout + (s->out_bias ? s->A : 0);
+  s->P = s->otau + (s->temp ? 1 : 0);
+}
+
+int orc_n_params(const orc_config *c) {
+  orc_shape s;
+  shape_of(c, &s);
+  return s.P;
+}
+
+/* Is parameter p a weight (part of W_in, a hidden W_l or W_out)? */
+static int is_weight(const orc_shape *s, int p) {
+  int l;
+  if (p < s->obin) return 1;
+  for (l = 0; l < s->L; l++) {
+    int w0 = s->oWh + l * (s->H * s->H + s->H);
+    if (p >= w0 && p < w0 + s->H * s->H) return 1;
+  }
+  return p >= s->oWout && p < s->obout;
+}
+
+/* Number of inputs of the sensor that input j of W_in belongs to: the
+ * patch (3k^2), the compass one-hot (4 inputs, 8-scalar form), and the
+ * internal scalars (energy and the reserved zeros).  The plain form treats
+ * the whole observation as one input. */
+static int sensor_fan_in(const orc_config *c, const orc_shape *s, int j) {
+  int patch = 3 * c->patch_k * c->patch_k;
+  if (c->policy_form != ORC_PAPER_FORM) return s->D;
+  if (j < patch) return patch;
+  if (c->n_scalars >= 8 && j >= patch + 1 && j < patch + 5) return 4;
+  return c->n_scalars >= 8 ? c->n_scalars - 4 : c->n_scalars;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -357,28 +423,36 @@ static int cmp_i32(const void *a, const void *b) {
   return (x > y) - (x < y);
 }
 
-/* Initial parameters of one founder: weight p ~ N(0,1) / sqrt(fan_in) drawn
- * from stream W_INIT at counter (slot, p/4), biases zero. */
+/* Initial parameters of one founder (Sec. 3.3: Kaiming initialisation, zero
+ * biases): weight p = N(0,1) * sqrt(gain / fan_in), the normal drawn from
+ * stream W_INIT at counter (slot, p/4); gain 1 in the plain (tanh) form and
+ * 2 in the paper (ReLU) form; fan_in is the input count of the weight's
+ * sensor (W_in) or H (hidden layers and head).  Biases and the
+ * log-temperature start at zero. */
 void orc_init_params(const orc_config *c, int32_t slot, float *row) {
-  int D = orc_obs_dim(c), H = c->hidden, A = c->n_actions;
-  int P = orc_n_params(c);
-  int oW1, ob1, oW2, ob2, oW3, ob3, p;
+  orc_shape s;
+  int p;
   uint32_t r[4];
   double n[4];
-  param_offsets(c, &oW1, &ob1, &oW2, &ob2, &oW3, &ob3);
-  (void)A;
-  for (p = 0; p < P; p++) {
+  double gain;
+  shape_of(c, &s);
+  gain = s.relu ? 2.0 : 1.0;
+  for (p = 0; p < s.P; p++) {
     double fan_in;
     if ((p & 3) == 0) {
       draw4(c, ST_W_INIT, (uint32_t)slot, (uint32_t)(p >> 2), 0u, r);
       orc_normals4(r, n);
     }
-    if (p >= ob1 && p < oW2) { row[p] = 0.0f; continue; }
-    if (p >= ob2 && p < oW3) { row[p] = 0.0f; continue; }
-    if (p >= ob3) { row[p] = 0.0f; continue; }
-    if (p < ob1) fan_in = (double)D;
-    else fan_in = (double)H; /* W2 and W3 both read H inputs */
-    row[p] = (float)(n[p & 3] / sqrt(fan_in));
+    if (!is_weight(&s, p)) {
+      row[p] = 0.0f;
+      continue;
+    }
+    if (p < s.obin) fan_in = (double)sensor_fan_in(c, &s, p % s.D);
+    else fan_in = (double)s.H;
+    if (gain == 1.0)
+      row[p] = (float)(n[p & 3] / sqrt(fan_in));
+    else
+      row[p] = (float)(n[p & 3] * sqrt(gain / fan_in));
   }
 }
 
@@ -487,8 +561,11 @@ void orc_observe(const orc_config *c, const orc_state *s, int32_t slot, double *
 }
 
 /* ------------------------------------------------------------------------ */
-/* Policy (Sec. 3.3): h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2),           */
-/* logits = W3 h2 + b3; action sampled from softmax(logits) by Gumbel-max.   */
+/* Policy (Sec. 3.3).  Plain form: h1 = tanh(W1 x + b1),                  */
+/* h2 = tanh(W2 h1 + b2), logits = W3 h2 + b3.  Paper form: h0 =             */
+/* ReLU(sum over sensors of (W_s x_s + b_s)), L layers h = ReLU(W_l h + b_l), */
+/* logits = (W_out h) / T with T = exp(tau).  The action is sampled from     */
+/* softmax(logits) by Gumbel-max.                                            */
 /* ------------------------------------------------------------------------ */
 
 /* The parameters the policy actually multiplies with, in FP64:
@@ -497,25 +574,32 @@ void orc_observe(const orc_config *c, const orc_state *s, int32_t slot, double *
  *   FP8 form:  every weight row r of each layer quantised as
  *              s_r * e4m3(w / s_r), biases FP32. */
 void orc_effective_params(const orc_config *c, const float *m, int use_master, double *w) {
-  int D = orc_obs_dim(c), H = c->hidden, A = c->n_actions, P = orc_n_params(c);
-  int oW1, ob1, oW2, ob2, oW3, ob3, p, row;
-  param_offsets(c, &oW1, &ob1, &oW2, &ob2, &oW3, &ob3);
-  for (p = 0; p < P; p++) w[p] = (double)m[p];
+  orc_shape s;
+  int p, row;
+  shape_of(c, &s);
+  for (p = 0; p < s.P; p++) w[p] = (double)m[p];
   if (use_master || c->precision == ORC_FP32) return;
   if (c->precision == ORC_BF16) {
-    for (p = 0; p < P; p++) {
-      int is_bias = (p >= ob1 && p < oW2) || (p >= ob2 && p < oW3) || p >= ob3;
-      if (!is_bias) w[p] = orc_bf16_value(orc_bf16_rne(m[p]));
-    }
+    for (p = 0; p < s.P; p++)
+      if (is_weight(&s, p)) w[p] = orc_bf16_value(orc_bf16_rne(m[p]));
     return;
   }
-  /* FP8: rows of W1 have D entries, rows of W2 and W3 have H entries */
-  for (row = 0; row < H + H + A; row++) {
+  /* FP8: rows of W_in have D entries; rows of the hidden layers and of
+   * the head have H entries */
+  for (row = 0; row < s.H + s.L * s.H + s.A; row++) {
     int start, n, j;
     float sc;
-    if (row < H) { start = oW1 + row * D; n = D; }
-    else if (row < 2 * H) { start = oW2 + (row - H) * H; n = H; }
-    else { start = oW3 + (row - 2 * H) * H; n = H; }
+    if (row < s.H) {
+      start = s.oWin + row * s.D;
+      n = s.D;
+    } else if (row < s.H + s.L * s.H) {
+      int l = (row - s.H) / s.H, o = (row - s.H) % s.H;
+      start = s.oWh + l * (s.H * s.H + s.H) + o * s.H;
+      n = s.H;
+    } else {
+      start = s.oWout + (row - s.H - s.L * s.H) * s.H;
+      n = s.H;
+    }
     sc = orc_fp8_row_scale(m + start, n);
     for (j = 0; j < n; j++) {
       float q = m[start + j] / sc; /* IEEE binary32 division */
@@ -524,25 +608,41 @@ void orc_effective_params(const orc_config *c, const float *m, int use_master, d
   }
 }
 
-/* Forward pass of one agent's MLP on observation x (FP64). */
+static double activate(const orc_shape *s, double v) {
+  if (s->relu) return v > 0.0 ? v : 0.0;
+  return tanh(v);
+}
+
+/* Forward pass of one agent's MLP on observation x (FP64).  The returned
+ * logits already carry the temperature (logit / T with T = exp(tau)), so
+ * the action is sampled from softmax(logits). */
 void orc_mlp(const orc_config *c, const double *w, const double *x, double *logits) {
-  int D = orc_obs_dim(c), H = c->hidden, A = c->n_actions;
-  int oW1, ob1, oW2, ob2, oW3, ob3, o, j;
-  double h1[512], h2[512];
-  param_offsets(c, &oW1, &ob1, &oW2, &ob2, &oW3, &ob3);
-  for (o = 0; o < H; o++) {
-    double acc = w[ob1 + o];
-    for (j = 0; j < D; j++) acc += w[oW1 + o * D + j] * x[j];
-    h1[o] = tanh(acc);
+  orc_shape s;
+  int o, j, l, k;
+  double ha[512], hb[512];
+  double *h = ha, *h2 = hb, *tmp;
+  shape_of(c, &s);
+  for (o = 0; o < s.H; o++) {
+    double acc = 0.0;
+    for (k = 0; k < s.ns; k++) acc += w[s.obin + k * s.H + o];  /* summed sensor biases */
+    for (j = 0; j < s.D; j++) acc += w[s.oWin + o * s.D + j] * x[j];
+    h[o] = activate(&s, acc);
   }
-  for (o = 0; o < H; o++) {
-    double acc = w[ob2 + o];
-    for (j = 0; j < H; j++) acc += w[oW2 + o * H + j] * h1[j];
-    h2[o] = tanh(acc);
+  for (l = 0; l < s.L; l++) {
+    int oW = s.oWh + l * (s.H * s.H + s.H), ob = oW + s.H * s.H;
+    for (o = 0; o < s.H; o++) {
+      double acc = w[ob + o];
+      for (j = 0; j < s.H; j++) acc += w[oW + o * s.H + j] * h[j];
+      h2[o] = activate(&s, acc);
+    }
+    tmp = h;
+    h = h2;
+    h2 = tmp;
   }
-  for (o = 0; o < A; o++) {
-    double acc = w[ob3 + o];
-    for (j = 0; j < H; j++) acc += w[oW3 + o * H + j] * h2[j];
+  for (o = 0; o < s.A; o++) {
+    double acc = s.out_bias ? w[s.obout + o] : 0.0;
+    for (j = 0; j < s.H; j++) acc += w[s.oWout + o * s.H + j] * h[j];
+    if (s.temp) acc = acc * exp(-w[s.otau]);
     logits[o] = acc;
   }
 }
@@ -559,6 +659,7 @@ int orc_policy(const orc_config *c, const orc_state *s, int use_master, double t
   int64_t t = *s->step;
   int bad = 0;
   if (A > 16 || c->hidden > 512 || c->e_repro <= 0) return -1;
+  if (c->policy_form == ORC_PAPER_FORM && (c->n_hidden < 1 || c->n_hidden > 8)) return -1;
 #pragma omp parallel
   {
     double *w = (double *)malloc(sizeof(double) * (size_t)P);

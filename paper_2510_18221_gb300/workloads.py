@@ -48,7 +48,15 @@ LARGE = dict(MID, name="large-2048x2048-262144slots-683-128-128-9-fp8",
              side=2048, slots=262144, init_alive=200000, patch_k=15, hidden=128,
              precision="fp8", steps=500)
 
-WORKLOADS = {"small": SMALL, "mid": MID, "paper": PAPER, "large": LARGE}
+# The paper's own policy form (Sec. 3.3) on the paper-scale world: separate
+# input linears for the vision patch, the internal scalars and the compass,
+# summed; two hidden ReLU layers of 64; an unbiased head; an evolvable
+# softmax temperature; weights streamed as BF16.
+PAPER_FORM = dict(PAPER, name="paperform-1024x1024-65536slots-RCV-2x64-bf16",
+                  policy_form="paper", n_hidden=2)
+
+WORKLOADS = {"small": SMALL, "mid": MID, "paper": PAPER, "large": LARGE,
+             "paperform": PAPER_FORM}
 
 
 def get(key: str, **overrides) -> dict:
