@@ -65,6 +65,16 @@ extern "C" {
 #define ECO_CANCEL_ALL 4 /* the paper's rule: every contested move fails   */
 #define ECO_GREEDY 8     /* argmax of the logits instead of sampling       */
 
+/* Policy forms.  Plain: h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2),
+ * logits = W3 h2 + b3 (the workloads' MLP).  Paper (Sec. 3.3): each sensor
+ * (vision patch, internal scalars, compass one-hot) has its own input linear
+ * layer; their outputs are summed and passed through ReLU, then n_hidden
+ * ReLU layers of width H, then an unbiased linear head; logits are divided
+ * by the evolvable temperature exp(tau).  Kaiming initialisation, zero
+ * biases and tau. */
+#define ECO_POLICY_PLAIN 0
+#define ECO_POLICY_PAPER 1
+
 /* Action codes: 0 stay, 1 north, 2 south, 3 east, 4 west, 5 attack;
  * nine-action sets add 6 turn-left, 7 turn-right, 8 eat. */
 
@@ -102,6 +112,9 @@ typedef struct {
                                     cooperative kernel when the device
                                     supports it, 1 = one kernel per phase
                                     (identical results)                     */
+  int32_t policy_form;           /* ECO_POLICY_PLAIN or ECO_POLICY_PAPER     */
+  int32_t n_hidden;              /* paper form: hidden H -> H layers (1..4);
+                                    the plain form ignores it (one layer)   */
 } eco_config;
 
 /* Statistics, one record per environment (App. E measurement API).
@@ -196,8 +209,11 @@ int eco_write_params(eco_handle *h, int32_t env, int32_t slot0, int32_t n, const
 
 /* Streamed copy of slots [slot0, slot0 + n), logical order: BF16 codes as
  * uint16 [n][P] or e4m3 codes as uint8 [n][P] (bias positions hold the
- * code of 0), plus for FP8 the row scales [n][2H + A] (rows of W1, W2,
- * W3).  ECO_EINVAL for the FP32 precision.  Synchronises. */
+ * code of 0), plus for FP8 the row scales [n][H + Lh*H + A], Lh the
+ * number of hidden layers (1 in the plain form, n_hidden in the paper
+ * form): the output rows of W_in, of each hidden layer, then of the head.
+ * row_scales must hold that many floats per slot.  ECO_EINVAL for the
+ * FP32 precision.  Synchronises. */
 int eco_read_streamed(eco_handle *h, int32_t env, int32_t slot0, int32_t n,
                       void *codes, float *row_scales);
 

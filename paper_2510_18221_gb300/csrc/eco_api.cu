@@ -94,6 +94,12 @@ static int validate(const eco_config *c, char *msg, size_t n) {
     return snprintf(msg, n, "bad energy constants"), ECO_EINVAL;
   if (!(c->sigma >= 0.0f) || !std::isfinite(c->sigma)) return snprintf(msg, n, "bad sigma"), ECO_EINVAL;
   if (c->launch_mode < 0 || c->launch_mode > 1) return snprintf(msg, n, "launch_mode must be 0 or 1"), ECO_EINVAL;
+  if (c->policy_form != ECO_POLICY_PLAIN && c->policy_form != ECO_POLICY_PAPER)
+    return snprintf(msg, n, "bad policy_form"), ECO_EINVAL;
+  if (c->policy_form == ECO_POLICY_PAPER && (c->n_hidden < 1 || c->n_hidden > 4))
+    return snprintf(msg, n, "n_hidden must be in [1, 4] for the paper form"), ECO_EINVAL;
+  if (3 * c->patch_k * c->patch_k + c->n_scalars < c->hidden)
+    return snprintf(msg, n, "observation smaller than the hidden width"), ECO_EINVAL;
   if (c->policy_variant < 0 || c->policy_variant > policy_variant_count())
     return snprintf(msg, n, "policy_variant out of range"), ECO_EINVAL;
   long long cells = 0, slots = 0;
@@ -116,23 +122,39 @@ static Layout make_layout(const eco_config *c) {
   L.D = 3 * c->patch_k * c->patch_k + c->n_scalars;
   L.H = c->hidden;
   L.A = c->n_actions;
-  L.P = L.H * L.D + L.H + L.H * L.H + L.H + L.A * L.H + L.A;
-  const int nW = L.D * L.H + L.H * L.H + L.A * L.H;
-  const int nB = 2 * L.H + L.A;
-  // FP32 masters: W1 | W2 | W3 | biases (W sections are multiples of 4 floats)
+  L.patch = 3 * c->patch_k * c->patch_k;
+  L.n_scalars = c->n_scalars;
+  if (c->policy_form == ECO_POLICY_PAPER) {
+    L.L = c->n_hidden;
+    L.ns = c->n_scalars >= 8 ? 3 : 2;  // vision, internal (+ compass)
+    L.relu = 1;
+    L.out_bias = 0;
+    L.temp = 1;
+  } else {
+    L.L = 1;
+    L.ns = 1;
+    L.relu = 0;
+    L.out_bias = 1;
+    L.temp = 0;
+  }
+  L.nW = L.D * L.H + L.L * L.H * L.H + L.A * L.H;
+  L.nB = L.ns * L.H + L.L * L.H + (L.out_bias ? L.A : 0) + (L.temp ? 1 : 0);
+  L.P = L.nW + L.nB;
+  const int rows = L.H + L.L * L.H + L.A;  // FP8 row scales
+  // FP32 masters: W_in | hidden | W_out | biases (W sections are multiples of 4 floats)
   L.moff_w1 = 0;
   L.moff_w2 = L.D * L.H * 4;
-  L.moff_w3 = L.moff_w2 + L.H * L.H * 4;
-  L.moff_bias = nW * 4;
-  L.mstride = pad((int64_t)(nW + nB) * 4, 128);
+  L.moff_w3 = L.moff_w2 + L.L * L.H * L.H * 4;
+  L.moff_bias = L.nW * 4;
+  L.mstride = pad((int64_t)L.P * 4, 128);
   L.es = c->precision == ECO_FP32 ? 4 : (c->precision == ECO_BF16 ? 2 : 1);
   L.off_w1 = 0;
   L.off_w2 = L.D * L.H * L.es;
-  L.off_w3 = L.off_w2 + L.H * L.H * L.es;
+  L.off_w3 = L.off_w2 + L.L * L.H * L.H * L.es;
   const int wend = L.off_w3 + L.A * L.H * L.es;
   L.off_scale = wend;
-  L.off_bias = (c->precision == ECO_FP8_E4M3) ? (int)(wend + pad(nB * 4, 16)) : wend;
-  L.stride = (c->precision == ECO_FP32) ? L.mstride : pad(L.off_bias + pad(nB * 4, 16), 128);
+  L.off_bias = (c->precision == ECO_FP8_E4M3) ? (int)(wend + pad(rows * 4, 16)) : wend;
+  L.stride = (c->precision == ECO_FP32) ? L.mstride : pad(L.off_bias + pad(L.nB * 4, 16), 128);
   return L;
 }
 
@@ -548,10 +570,8 @@ extern "C" int eco_policy_bytes(eco_handle *h, int64_t *bytes, int64_t *n_alive)
   CUDA_TRY(h, cudaMemcpyAsync(&n, h->d.counters + CNT_N_ALIVE, sizeof n, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   const Layout &L = h->L;
-  const int64_t nW = (int64_t)L.D * L.H + L.H * L.H + L.A * L.H;
-  const int64_t nB = 2 * L.H + L.A;
-  int64_t per = nW * L.es + nB * 4;
-  if (h->R.precision == ECO_FP8_E4M3) per += nB * 4;  // row scales
+  int64_t per = (int64_t)L.nW * L.es + (int64_t)L.nB * 4;
+  if (h->R.precision == ECO_FP8_E4M3) per += (int64_t)(L.H + L.L * L.H + L.A) * 4;  // row scales
   if (bytes) *bytes = per * n;
   if (n_alive) *n_alive = n;
   return ECO_OK;
@@ -670,19 +690,9 @@ extern "C" int eco_write_state(eco_handle *h, int32_t env, const eco_state_view 
 // Logical index of every master element of the tiled block (host copy of
 // the layout map), or -1 for padding.
 static void logical_map(const Layout &L, std::vector<int> &map) {
-  const int D = L.D, H = L.H, A = L.A;
   const int per = (int)(L.mstride / 4);
   map.assign(per, -1);
-  int q = 0;
-  for (int j = 0; j < D; ++j)
-    for (int o = 0; o < H; ++o) map[q++] = o * D + j;
-  for (int j = 0; j < H; ++j)
-    for (int o = 0; o < H; ++o) map[q++] = D * H + H + o * H + j;
-  for (int a = 0; a < A; ++a)
-    for (int j = 0; j < H; ++j) map[q++] = D * H + 2 * H + H * H + a * H + j;
-  for (int o = 0; o < H; ++o) map[q++] = D * H + o;
-  for (int o = 0; o < H; ++o) map[q++] = D * H + H + H * H + o;
-  for (int a = 0; a < A; ++a) map[q++] = D * H + 2 * H + H * H + A * H + a;
+  for (int q = 0; q < L.P; ++q) map[q] = layout_logical(L, q);
 }
 
 static int check_range(eco_handle *h, int32_t env, int32_t slot0, int32_t n) {
@@ -744,8 +754,8 @@ extern "C" int eco_read_streamed(eco_handle *h, int32_t env, int32_t slot0, int3
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   std::vector<int> map;
   logical_map(L, map);
-  const int nW = L.D * L.H + L.H * L.H + L.A * L.H;
-  const int nB = 2 * L.H + L.A;
+  const int nW = L.nW;
+  const int nB = L.H + L.L * L.H + L.A;  // row scales
   for (int i = 0; i < n; ++i) {
     const uint8_t *blk = buf.data() + (size_t)i * L.stride;
     if (codes) {

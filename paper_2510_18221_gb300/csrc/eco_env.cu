@@ -437,7 +437,8 @@ __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0,
   const int D = L.D, H = L.H, A = L.A;
   const int nb = d.counters[CNT_N_BIRTHS];
   const int tiles = H / kMutRows;
-  const int items = 2 * tiles + 1;
+  const int wtiles = (1 + L.L) * tiles;  // W_in, then each hidden layer
+  const int items = wtiles + 1;
   const uint32_t t = (uint32_t)d.step[0];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -451,13 +452,16 @@ __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0,
     const float *pm = d.master + (int64_t)pc.x * mper;
     float *cm = d.master + (int64_t)pc.y * mper;
     uint8_t *cq = d.wq + (int64_t)pc.y * L.stride;
-    if (it < 2 * tiles) {
-      const bool l1 = it < tiles;
-      const int o0 = (l1 ? it : it - tiles) * kMutRows;
+    if (it < wtiles) {
+      const int layer = it / tiles;  // 0: W_in; l + 1: hidden layer l
+      const bool l1 = layer == 0;
+      const int o0 = (it - layer * tiles) * kMutRows;
       const int nin = l1 ? D : H;
       const int rs = nin + 1;  // padded shared-memory row stride
-      const int lbase = l1 ? o0 * D : D * H + H + o0 * H;  // logical (o0, 0)
-      const int qbase = l1 ? 0 : D * H;                    // physical layer start
+      // logical (o0, 0) and the physical start of the layer
+      const int lbase = l1 ? o0 * D : D * H + L.ns * H + (layer - 1) * (H * H + H) + o0 * H;
+      const int qbase = l1 ? 0 : D * H + (layer - 1) * H * H;
+      const int srow = l1 ? 0 : H + (layer - 1) * H;  // first FP8 scale row of the layer
       const int nel = kMutRows * nin;
       const int g0 = lbase >> 2, g1 = (lbase + nel - 1) >> 2;
       for (int g = g0 + tid; g <= g1; g += nt) {
@@ -498,7 +502,7 @@ __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0,
           if (s == 0.0f) s = 1.0f;
           if (lane == 0) {
             s_scale[rr] = s;
-            reinterpret_cast<float *>(cq + L.off_scale)[(l1 ? 0 : H) + o0 + rr] = s;
+            reinterpret_cast<float *>(cq + L.off_scale)[srow + o0 + rr] = s;
           }
         }
         __syncthreads();
@@ -509,22 +513,13 @@ __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0,
       }
       __syncthreads();
     } else {
-      // W3 (output-major, logical order = physical order) and the biases
-      const int n3 = A * H, nbias = 2 * H + A;
-      const int l3 = D * H + 2 * H + H * H;  // logical start of W3
-      const int q3 = D * H + H * H;          // physical start of W3
-      const int qb = L.moff_bias / 4;
+      // the head (output-major) and every bias (and tau): master elements
+      // [q3, q3 + n3) and [nW, nW + nB)
+      const int n3 = A * H, nbias = L.nB;
+      const int q3 = D * H + L.L * H * H;  // physical start of W_out
       for (int e = tid; e < n3 + nbias; e += nt) {
-        int p, q;
-        if (e < n3) {
-          p = l3 + e;
-          q = q3 + e;
-        } else {
-          const int k = e - n3;
-          q = qb + k;
-          p = (k < H) ? D * H + k : (k < 2 * H) ? D * H + H + H * H + (k - H)
-                                               : D * H + 2 * H + H * H + A * H + (k - 2 * H);
-        }
+        const int q = e < n3 ? q3 + e : L.nW + (e - n3);
+        const int p = layout_logical(L, q);
         const U4 r = philox(t, lp, (uint32_t)(p >> 2), 0u, ed.seed, S_MUTATE);
         const float v = fmaf(R.sigma, normal_of(r, p & 3), pm[q]);
         cm[q] = v;
@@ -543,7 +538,7 @@ __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0,
           for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
           float s = __fdiv_rn(mx, 448.0f);
           if (s == 0.0f) s = 1.0f;
-          if (lane == 0) reinterpret_cast<float *>(cq + L.off_scale)[2 * H + a] = s;
+          if (lane == 0) reinterpret_cast<float *>(cq + L.off_scale)[H + L.L * H + a] = s;
           for (int j = lane; j < H; j += 32) cq[q3 + a * H + j] = e4m3_sat(__fdiv_rn(msm[a * H + j], s));
         }
       }

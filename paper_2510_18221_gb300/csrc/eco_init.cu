@@ -157,29 +157,12 @@ __global__ void __launch_bounds__(1024) k_place_assign(Dev d) {
   if (threadIdx.x == 0 && total != ed.init_alive) atomicOr(&d.counters[CNT_STATUS], 2);
 }
 
-// Logical parameter index of master element q (see eco_env.cu).
-__device__ __forceinline__ int master_logical_i(const Layout &L, int q) {
-  const int D = L.D, H = L.H, A = L.A;
-  const int n1 = D * H, n2 = H * H, n3 = A * H;
-  if (q < n1) {
-    const int j = q / H, o = q - j * H;
-    return o * D + j;
-  }
-  q -= n1;
-  if (q < n2) {
-    const int j = q / H, o = q - j * H;
-    return D * H + H + o * H + j;
-  }
-  q -= n2;
-  if (q < n3) return D * H + 2 * H + H * H + q;
-  return -1;  // biases and padding
-}
-
-// Founders' weights: N(0,1) / sqrt(fan_in) from stream W_INIT at counter
-// (local slot, p / 4), biases zero; every other slot all zero.
+// Founders' weights (Sec. 3.3: Kaiming initialisation, zero biases): weight
+// p = N(0,1) * sqrt(gain / fan_in) from stream W_INIT at counter (local
+// slot, p / 4), gain 1 for the plain (tanh) form and 2 for the paper (ReLU)
+// form; biases and tau zero; every other slot all zero.
 __global__ void k_init_params(Dev d, Layout L) {
   const int64_t per_slot = L.mstride / 4;
-  const int nW1 = L.D * L.H, nW = L.D * L.H + L.H * L.H + L.A * L.H;
   const int64_t total = (int64_t)d.total_slots * per_slot;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -188,11 +171,12 @@ __global__ void k_init_params(Dev d, Layout L) {
     const EnvDesc ed = d.env[d.env_of[s]];
     const int ls = s - ed.slot_off;
     float w = 0.0f;
-    if (ls < ed.init_alive && q < nW) {
-      const int p = master_logical_i(L, q);
+    if (ls < ed.init_alive && q < L.nW) {
+      const int p = layout_logical(L, q);
       const U4 r = philox((uint32_t)ls, (uint32_t)(p >> 2), 0u, 0u, ed.seed, S_W_INIT);
-      const float fan = (q < nW1) ? (float)L.D : (float)L.H;
-      w = __fdiv_rn(normal_of(r, p & 3), sqrtf(fan));
+      const float fan = (float)layout_fan_in(L, q);
+      const float n = normal_of(r, p & 3);
+      w = L.relu ? n * sqrtf(__fdiv_rn(2.0f, fan)) : __fdiv_rn(n, sqrtf(fan));
     }
     d.master[i] = w;
   }
@@ -201,9 +185,8 @@ __global__ void k_init_params(Dev d, Layout L) {
 // Streamed copy of slots [slot0, slot0 + n): BF16 elementwise (RNE), FP8 per
 // output row (scale = max|w| / 448, satfinite RNE codes), biases FP32.
 __global__ void k_requant_bf16(Dev d, Layout L, int slot0, int n) {
-  const int nW = L.D * L.H + L.H * L.H + L.A * L.H;
-  const int nB = 2 * L.H + L.A;
-  const int per = nW + nB;
+  const int nW = L.nW;
+  const int per = L.nW + L.nB;
   const int64_t total = (int64_t)n * per;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -220,8 +203,15 @@ __global__ void k_requant_bf16(Dev d, Layout L, int slot0, int n) {
 }
 
 __global__ void k_requant_fp8(Dev d, Layout L, int slot0, int n) {
-  const int H = L.H, A = L.A, rows = 2 * H + A;
+  const int H = L.H, rows = H + L.L * H + L.A;
   const int lane = threadIdx.x & 31;
+  // biases (and tau) are copied unchanged
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)n * L.nB;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int s = slot0 + (int)(i / L.nB), k = (int)(i % L.nB);
+    reinterpret_cast<float *>(d.wq + (int64_t)s * L.stride + L.off_bias)[k] =
+        d.master[(int64_t)s * (L.mstride / 4) + L.moff_bias / 4 + k];
+  }
   const int64_t warps = (int64_t)n * rows;
   for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < warps;
        w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -230,9 +220,14 @@ __global__ void k_requant_fp8(Dev d, Layout L, int slot0, int n) {
     const float *m = d.master + (int64_t)s * (L.mstride / 4);
     uint8_t *blk = d.wq + (int64_t)s * L.stride;
     int base, stride, cnt;
-    if (row < H) { base = row; stride = H; cnt = L.D; }
-    else if (row < 2 * H) { base = L.D * H + (row - H); stride = H; cnt = H; }
-    else { base = L.D * H + H * H + (row - 2 * H) * H; stride = 1; cnt = H; }
+    if (row < H) {  // W_in row o: elements (j, o), j < D
+      base = row; stride = H; cnt = L.D;
+    } else if (row < H + L.L * H) {  // hidden layer l, row o
+      const int l = (row - H) / H, o = (row - H) - l * H;
+      base = L.D * H + l * H * H + o; stride = H; cnt = H;
+    } else {  // head row a
+      base = L.D * H + L.L * H * H + (row - H - L.L * H) * H; stride = 1; cnt = H;
+    }
     float mx = 0.0f;
     for (int j = lane; j < cnt; j += 32) mx = fmaxf(mx, fabsf(m[base + j * stride]));
 #pragma unroll
@@ -243,10 +238,7 @@ __global__ void k_requant_fp8(Dev d, Layout L, int slot0, int n) {
       const int idx = base + j * stride;
       blk[idx] = (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(m[idx], sc), __NV_SATFINITE, __NV_E4M3);
     }
-    if (lane == 0) {
-      reinterpret_cast<float *>(blk + L.off_scale)[row] = sc;
-      reinterpret_cast<float *>(blk + L.off_bias)[row] = m[L.moff_bias / 4 + row];
-    }
+    if (lane == 0) reinterpret_cast<float *>(blk + L.off_scale)[row] = sc;
   }
 }
 
@@ -332,10 +324,10 @@ cudaError_t launch_requant(const Dev &d, const Layout &L, const Rules &R, int sl
                            cudaStream_t s) {
   if (R.precision == PREC_FP32 || n <= 0) return cudaSuccess;
   if (R.precision == PREC_BF16) {
-    const long long work = (long long)n * (L.D * L.H + L.H * L.H + L.A * L.H + 2 * L.H + L.A);
+    const long long work = (long long)n * (L.nW + L.nB);
     k_requant_bf16<<<grid_for(work, 256, 152 * 32), 256, 0, s>>>(d, L, slot0, n);
   } else {
-    const long long work = (long long)n * (2 * L.H + L.A) * 32;
+    const long long work = (long long)n * (L.H + L.L * L.H + L.A) * 32;
     k_requant_fp8<<<grid_for(work, 256, 152 * 32), 256, 0, s>>>(d, L, slot0, n);
   }
   return cudaGetLastError();

@@ -107,14 +107,81 @@ struct EnvDesc {
   uint32_t seed;
 };
 
+// Shape and block layout of one agent's parameters.  Logical order (the
+// order of eco_read_params): W_in [H][D], one input bias [H] per sensor,
+// L hidden layers (W_l [H][H], b_l [H]), W_out [A][H], b_out [A] (plain form
+// only), tau (paper form only).  The plain form is one sensor, L = 1, tanh,
+// a biased head and no temperature (W1 b1 W2 b2 W3 b3); the paper form
+// (Sec. 3.3) is 2-3 sensors, L hidden layers, ReLU, an unbiased head and
+// the log-temperature tau (logits are divided by exp(tau)).
+// Tiled block (streamed and master): W_in | W_1..W_L | W_out | [FP8 row
+// scales: H + L*H + A] | biases: b_in (ns*H) | b_1..b_L (L*H) | [b_out (A)]
+// | [tau].
 struct Layout {
   int D, H, A, P;     // observation size, hidden, actions, parameter count
+  int L;              // hidden H -> H layers
+  int ns;             // sensors (input bias vectors summed into layer 1)
+  int relu;           // 1: ReLU, 0: tanh
+  int out_bias;       // head has a bias
+  int temp;           // a log-temperature parameter follows the biases
+  int patch;          // 3 k^2: inputs of the vision sensor
+  int n_scalars;      // 4 or 8
+  int nW, nB;         // weight elements, bias (+ tau) elements
   int es;             // bytes per streamed weight element
   int64_t stride;     // bytes per slot, streamed copy
   int off_w1, off_w2, off_w3, off_scale, off_bias;  // byte offsets, streamed
+                                                    // (off_w2: first hidden layer)
   int64_t mstride;    // bytes per slot, FP32 masters
   int moff_w1, moff_w2, moff_w3, moff_bias;          // byte offsets, masters
 };
+
+// Logical index of master element q of the tiled block (or -1 for padding).
+__host__ __device__ __forceinline__ int layout_logical(const Layout &L, int q) {
+  const int D = L.D, H = L.H, A = L.A;
+  const int n1 = D * H, nh = L.L * H * H, n3 = A * H;
+  const int hid0 = D * H + L.ns * H;  // logical start of hidden layer 0
+  if (q < n1) {  // W_in (j, o) at j*H + o
+    const int j = q / H, o = q - j * H;
+    return o * D + j;
+  }
+  q -= n1;
+  if (q < nh) {  // hidden layer l: (j, o) at l*H*H + j*H + o
+    const int l = q / (H * H), r = q - l * H * H;
+    const int j = r / H, o = r - j * H;
+    return hid0 + l * (H * H + H) + o * H + j;
+  }
+  q -= nh;
+  const int out0 = hid0 + L.L * (H * H + H);
+  if (q < n3) return out0 + q;  // W_out (a, j) at a*H + j
+  q -= n3;
+  if (q < L.ns * H) return D * H + q;  // input biases
+  q -= L.ns * H;
+  if (q < L.L * H) {  // hidden biases
+    const int l = q / H;
+    return hid0 + l * (H * H + H) + H * H + (q - l * H);
+  }
+  q -= L.L * H;
+  int k = out0 + n3;
+  if (L.out_bias) {
+    if (q < A) return k + q;
+    q -= A;
+    k += A;
+  }
+  if (L.temp && q == 0) return k;
+  return -1;
+}
+
+// Fan-in of master weight element q (q < nW): the vision patch, the compass
+// one-hot (4 inputs, 8-scalar form) or the internal scalars for W_in in the
+// paper form; D for W_in in the plain form; H for hidden layers and the head.
+__host__ __device__ __forceinline__ int layout_fan_in(const Layout &L, int q) {
+  if (q >= L.D * L.H) return L.H;
+  if (L.ns == 1) return L.D;
+  const int j = q / L.H;
+  if (j < L.patch) return L.patch;
+  if (L.n_scalars >= 8 && j >= L.patch + 1 && j < L.patch + 5) return 4;
+  return L.n_scalars >= 8 ? L.n_scalars - 4 : L.n_scalars;
+}
 
 struct Rules {
   int patch_k, n_scalars, flags, precision;

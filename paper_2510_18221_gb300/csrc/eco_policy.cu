@@ -140,14 +140,16 @@ struct Log2<1> {
   static constexpr int v = 0;
 };
 
-// One input-major layer: out[o] = tanh(s_o * sum_j W[j][o] x[j] + b_o) for
-// o in [0, H), written to shared memory by lanes 0 .. H/E - 1.
+// One input-major layer: out[o] = act(s_o * sum_j W[j][o] x[j] + b_o) for
+// o in [0, H), written to shared memory by lanes 0 .. H/E - 1.  b_o is the
+// sum of nbias bias vectors (the paper form's per-sensor input biases);
+// act is ReLU or tanh.
 template <int PREC, int H, int UNROLL>
 __device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int n_in,
                                                const float *__restrict__ x,
-                                               const float *__restrict__ bias,
+                                               const float *__restrict__ bias, int nbias,
                                                const float *__restrict__ scale,
-                                               float *__restrict__ out, int lane) {
+                                               float *__restrict__ out, int lane, int relu) {
   constexpr int E = Unit<PREC>::E;
   constexpr int UPJ = H / E;  // units per input
   constexpr int LG = Log2<UPJ>::v;
@@ -178,7 +180,10 @@ __device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int 
     for (int e = 0; e < E; ++e) {
       const int o = lane * E + e;
       const float s = (PREC == PREC_FP8) ? __ldg(scale + o) : 1.0f;
-      out[o] = tanhf(fmaf(acc[e], s, __ldg(bias + o)));
+      float b = __ldg(bias + o);
+      for (int k = 1; k < nbias; ++k) b += __ldg(bias + k * H + o);
+      const float v = fmaf(acc[e], s, b);
+      out[o] = relu ? fmaxf(v, 0.0f) : tanhf(v);
     }
   }
 }
@@ -265,26 +270,39 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
     const float *bias = reinterpret_cast<const float *>(blk + L.off_bias);
     const float *scale = reinterpret_cast<const float *>(blk + L.off_scale);
 
-    // -- layer 1: h1 = tanh(W1 x + b1) -> hs
-    layer_in_major<PREC, H, UNROLL>(wb + L.off_w1 / 16, L.D, xs, bias, scale, hs, lane);
+    // -- input layer: act(sum over sensors of (W_s x_s + b_s)) -> hs
+    layer_in_major<PREC, H, UNROLL>(wb + L.off_w1 / 16, L.D, xs, bias, L.ns, scale, hs, lane,
+                                    L.relu);
     __syncwarp();
-    // -- layer 2: h2 = tanh(W2 h1 + b2) -> xs
-    layer_in_major<PREC, H, UNROLL>(wb + L.off_w2 / 16, H, hs, bias + H, scale + H, xs, lane);
-    __syncwarp();
+    // -- hidden layers: h = act(W_l h + b_l), alternating between hs and xs
+    float *cur = hs, *nxt = xs;
+    for (int l = 0; l < L.L; ++l) {
+      layer_in_major<PREC, H, UNROLL>(wb + (L.off_w2 + l * H * H * L.es) / 16, H, cur,
+                                      bias + L.ns * H + l * H, 1, scale + H + l * H, nxt, lane,
+                                      L.relu);
+      __syncwarp();
+      float *tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    }
 
-    // -- head: logits = W3 h2 + b3 (output-major rows of H / E units)
+    // -- head: logits = (W_out h [+ b_out]) / exp(tau) (output-major rows of
+    //    H / E units; the temperature only in the paper form)
     const uint4 *w3 = wb + L.off_w3 / 16;
     const int U3 = L.A * UPJ;
+    const float *hb = bias + L.ns * H + L.L * H;  // head bias, then tau
+    const float tmul = L.temp ? expf(-__ldg(hb + (L.out_bias ? L.A : 0))) : 1.0f;
     for (int base = 0; base < U3; base += 32) {
       const int u = base + lane;
       float part = 0.0f;
-      if (u < U3) part = Unit<PREC>::dot(ldg_stream(w3 + u), xs + (u & (UPJ - 1)) * E);
+      if (u < U3) part = Unit<PREC>::dot(ldg_stream(w3 + u), cur + (u & (UPJ - 1)) * E);
 #pragma unroll
       for (int off = 1; off < UPJ; off <<= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, off);
       if (u < U3 && (lane & (UPJ - 1)) == 0) {
         const int a = u >> LG;
-        const float s = (PREC == PREC_FP8) ? __ldg(scale + 2 * H + a) : 1.0f;
-        ls[a] = fmaf(part, s, __ldg(bias + 2 * H + a));
+        const float s = (PREC == PREC_FP8) ? __ldg(scale + H + L.L * H + a) : 1.0f;
+        const float v = L.out_bias ? fmaf(part, s, __ldg(hb + a)) : part * s;
+        ls[a] = L.temp ? v * tmul : v;
       }
     }
     __syncwarp();
@@ -407,7 +425,7 @@ static PolicyFn pick(int prec, int H, int variant) {
   return nullptr;
 }
 
-int policy_xs_floats(const Layout &L) { return (L.D + 3) & ~3; }
+int policy_xs_floats(const Layout &L) { return ((L.D > L.H ? L.D : L.H) + 3) & ~3; }
 
 cudaError_t policy_prepare(const Layout &L, const Rules &R, int variant, PolicyLaunch *pl) {
   PolicyFn fn = pick(R.precision, L.H, variant);

@@ -26,6 +26,8 @@ ECO_OK, ECO_EINVAL, ECO_ENOMEM, ECO_ECUDA, ECO_ETIMEOUT, ECO_EABI = 0, -1, -2, -
 ECO_FP32, ECO_BF16, ECO_FP8_E4M3 = 0, 1, 2
 ECO_AUTO_EAT, ECO_ROTATE_OBS, ECO_CANCEL_ALL, ECO_GREEDY = 1, 2, 4, 8
 PRECISIONS = {"fp32": ECO_FP32, "bf16": ECO_BF16, "fp8": ECO_FP8_E4M3}
+ECO_POLICY_PLAIN, ECO_POLICY_PAPER = 0, 1
+POLICY_FORMS = {"plain": ECO_POLICY_PLAIN, "paper": ECO_POLICY_PAPER}
 FLAGS = {"auto_eat": ECO_AUTO_EAT, "rotate_obs": ECO_ROTATE_OBS,
          "cancel_all": ECO_CANCEL_ALL, "greedy": ECO_GREEDY}
 
@@ -54,6 +56,7 @@ class eco_config(ctypes.Structure):
         ("e_food", ctypes.c_int32), ("e_repro", ctypes.c_int32),
         ("attack_num", ctypes.c_int32), ("attack_den", ctypes.c_int32),
         ("policy_variant", ctypes.c_int32), ("launch_mode", ctypes.c_int32),
+        ("policy_form", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
     ]
 
 
@@ -223,7 +226,7 @@ def eco_move_claims_noalloc(side: int, n_agents: int, pos: int, act: int, facing
 
 _SHARED = ("patch_k", "n_scalars", "hidden", "n_actions", "precision", "flags", "sigma",
            "food_density", "regrow_p", "wall_density", "e_init", "e_metab", "e_food",
-           "e_repro", "attack_num", "attack_den")
+           "e_repro", "attack_num", "attack_den", "policy_form", "n_hidden")
 
 
 def make_config(envs: Sequence[dict], policy_variant: int = 0, launch_mode: int = 0):
@@ -251,7 +254,8 @@ def make_config(envs: Sequence[dict], policy_variant: int = 0, launch_mode: int 
         sigma=w0["sigma"], food_density=w0["food_density"], regrow_p=w0["regrow_p"],
         wall_density=w0["wall_density"], e_init=w0["e_init"], e_metab=w0["e_metab"],
         e_food=w0["e_food"], e_repro=w0["e_repro"], attack_num=w0["attack_num"],
-        attack_den=w0["attack_den"], policy_variant=policy_variant, launch_mode=launch_mode)
+        attack_den=w0["attack_den"], policy_variant=policy_variant, launch_mode=launch_mode,
+        policy_form=POLICY_FORMS[w0.get("policy_form", "plain")], n_hidden=w0.get("n_hidden", 1))
     return cfg, (side, slots, alive, seed)
 
 
@@ -363,7 +367,8 @@ class Env:
     def read_streamed(self, env: int = 0, slot0: int = 0, n: int = 1):
         prec = self.cfg.precision
         codes = np.zeros((n, self.P), np.uint16 if prec == ECO_BF16 else np.uint8)
-        scales = np.zeros((n, 2 * self.H + self.A), np.float32)
+        layers = self.cfg.n_hidden if self.cfg.policy_form == ECO_POLICY_PAPER else 1
+        scales = np.zeros((n, self.H + layers * self.H + self.A), np.float32)
         _check(lib().eco_read_streamed(self.h, int(env), int(slot0), int(n), _p(codes),
                                        _p(scales)), self.h)
         return codes, (scales if prec == ECO_FP8_E4M3 else None)

@@ -122,3 +122,11 @@ def test_long_mid_1000_steps(seed):
 def test_long_paper_1000_steps():
     rep = _lockstep(workloads.get("paper"), 1000, sample=128)
     print("paper-scale 1000-step lock-step:", rep)
+
+
+def test_paperform_workload_lockstep():
+    """The paper's policy form at paper scale (1024x1024, 65,536 slots,
+    50,000 founders, RCV sensors, 2 x 64 ReLU, BF16)."""
+    rep = _lockstep(workloads.get("paperform"), 3, sample=256)
+    assert rep["steps"] == 3
+    print("paper-form paper-scale lock-step:", rep)

@@ -190,3 +190,52 @@ def test_per_phase_launch_form_lockstep():
     w = workloads.scaled("mid", 128, 2048, 1500, precision="fp8", e_init=190)
     rep = _run(w, 15, launch_mode=1)
     assert rep["births"] > 10
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+def test_paper_form_policy_lockstep(prec):
+    """Sec. 3.3's policy: per-sensor input linears summed, two ReLU hidden
+    layers, unbiased head, evolvable temperature."""
+    w = workloads.scaled("mid", 128, 2048, 1500, precision=prec, e_init=190,
+                         policy_form="paper", n_hidden=2)
+    rep = _run(w, 20)
+    assert rep["births"] > 10
+
+
+@pytest.mark.parametrize("L,base", [(1, "small"), (3, "mid"), (2, "large")])
+def test_paper_form_shapes(L, base):
+    side, slots, k = (64, 256, 200) if base == "small" else (64, 600, 500)
+    w = workloads.scaled(base, side, slots, k, policy_form="paper", n_hidden=L, e_init=190,
+                         precision="bf16" if base != "large" else "fp8")
+    _run(w, 8)
+
+
+def test_paper_form_quantised_copy_bit_exact():
+    from paper_2510_18221_gb300 import eco
+    from tests import inputs
+    w = workloads.scaled("mid", 32, 8, 4, precision="fp8", policy_form="paper", n_hidden=3)
+    env = eco.Env(w)
+    orc = oracle.Oracle(w)
+    rows = inputs.random_params(orc.P, n_rows=8, seed=8)
+    env.write_params(0, 0, rows)
+    assert np.array_equal(env.read_params(0, 0, 8), rows)
+    codes, scales = env.read_streamed(0, 0, 8)
+    D, H, A = orc.D, 64, 9
+    starts = [(0, D)] + [(H * D + 3 * H + l * (H * H + H), H) for l in range(3)]
+    head = H * D + 3 * H + 3 * (H * H + H)
+    for s in range(8):
+        m = rows[s]
+        r = 0
+        for st, n in starts:
+            for o in range(H):
+                row = m[st + o * n:st + (o + 1) * n]
+                sc = oracle.fp8_row_scale(row)
+                assert scales[s, r] == np.float32(sc)
+                want = [oracle.e4m3_encode(float(np.float32(v) / np.float32(sc))) for v in row]
+                assert np.array_equal(codes[s, st + o * n:st + (o + 1) * n], np.array(want, np.uint8))
+                r += 1
+        for a in range(A):
+            row = m[head + a * H:head + (a + 1) * H]
+            assert scales[s, r] == np.float32(oracle.fp8_row_scale(row))
+            r += 1
+    env.close()
