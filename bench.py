@@ -44,7 +44,7 @@ KERNELS_PER_STEP = {0: 2, 1: 12}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="eco", choices=["eco", "reference"])
     ap.add_argument("--workload", default="paper")
@@ -107,17 +107,22 @@ def committed_traffic(workload_name):
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    """nvidia-smi clock / throttle sampling around the timed region.  Each
+    sample carries nvidia-smi's own timestamp; `stop(t0, t1)` keeps the
+    samples whose timestamp lies in the wall-clock window [t0, t1] of the
+    timed region, and falls back to the samples nearest to it (flagged
+    "window": "adjacent") when the region is shorter than the interval."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
 
     def __init__(self, device_id: str | None):
         self.lines = []
         self.proc = None
         cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-               "-lms", "100"]
+               "-lms", str(self.INTERVAL_MS)]
         if device_id:
             cmd += ["-i", device_id]
         try:
@@ -128,38 +133,66 @@ class ClockSampler:
             return
         self.t = threading.Thread(target=self._read, daemon=True)
         self.t.start()
+        time.sleep(0.5)   # nvidia-smi start-up, so that sampling covers the region
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
-    def stop(self):
+    @staticmethod
+    def _when(stamp: str):
+        import datetime
+        try:
+            return datetime.datetime.strptime(stamp, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def stop(self, t0: float, t1: float):
         if not self.proc:
             return None
+        time.sleep(2 * self.INTERVAL_MS / 1000.0)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.t.join(timeout=2)
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                power = float(parts[4]) if parts[4] not in ("", "[N/A]") else None
+                rows.append((self._when(parts[0]), float(parts[2]), float(parts[3]), parts[6:10], power))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
+        inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+        window = "timed region"
+        if not inside:
+            timed = [r for r in rows if r[0] is not None]
+            timed.sort(key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))
+            inside = timed[:2]
+            window = "adjacent"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        reasons = set()
+        for r in inside:
+            for n, v in zip(names, r[3]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(r[1] for r in inside),
+                "sm_max_mhz": max(r[2] for r in inside), "reasons": sorted(reasons),
+                "samples": len(inside), "interval_ms": self.INTERVAL_MS, "window": window,
+                "power_w_max": max((r[4] for r in inside if r[4] is not None), default=None)}
+
+
+def mlp_shape(w) -> str:
+    """Layer widths of the policy: input, H per hidden activation, actions."""
+    layers = w.get("n_hidden", 1) if w.get("policy_form", "plain") == "paper" else 1
+    return "-".join(str(v) for v in [3 * w["patch_k"] ** 2 + w["n_scalars"]]
+                    + [w["hidden"]] * (1 + layers) + [w["n_actions"]])
 
 
 def cpu_baseline_sample(w, seconds, window, steps_cap=None):
@@ -197,9 +230,9 @@ def cpu_baseline_sample(w, seconds, window, steps_cap=None):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": agent_steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d timed steps (within steps %d..%d after reset) of a %dx%d world, %d slots, "
-                      "%d founders, MLP %d-%d-%d-%d %s (same rules and founder density), %.1f s" %
-                      (n, w0, w1, side, side, slots, founders, o.D, w["hidden"], w["hidden"],
-                       w["n_actions"], w["precision"], el)}, agent_steps, el
+                      "%d founders, MLP %s %s (same rules and founder density), %.1f s" %
+                      (n, w0, w1, side, side, slots, founders, mlp_shape(w), w["precision"], el)}, \
+        agent_steps, el
 
 
 def run_reference(args, rank, world):
@@ -266,12 +299,14 @@ def main():
     barrier()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    wall0 = time.time()
     t_start.record(env.stream)
     env.step_timed(args.steps)
     t_end.record(env.stream)
     t_end.synchronize()
+    wall1 = time.time()
     barrier()
-    clk = clocks.stop() if clocks else None
+    clk = clocks.stop(wall0, wall1) if clocks else None
     ms = t_start.elapsed_time(t_end)
     s1 = env.stats()
     policy_ms, n_timed = env.policy_timing()
@@ -361,8 +396,8 @@ def main():
                 "grid": "%dx%d" % (w["side"], w["side"]) if len(envs) == 1 else "mixed",
                 "slots": sum(e["slots"] for e in envs),
                 "founders": sum(e["init_alive"] for e in envs),
-                "mlp": "%d-%d-%d-%d" % (3 * w["patch_k"] ** 2 + w["n_scalars"], w["hidden"],
-                                        w["hidden"], w["n_actions"]),
+                "mlp": mlp_shape(w),
+                "policy_form": w.get("policy_form", "plain"),
                 "weights": w["precision"], "parallelism": "independent worlds, one per GPU",
                 "l2": "inputs larger than L2 (%.2f GB of weights streamed per step)" %
                       (policy_bytes / max(1, args.steps) / 1e9),
