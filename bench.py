@@ -44,7 +44,7 @@ KERNELS_PER_STEP = {0: 2, 1: 12}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="eco", choices=["eco", "reference"])
     ap.add_argument("--workload", default="paper")
