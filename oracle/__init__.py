@@ -42,6 +42,16 @@ FLAG_NAMES = {"auto_eat": AUTO_EAT, "rotate_obs": ROTATE_OBS,
 # Action codes (the build's reading of the configs' action sets).
 STAY, NORTH, SOUTH, EAST, WEST, ATTACK, TURN_LEFT, TURN_RIGHT, EAT = range(9)
 
+# Rule sets, and the paper rule set's action codes (Sec. 3.2 "Actions").
+RULES_SIMPLE, RULES_PAPER = 0, 1
+RULES = {"simple": RULES_SIMPLE, "paper": RULES_PAPER}
+P_REST, P_ROT_CW, P_ROT_CCW, P_FORWARD, P_ATTACK, P_EAT, P_REPRODUCE = range(7)
+
+# Constants of the paper rule set, read from the workload dictionary (0 when
+# absent: the simple rule set ignores them).
+PAPER_RULE_FIELDS = ("hp_max", "hp_child", "attack_damage", "heal_rate", "heal_cost",
+                     "age_div", "starve_damage", "e_act", "e_cap", "e_child")
+
 
 def build(force: bool = False) -> str:
     """Compile ``eco_oracle.c`` into ``liboracle.so`` next to it."""
@@ -69,6 +79,12 @@ class Config(ctypes.Structure):
         ("e_food", ctypes.c_int32), ("e_repro", ctypes.c_int32),
         ("attack_num", ctypes.c_int32), ("attack_den", ctypes.c_int32),
         ("policy_form", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
+        ("rules", ctypes.c_int32), ("hp_max", ctypes.c_int32),
+        ("hp_child", ctypes.c_int32), ("attack_damage", ctypes.c_int32),
+        ("heal_rate", ctypes.c_int32), ("heal_cost", ctypes.c_int32),
+        ("age_div", ctypes.c_int32), ("starve_damage", ctypes.c_int32),
+        ("e_act", ctypes.c_int32), ("e_cap", ctypes.c_int32),
+        ("e_child", ctypes.c_int32),
     ]
 
 
@@ -77,13 +93,16 @@ _P = ctypes.c_void_p
 
 class State(ctypes.Structure):
     _fields_ = [(n, _P) for n in ("food", "wall", "occ", "alive", "x", "y", "facing",
-                                  "energy", "parent", "birth_step", "master", "step")]
+                                  "energy", "parent", "birth_step", "master", "step",
+                                  "hp", "age", "res")]
 
 
 STAT_FIELDS = ["agent_steps"] + ["act%d" % i for i in range(16)] + [
     "moves", "move_blocked", "move_lost", "eaten", "attacks", "attack_hits",
     "energy_transferred", "deaths", "dead_energy", "births", "failed_births",
-    "regrown", "alive", "food_total", "energy_total"]
+    "regrown", "alive", "food_total", "energy_total",
+    "res_total", "eaten_energy", "metab_paid", "heals", "starved", "damage",
+    "food_emptied", "food_refilled"]
 
 
 class Stats(ctypes.Structure):
@@ -219,14 +238,16 @@ def make_config(cfg: dict) -> Config:
         attack_num=cfg["attack_num"], attack_den=cfg["attack_den"],
         policy_form=POLICY_FORMS[cfg.get("policy_form", "plain")]
         if isinstance(cfg.get("policy_form", "plain"), str) else int(cfg["policy_form"]),
-        n_hidden=cfg.get("n_hidden", 1))
+        n_hidden=cfg.get("n_hidden", 1),
+        rules=RULES[cfg.get("rules", "simple")],
+        **{k: int(cfg.get(k, 0)) for k in PAPER_RULE_FIELDS})
 
 
 class Oracle:
     """One environment held as numpy arrays, stepped by the C oracle."""
 
     ARRAYS = ("food", "wall", "occ", "alive", "x", "y", "facing", "energy",
-              "parent", "birth_step", "master", "step")
+              "parent", "birth_step", "master", "step", "hp", "age", "res")
 
     def __init__(self, cfg: dict, allocate: bool = True):
         self.cfg = dict(cfg)
@@ -252,6 +273,9 @@ class Oracle:
             self.birth_step = np.full(S, -1, np.int32)
             self.master = np.zeros((S, self.P), np.float32)
             self.step = np.zeros(1, np.int64)
+            self.hp = np.zeros(S, np.int32)
+            self.age = np.zeros(S, np.int32)
+            self.res = np.zeros(N, np.int32)
 
     # -- plumbing ----------------------------------------------------------
     def _state(self) -> State:

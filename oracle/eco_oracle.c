@@ -18,6 +18,13 @@
  *   Sec. 3.3  Policies: per-agent MLP, softmax sampling, bfloat16 weights,
  *             Kaiming init with zero biases, Gaussian mutation of all
  *             parameters of the child.
+ *   Sec. 3.2 "Resources and Agent Health", "Actions", App. F.7 (attack
+ *             strength), App. F.8 (agent HP): the paper's rule set -- HP with
+ *             starvation, attack and age damage and healing from energy,
+ *             rotate / forward moves, a 3x3 attack in front that can kill,
+ *             explicit eat and reproduce actions, resources dropped where an
+ *             agent dies.  One resource (energy lying on cells) stands in for
+ *             the paper's water / energy / biomass.
  *   App. E    the step runs every phase of the environment each step.
  *
  * Precision: the policy runs in FP64 on the FP32-stored master parameters
@@ -72,7 +79,31 @@ enum {
   ST_REGROW = 11
 };
 
-/* Action codes.  Small config: 0..5; mid and larger configs add 6..8. */
+/* Rule sets.  Simple: the workloads' rules (death at zero energy, a
+ * 50% energy-stealing attack on the faced cell, reproduction at a
+ * threshold).  Paper (Sec. 3.2, App. F.7-F.8): HP, rotate / forward moves,
+ * a 3x3 attack in front, eat and reproduce actions, resource drop at death. */
+enum {
+  ORC_RULES_SIMPLE = 0,
+  ORC_RULES_PAPER = 1
+};
+
+/* Action codes of the paper rule set (Sec. 3.2 "Actions": rest, three
+ * moves, attack, eat -- one resource here, so one eat action -- and
+ * reproduce). */
+enum {
+  P_REST = 0,
+  P_ROT_CW = 1,
+  P_ROT_CCW = 2,
+  P_FORWARD = 3,
+  P_ATTACK = 4,
+  P_EAT = 5,
+  P_REPRODUCE = 6,
+  P_N_ACTIONS = 7
+};
+
+/* Action codes of the simple rule set.  Small config: 0..5; mid and larger
+ * configs add 6..8. */
 enum {
   A_STAY = 0,
   A_NORTH = 1,
@@ -103,6 +134,20 @@ typedef struct {
   int32_t e_init, e_metab, e_food, e_repro, attack_num, attack_den;
   int32_t policy_form; /* ORC_PLAIN or ORC_PAPER_FORM (see the layout below) */
   int32_t n_hidden;    /* paper form: hidden H -> H layers (plain form: 1)  */
+  /* Paper rule set only (ORC_RULES_PAPER).  HP is counted in quarter
+   * points, so that the paper's 10 HP maximum, 5 HP child, full / half /
+   * quarter attack (10 / 5 / 2.5 HP) are whole numbers: 40, 20, 40/20/10. */
+  int32_t rules;         /* ORC_RULES_SIMPLE or ORC_RULES_PAPER            */
+  int32_t hp_max;        /* HP ceiling; founders start at it               */
+  int32_t hp_child;      /* HP of a newborn                                */
+  int32_t attack_damage; /* HP taken from every agent in the 3x3 square    */
+  int32_t heal_rate;     /* HP regained per step while energy allows       */
+  int32_t heal_cost;     /* energy paid for one step of healing            */
+  int32_t age_div;       /* age damage per step = floor(age / age_div)     */
+  int32_t starve_damage; /* HP lost in a step whose cost exceeds the energy */
+  int32_t e_act;         /* extra energy cost of any action but rest       */
+  int32_t e_cap;         /* stomach capacity: eating stops at this energy  */
+  int32_t e_child;       /* energy a parent hands to its child             */
 } orc_config;
 
 enum {
@@ -123,6 +168,10 @@ typedef struct {
   int32_t *birth_step; /* [S] step of birth, -1 for founders             */
   float *master;       /* [S][P] parameters, logical order (see below)   */
   int64_t *step;       /* the step counter t                             */
+  int32_t *hp;         /* [S] paper rules: HP in quarter points           */
+  int32_t *age;        /* [S] paper rules: steps survived                 */
+  int32_t *res;        /* [L*L] paper rules: energy lying on the cell;    */
+                       /*   food[c] == (res[c] > 0)                       */
 } orc_state;
 
 typedef struct {
@@ -143,6 +192,15 @@ typedef struct {
   int64_t alive;              /* alive at the end of the step            */
   int64_t food_total;         /* food cells at the end of the step       */
   int64_t energy_total;       /* sum of alive energies at the end        */
+  /* paper rules only (0 under the simple rules) */
+  int64_t res_total;          /* energy lying on cells at the end        */
+  int64_t eaten_energy;       /* energy moved from cells into stomachs   */
+  int64_t metab_paid;         /* energy paid for actions                 */
+  int64_t heals;              /* agents that healed this step            */
+  int64_t starved;            /* agents whose cost exceeded their energy */
+  int64_t damage;             /* HP dealt by attacks                     */
+  int64_t food_emptied;       /* cells emptied by eating                 */
+  int64_t food_refilled;      /* empty cells that received a death drop  */
 } orc_stats;
 
 /* ------------------------------------------------------------------------ */
@@ -472,6 +530,8 @@ int orc_reset(const orc_config *c, orc_state *s) {
     s->wall[cell] = (uint8_t)(r[cell & 3] < thr_wall);
     draw4(c, ST_FOOD_INIT, (uint32_t)(cell >> 2), 0u, 0u, r);
     s->food[cell] = (uint8_t)(!s->wall[cell] && r[cell & 3] < thr_food);
+    /* paper rules: a food cell holds one bite, e_food energy */
+    s->res[cell] = (c->rules == ORC_RULES_PAPER && s->food[cell]) ? c->e_food : 0;
     s->occ[cell] = -1;
   }
 
@@ -501,6 +561,8 @@ int orc_reset(const orc_config *c, orc_state *s) {
     s->energy[slot] = 0;
     s->parent[slot] = -1;
     s->birth_step[slot] = -1;
+    s->hp[slot] = 0;
+    s->age[slot] = 0;
   }
   for (i = 0; i < K; i++) {
     cell = chosen[i];
@@ -510,6 +572,7 @@ int orc_reset(const orc_config *c, orc_state *s) {
     draw4(c, ST_FACING_INIT, (uint32_t)(i >> 2), 0u, 0u, r);
     s->facing[i] = (uint8_t)(r[i & 3] >> 30);
     s->energy[i] = c->e_init;
+    s->hp[i] = c->rules == ORC_RULES_PAPER ? c->hp_max : 0;
     s->occ[cell] = i;
   }
 #pragma omp parallel for schedule(dynamic, 16)
@@ -530,7 +593,10 @@ int orc_reset(const orc_config *c, orc_state *s) {
 /* Observation (Sec. 3.2 "Sensors"): a k x k patch around the agent with     */
 /* channels (food, agent, wall), rotated so that the agent's facing is the  */
 /* top row, flattened (row, column, channel), then the scalars             */
-/* [energy / e_repro, one-hot facing (8-scalar form), zeros].               */
+/* [energy / e_repro, one-hot facing (8-scalar form), zeros].  Under the    */
+/* paper rules the zeros become the internal and external sensors: HP /     */
+/* hp_max, age / (age + age_div), and the energy r lying on the agent's     */
+/* cell as r / (r + e_food), all in [0, 1).                                 */
 /* ------------------------------------------------------------------------ */
 
 void orc_observe(const orc_config *c, const orc_state *s, int32_t slot, double *x) {
@@ -558,6 +624,14 @@ void orc_observe(const orc_config *c, const orc_state *s, int32_t slot, double *
   for (i = 0; i < c->n_scalars; i++) x[base + i] = 0.0;
   x[base] = (double)s->energy[slot] / (double)c->e_repro;
   if (c->n_scalars >= 8) x[base + 1 + f] = 1.0;
+  if (c->rules == ORC_RULES_PAPER) {
+    int extra = c->n_scalars >= 8 ? base + 5 : base + 1;
+    int here = cell_of(s->x[slot], s->y[slot], L);
+    double age = (double)s->age[slot], res = (double)s->res[here];
+    x[extra + 0] = (double)s->hp[slot] / (double)c->hp_max;
+    x[extra + 1] = age / (age + (double)c->age_div);
+    x[extra + 2] = res / (res + (double)c->e_food);
+  }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -728,8 +802,8 @@ void orc_mutate(const orc_config *c, int64_t step, int32_t parent_slot,
 
 /* ------------------------------------------------------------------------ */
 /* Transition (Sec. 3.2 "Actions", "Resources and Agent Health").  Phase    */
-/* order: face/turn, move, eat, attack, metabolism + death, reproduction +  */
-/* mutation, regrowth.                                                       */
+/* order: face/turn, move, eat, attack, metabolism + death (health under    */
+/* the paper rules), reproduction + mutation, regrowth.                     */
 /* ------------------------------------------------------------------------ */
 
 static uint64_t claim_key(const orc_config *c, uint32_t stream, int64_t t, int32_t slot) {
@@ -743,10 +817,21 @@ static int32_t claim_slot(uint64_t key) {
   return (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFu));
 }
 
+
+/* The cell at `fwd` steps ahead and `lat` steps to the right of an agent at
+ * (x, y) facing f, on the torus. */
+static int cell_ahead(int x, int y, int f, int fwd, int lat, int L) {
+  int right = (f + 1) & 3;
+  int dx = fwd * DIR_DX[f] + lat * DIR_DX[right];
+  int dy = fwd * DIR_DY[f] + lat * DIR_DY[right];
+  return cell_of(wrap(x + dx, L), wrap(y + dy, L), L);
+}
+
 int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
                    orc_stats *st, int32_t *birth_parent, int32_t *birth_child) {
   int L = c->side, N = L * L, S = c->slots, A = c->n_actions;
   int P = orc_n_params(c);
+  int paper = c->rules == ORC_RULES_PAPER;
   int64_t t = *s->step;
   uint32_t thr_regrow = orc_threshold(c->regrow_p);
   uint64_t *best_cell = (uint64_t *)calloc((size_t)N, sizeof(uint64_t));
@@ -754,47 +839,58 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
   uint64_t *best_victim = (uint64_t *)calloc((size_t)S, sizeof(uint64_t));
   int32_t *target = (int32_t *)malloc(sizeof(int32_t) * (size_t)S);
   int32_t *esnap = (int32_t *)malloc(sizeof(int32_t) * (size_t)S);
+  int32_t *dmg = (int32_t *)calloc((size_t)S, sizeof(int32_t));
   int32_t *winners = (int32_t *)malloc(sizeof(int32_t) * (size_t)S);
   int32_t *free_slots = (int32_t *)malloc(sizeof(int32_t) * (size_t)S);
-  int slot, cell, nwin = 0, nfree = 0, i;
+  int slot, cell, nwin = 0, nfree = 0, i, rc = 0;
   static const int MOVE_DIR[5] = {-1, 0, 2, 1, 3}; /* action -> N S E W dir */
 
   memset(st, 0, sizeof(*st));
-  if (!best_cell || !count_cell || !best_victim || !target || !esnap || !winners || !free_slots) {
-    free(best_cell); free(count_cell); free(best_victim); free(target);
-    free(esnap); free(winners); free(free_slots);
-    return -1;
+  if (!best_cell || !count_cell || !best_victim || !target || !esnap || !dmg || !winners ||
+      !free_slots) {
+    rc = -1;
+    goto done;
   }
   for (slot = 0; slot < S; slot++) {
     if (!s->alive[slot]) continue;
     if (action[slot] >= A) {
-      free(best_cell); free(count_cell); free(best_victim); free(target);
-      free(esnap); free(winners); free(free_slots);
-      return -2;
+      rc = -2;
+      goto done;
     }
     st->agent_steps++;
     st->act[action[slot]]++;
   }
 
-  /* 1. Facing: a move action faces its direction whether or not the move
-   *    succeeds; turn-left / turn-right rotate by a quarter. */
+  /* 1. Facing.  Simple rules: a move action faces its direction whether or
+   *    not the move succeeds; turn-left / turn-right rotate by a quarter.
+   *    Paper rules: rotate clockwise / counter-clockwise by a quarter. */
   for (slot = 0; slot < S; slot++) {
     int a = action[slot];
     if (!s->alive[slot]) continue;
-    if (a >= A_NORTH && a <= A_WEST) s->facing[slot] = (uint8_t)MOVE_DIR[a];
-    else if (A > A_TURN_LEFT && a == A_TURN_LEFT) s->facing[slot] = (uint8_t)((s->facing[slot] + 3) & 3);
-    else if (A > A_TURN_RIGHT && a == A_TURN_RIGHT) s->facing[slot] = (uint8_t)((s->facing[slot] + 1) & 3);
+    if (paper) {
+      if (a == P_ROT_CW) s->facing[slot] = (uint8_t)((s->facing[slot] + 1) & 3);
+      else if (a == P_ROT_CCW) s->facing[slot] = (uint8_t)((s->facing[slot] + 3) & 3);
+    } else if (a >= A_NORTH && a <= A_WEST) {
+      s->facing[slot] = (uint8_t)MOVE_DIR[a];
+    } else if (A > A_TURN_LEFT && a == A_TURN_LEFT) {
+      s->facing[slot] = (uint8_t)((s->facing[slot] + 3) & 3);
+    } else if (A > A_TURN_RIGHT && a == A_TURN_RIGHT) {
+      s->facing[slot] = (uint8_t)((s->facing[slot] + 1) & 3);
+    }
   }
 
-  /* 2. Moves.  A move into a wall or into a cell occupied when the step
-   *    began is cancelled.  Several agents moving into one free cell: the
-   *    highest CLAIM_MOVE draw wins (ties to the lower slot), or, with the
-   *    paper's cancel-all rule, every contested move is cancelled. */
+  /* 2. Moves, one cell in the facing direction (N/S/E/W actions, or move
+   *    forward under the paper rules).  A move into a wall or into a cell
+   *    occupied when the step began is cancelled.  Several agents moving
+   *    into one free cell: the highest CLAIM_MOVE draw wins (ties to the
+   *    lower slot), or, with the paper's cancel-all rule, every contested
+   *    move is cancelled. */
   for (slot = 0; slot < S; slot++) {
     int a = action[slot], tc;
     uint64_t key;
     target[slot] = -1;
-    if (!s->alive[slot] || a < A_NORTH || a > A_WEST) continue;
+    if (!s->alive[slot]) continue;
+    if (paper ? a != P_FORWARD : (a < A_NORTH || a > A_WEST)) continue;
     tc = neighbour(s->x[slot], s->y[slot], s->facing[slot], L);
     if (s->wall[tc] || s->occ[tc] != -1) {
       st->move_blocked++;
@@ -822,13 +918,31 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
     st->moves++;
   }
 
-  /* 3. Eat: the food on the agent's cell (automatic in the small rule set,
-   *    the eat action otherwise) becomes e_food energy. */
+  /* 3. Eat.  Simple rules: the food on the agent's cell (automatic in the
+   *    small rule set, the eat action otherwise) becomes e_food energy.
+   *    Paper rules: the eat action moves one bite, min(e_food, energy on
+   *    the cell, e_cap - energy), from the cell into the stomach. */
   for (slot = 0; slot < S; slot++) {
     int here;
     if (!s->alive[slot]) continue;
-    if (!((c->flags & ORC_AUTO_EAT) || (A > A_EAT && action[slot] == A_EAT))) continue;
     here = cell_of(s->x[slot], s->y[slot], L);
+    if (paper) {
+      int32_t bite = c->e_food;
+      if (action[slot] != P_EAT) continue;
+      if (s->res[here] < bite) bite = s->res[here];
+      if (c->e_cap - s->energy[slot] < bite) bite = c->e_cap - s->energy[slot];
+      if (bite <= 0) continue;
+      s->res[here] -= bite;
+      s->energy[slot] += bite;
+      st->eaten++;
+      st->eaten_energy += bite;
+      if (s->res[here] == 0) {
+        s->food[here] = 0;
+        st->food_emptied++;
+      }
+      continue;
+    }
+    if (!((c->flags & ORC_AUTO_EAT) || (A > A_EAT && action[slot] == A_EAT))) continue;
     if (s->food[here]) {
       s->food[here] = 0;
       s->energy[slot] += c->e_food;
@@ -836,62 +950,133 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
     }
   }
 
-  /* 4. Attack on the faced cell.  A victim yields to one attacker (highest
-   *    CLAIM_ATTACK draw, ties to the lower slot), which takes
-   *    floor(e * num / den) of the victim's post-eat energy.  Every amount
-   *    is computed from the post-eat snapshot, so the outcome does not
-   *    depend on any order. */
-  for (slot = 0; slot < S; slot++) esnap[slot] = s->energy[slot];
-  for (slot = 0; slot < S; slot++) {
-    int tc, v;
-    uint64_t key;
-    if (!s->alive[slot] || action[slot] != A_ATTACK) continue;
-    st->attacks++;
-    tc = neighbour(s->x[slot], s->y[slot], s->facing[slot], L);
-    v = s->occ[tc];
-    if (v < 0) continue;
-    key = claim_key(c, ST_CLAIM_ATTACK, t, slot);
-    if (key > best_victim[v]) best_victim[v] = key;
-  }
-  for (slot = 0; slot < S; slot++) {
-    int32_t w, amount;
-    if (best_victim[slot] == 0) continue;
-    w = claim_slot(best_victim[slot]);
-    amount = (int32_t)(((int64_t)esnap[slot] * c->attack_num) / c->attack_den);
-    s->energy[slot] -= amount;
-    s->energy[w] += amount;
-    st->attack_hits++;
-    st->energy_transferred += amount;
+  /* 4. Attack.  Simple rules: on the faced cell; a victim yields to one
+   *    attacker (highest CLAIM_ATTACK draw, ties to the lower slot), which
+   *    takes floor(e * num / den) of the victim's post-eat energy.  Every
+   *    amount is computed from the post-eat snapshot, so the outcome does
+   *    not depend on any order.  Paper rules: every agent in the 3x3 square
+   *    directly in front (1..3 cells ahead, one to either side) loses
+   *    attack_damage HP per attacker. */
+  if (paper) {
+    for (slot = 0; slot < S; slot++) {
+      int fwd, lat;
+      if (!s->alive[slot] || action[slot] != P_ATTACK) continue;
+      st->attacks++;
+      for (fwd = 1; fwd <= 3; fwd++) {
+        for (lat = -1; lat <= 1; lat++) {
+          int v = s->occ[cell_ahead(s->x[slot], s->y[slot], s->facing[slot], fwd, lat, L)];
+          if (v < 0) continue;
+          dmg[v] += c->attack_damage;
+          st->attack_hits++;
+          st->damage += c->attack_damage;
+        }
+      }
+    }
+  } else {
+    for (slot = 0; slot < S; slot++) esnap[slot] = s->energy[slot];
+    for (slot = 0; slot < S; slot++) {
+      int tc, v;
+      uint64_t key;
+      if (!s->alive[slot] || action[slot] != A_ATTACK) continue;
+      st->attacks++;
+      tc = neighbour(s->x[slot], s->y[slot], s->facing[slot], L);
+      v = s->occ[tc];
+      if (v < 0) continue;
+      key = claim_key(c, ST_CLAIM_ATTACK, t, slot);
+      if (key > best_victim[v]) best_victim[v] = key;
+    }
+    for (slot = 0; slot < S; slot++) {
+      int32_t w, amount;
+      if (best_victim[slot] == 0) continue;
+      w = claim_slot(best_victim[slot]);
+      amount = (int32_t)(((int64_t)esnap[slot] * c->attack_num) / c->attack_den);
+      s->energy[slot] -= amount;
+      s->energy[w] += amount;
+      st->attack_hits++;
+      st->energy_transferred += amount;
+    }
   }
 
-  /* 5. Metabolism and death: every agent pays e_metab; an agent whose
-   *    energy is then <= 0 dies and frees its cell and slot. */
+  /* 5. Simple rules: every agent pays e_metab; an agent whose energy is then
+   *    <= 0 dies and frees its cell and slot.
+   *    Paper rules, per agent in this order: pay the action's cost
+   *    (e_metab, plus e_act for anything but rest); a cost above the
+   *    energy empties the stomach and costs starve_damage HP.  Then the
+   *    attack damage and the age damage floor(age / age_div) come off the
+   *    HP.  A survivor below hp_max with at least heal_cost energy heals
+   *    heal_rate HP (capped at hp_max) for heal_cost energy.  At HP <= 0 the
+   *    agent dies and its energy is dropped on its cell; otherwise it ages
+   *    by one step. */
   for (slot = 0; slot < S; slot++) {
+    int here;
     if (!s->alive[slot]) continue;
+    here = cell_of(s->x[slot], s->y[slot], L);
+    if (paper) {
+      int32_t cost = c->e_metab + (action[slot] != P_REST ? c->e_act : 0);
+      int32_t hp = s->hp[slot];
+      if (s->energy[slot] >= cost) {
+        s->energy[slot] -= cost;
+        st->metab_paid += cost;
+      } else {
+        st->metab_paid += s->energy[slot];
+        s->energy[slot] = 0;
+        hp -= c->starve_damage;
+        st->starved++;
+      }
+      hp -= dmg[slot];
+      hp -= s->age[slot] / c->age_div;
+      if (hp > 0 && hp < c->hp_max && c->heal_rate > 0 && s->energy[slot] >= c->heal_cost) {
+        hp += c->heal_rate;
+        if (hp > c->hp_max) hp = c->hp_max;
+        s->energy[slot] -= c->heal_cost;
+        st->heals++;
+      }
+      if (hp <= 0) {
+        int32_t e = s->energy[slot];
+        st->deaths++;
+        st->dead_energy += e;
+        if (e > 0 && s->res[here] == 0) {
+          s->food[here] = 1;
+          st->food_refilled++;
+        }
+        s->res[here] += e;
+        s->alive[slot] = 0;
+        s->occ[here] = -1;
+        s->energy[slot] = 0;
+        s->hp[slot] = 0;
+      } else {
+        s->hp[slot] = hp;
+        s->age[slot]++;
+      }
+      continue;
+    }
     s->energy[slot] -= c->e_metab;
     if (s->energy[slot] <= 0) {
       st->deaths++;
       st->dead_energy += s->energy[slot];
       s->alive[slot] = 0;
-      s->occ[cell_of(s->x[slot], s->y[slot], L)] = -1;
+      s->occ[here] = -1;
       s->energy[slot] = 0;
     }
   }
 
-  /* 6. Reproduction: an agent with energy >= e_repro places one child on
-   *    the cell behind it, if that cell is not a wall and is free after the
-   *    deaths.  One winner per cell (highest CLAIM_BIRTH draw, ties to the
-   *    lower slot).  Winners, in ascending slot order, take the free slots
-   *    in ascending order; winners left without a slot keep their energy.
-   *    The child gets floor(e/2), the parent keeps the rest; the child
-   *    faces as the parent did and carries the parent's parameters mutated
-   *    by sigma * N(0,1). */
+  /* 6. Reproduction: an agent with energy >= e_repro (under the paper rules:
+   *    that also took the reproduce action) places one child on the cell
+   *    behind it, if that cell is not a wall and is free after the deaths.
+   *    One winner per cell (highest CLAIM_BIRTH draw, ties to the lower
+   *    slot).  Winners, in ascending slot order, take the free slots in
+   *    ascending order; winners left without a slot keep their energy.
+   *    Simple rules: the child gets floor(e/2), the parent keeps the rest.
+   *    Paper rules: the parent hands e_child to the child, which starts at
+   *    hp_child HP and age 0.  The child faces as the parent did and
+   *    carries the parent's parameters mutated by sigma * N(0,1). */
   for (i = 0; i < N; i++) best_cell[i] = 0;
   for (slot = 0; slot < S; slot++) {
     int tc;
     uint64_t key;
     target[slot] = -1;
     if (!s->alive[slot] || s->energy[slot] < c->e_repro) continue;
+    if (paper && action[slot] != P_REPRODUCE) continue;
     tc = neighbour(s->x[slot], s->y[slot], (s->facing[slot] + 2) & 3, L);
     if (s->wall[tc] || s->occ[tc] != -1) continue;
     target[slot] = tc;
@@ -911,9 +1096,11 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
     ch = free_slots[i];
     tc = target[p];
     e = s->energy[p];
-    ce = e / 2;
+    ce = paper ? c->e_child : e / 2;
     s->energy[p] = e - ce;
     s->energy[ch] = ce;
+    s->hp[ch] = paper ? c->hp_child : 0;
+    s->age[ch] = 0;
     s->alive[ch] = 1;
     s->x[ch] = tc % L;
     s->y[ch] = tc / L;
@@ -927,14 +1114,16 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
     st->births++;
   }
 
-  /* 7. Regrowth: every non-wall cell without food regrows one unit with
-   *    probability regrow_p (stream REGROW at counter (step, cell/4)). */
+  /* 7. Regrowth: every non-wall cell without food regrows with probability
+   *    regrow_p (stream REGROW at counter (step, cell/4)): one food unit, or
+   *    under the paper rules one bite of e_food energy. */
   for (cell = 0; cell < N; cell++) {
     uint32_t r[4];
     if (s->wall[cell] || s->food[cell]) continue;
     draw4(c, ST_REGROW, (uint32_t)t, (uint32_t)(cell >> 2), 0u, r);
     if (r[cell & 3] < thr_regrow) {
       s->food[cell] = 1;
+      if (paper) s->res[cell] = c->e_food;
       st->regrown++;
     }
   }
@@ -944,10 +1133,14 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
     st->alive++;
     st->energy_total += s->energy[slot];
   }
-  for (cell = 0; cell < N; cell++) st->food_total += s->food[cell];
+  for (cell = 0; cell < N; cell++) {
+    st->food_total += s->food[cell];
+    if (paper) st->res_total += s->res[cell];
+  }
   *s->step = t + 1;
 
+done:
   free(best_cell); free(count_cell); free(best_victim); free(target);
-  free(esnap); free(winners); free(free_slots);
-  return 0;
+  free(esnap); free(dmg); free(winners); free(free_slots);
+  return rc;
 }

@@ -55,8 +55,24 @@ LARGE = dict(MID, name="large-2048x2048-262144slots-683-128-128-9-fp8",
 PAPER_FORM = dict(PAPER, name="paperform-1024x1024-65536slots-RCV-2x64-bf16",
                   policy_form="paper", n_hidden=2)
 
+# The paper's rule set (Sec. 3.2 "Resources and Agent Health", "Actions";
+# App. F.7-F.8), one resource: HP in quarter points (10 HP maximum, children
+# start at 5 HP, the full attack takes 10 HP, healing 1 HP per step for one
+# energy unit), age damage floor(age / 1000) quarter points per step, 2 HP
+# per step while starving; actions rest, rotate cw / ccw, forward, attack
+# (the 3x3 square in front), eat (one bite of up to 20 energy, stomach 400),
+# reproduce (at >= 200 energy, handing 100 to the child).
+PAPER_RULES = dict(rules="paper", n_actions=7, hp_max=40, hp_child=20, attack_damage=40,
+                   heal_rate=4, heal_cost=1, age_div=1000, starve_damage=8, e_act=1,
+                   e_cap=400, e_child=100)
+
+# The paper's rules and policy form together on the paper-scale world
+# (RCV+A agents: vision, compass, internal sensors; attack enabled).
+ECOLOGY = dict(PAPER_FORM, name="ecology-1024x1024-65536slots-RCV+A-2x64-7act-bf16",
+               **PAPER_RULES)
+
 WORKLOADS = {"small": SMALL, "mid": MID, "paper": PAPER, "large": LARGE,
-             "paperform": PAPER_FORM}
+             "paperform": PAPER_FORM, "ecology": ECOLOGY}
 
 
 def get(key: str, **overrides) -> dict:
