@@ -398,6 +398,7 @@ def main():
                 "founders": sum(e["init_alive"] for e in envs),
                 "mlp": mlp_shape(w),
                 "policy_form": w.get("policy_form", "plain"),
+                "rules": w.get("rules", "simple"),
                 "weights": w["precision"], "parallelism": "independent worlds, one per GPU",
                 "l2": "inputs larger than L2 (%.2f GB of weights streamed per step)" %
                       (policy_bytes / max(1, args.steps) / 1e9),

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define ECO_ABI_VERSION 1
+#define ECO_ABI_VERSION 2
 
 /* Status codes. */
 #define ECO_OK 0
@@ -75,8 +75,34 @@ extern "C" {
 #define ECO_POLICY_PLAIN 0
 #define ECO_POLICY_PAPER 1
 
-/* Action codes: 0 stay, 1 north, 2 south, 3 east, 4 west, 5 attack;
- * nine-action sets add 6 turn-left, 7 turn-right, 8 eat. */
+/* Rule sets.  Simple: the workloads' rules -- energy is life (death at
+ * e <= 0), the attack takes a fraction of the faced agent's energy,
+ * reproduction happens at e >= e_repro.  Paper (Sec. 3.2 "Resources and
+ * Agent Health" and "Actions"; App. F.7 attack strength, App. F.8 agent HP),
+ * with one resource, energy, lying on cells and carried in a stomach:
+ *   - HP (quarter points) is life; founders start at hp_max, children at
+ *     hp_child;
+ *   - each step costs e_metab (rest) or e_metab + e_act (any other action);
+ *     a cost above the energy empties the stomach and costs starve_damage
+ *     HP; attacks and age (floor(age / age_div) per step) take HP; a
+ *     survivor below hp_max with >= heal_cost energy heals heal_rate HP for
+ *     heal_cost energy; at HP <= 0 the agent dies and its energy is added to
+ *     its cell;
+ *   - attack: every agent in the 3x3 square in front (1..3 cells ahead, one
+ *     to either side) loses attack_damage HP per attacker;
+ *   - eat: moves min(e_food, energy on the cell, e_cap - energy) into the
+ *     stomach; a cell "has food" while it holds energy;
+ *   - reproduce (the action, at energy >= e_repro): the child on the cell
+ *     behind gets e_child energy from the parent;
+ *   - regrowth puts e_food energy on an empty cell with probability
+ *     regrow_p. */
+#define ECO_RULES_SIMPLE 0
+#define ECO_RULES_PAPER 1
+
+/* Action codes.  Simple rules: 0 stay, 1 north, 2 south, 3 east, 4 west,
+ * 5 attack; nine-action sets add 6 turn-left, 7 turn-right, 8 eat.  Paper
+ * rules (7 actions): 0 rest, 1 rotate clockwise, 2 rotate counter-
+ * clockwise, 3 forward, 4 attack, 5 eat, 6 reproduce. */
 
 typedef struct eco_handle eco_handle;
 
@@ -93,7 +119,7 @@ typedef struct {
   int32_t patch_k;               /* odd patch side k: D = 3k^2 + n_scalars   */
   int32_t n_scalars;             /* 4 or 8                                   */
   int32_t hidden;                /* H in {32, 64, 128}                       */
-  int32_t n_actions;             /* A in {6, 9}                              */
+  int32_t n_actions;             /* A in {6, 9}; 7 under the paper rules     */
   int32_t precision;             /* ECO_FP32 / ECO_BF16 / ECO_FP8_E4M3       */
   int32_t flags;                 /* ECO_AUTO_EAT | ECO_ROTATE_OBS | ...      */
   float sigma;                   /* mutation standard deviation              */
@@ -115,6 +141,19 @@ typedef struct {
   int32_t policy_form;           /* ECO_POLICY_PLAIN or ECO_POLICY_PAPER     */
   int32_t n_hidden;              /* paper form: hidden H -> H layers (1..4);
                                     the plain form ignores it (one layer)   */
+  /* Rule set, and the constants only the paper rules use (HP in quarter
+   * points: the paper's 10 HP maximum is 40). */
+  int32_t rules;                 /* ECO_RULES_SIMPLE or ECO_RULES_PAPER      */
+  int32_t hp_max;                /* >= 1                                     */
+  int32_t hp_child;              /* in [1, hp_max]                           */
+  int32_t attack_damage;         /* HP per attacker covering a victim, >= 0  */
+  int32_t heal_rate;             /* HP healed per step, >= 0                 */
+  int32_t heal_cost;             /* energy per step of healing, >= 0         */
+  int32_t age_div;               /* age damage floor(age / age_div), >= 1    */
+  int32_t starve_damage;         /* HP lost when the cost exceeds the energy */
+  int32_t e_act;                 /* extra cost of any action but rest, >= 0  */
+  int32_t e_cap;                 /* stomach capacity, >= max(e_init, 1)      */
+  int32_t e_child;               /* energy handed to a child, in [1, e_repro] */
 } eco_config;
 
 /* Statistics, one record per environment (App. E measurement API).
@@ -130,16 +169,28 @@ enum {
   ECO_STAT_MOVE_LOST,         /* (sum) lost a contested cell                */
   ECO_STAT_EATEN,             /* (sum) food units eaten                     */
   ECO_STAT_ATTACKS,           /* (sum) attack actions                       */
-  ECO_STAT_ATTACK_HITS,       /* (sum) energy transfers                     */
+  ECO_STAT_ATTACK_HITS,       /* (sum) energy transfers (paper rules: agents
+                                 hit, counted once per attacker)           */
   ECO_STAT_ENERGY_TRANSFERRED,/* (sum) energy moved by attacks              */
   ECO_STAT_DEATHS,            /* (sum)                                      */
-  ECO_STAT_DEAD_ENERGY,       /* (sum) energies (<= 0) of agents that died  */
+  ECO_STAT_DEAD_ENERGY,       /* (sum) energies of agents that died (<= 0
+                                 under the simple rules; dropped on the
+                                 cell under the paper rules)              */
   ECO_STAT_BIRTHS,            /* (sum)                                      */
   ECO_STAT_FAILED_BIRTHS,     /* (sum) birth-cell winners without a slot    */
   ECO_STAT_REGROWN,           /* (sum) cells that regrew food               */
   ECO_STAT_ALIVE,             /* (now) alive agents                         */
   ECO_STAT_FOOD_TOTAL,        /* (now) cells holding food                   */
   ECO_STAT_ENERGY_TOTAL,      /* (now) summed energy of alive agents        */
+  /* paper rules only (0 under the simple rules) */
+  ECO_STAT_RES_TOTAL,         /* (now) energy lying on cells                */
+  ECO_STAT_EATEN_ENERGY,      /* (sum) energy moved from cells to stomachs  */
+  ECO_STAT_METAB_PAID,        /* (sum) energy paid for actions              */
+  ECO_STAT_HEALS,             /* (sum) agent-steps of healing               */
+  ECO_STAT_STARVED,           /* (sum) agent-steps whose cost exceeded e    */
+  ECO_STAT_DAMAGE,            /* (sum) HP dealt by attacks                  */
+  ECO_STAT_FOOD_EMPTIED,      /* (sum) cells emptied by eating              */
+  ECO_STAT_FOOD_REFILLED,     /* (sum) empty cells that received a drop     */
   ECO_N_STATS
 };
 
@@ -161,6 +212,11 @@ typedef struct {
   int32_t *parent;     /* [slots] parent slot, -1 for founders              */
   int32_t *birth_step; /* [slots] step of birth, -1 for founders            */
   int64_t *step;       /* [1] steps completed                               */
+  int32_t *hp;         /* [slots] paper rules: HP (quarter points)          */
+  int32_t *age;        /* [slots] paper rules: steps survived               */
+  int32_t *res;        /* [L*L] paper rules: energy lying on the cell; on
+                          write, food is taken as res > 0 (the food array
+                          is then ignored)                                  */
 } eco_state_view;
 
 /* Parameter count P and observation size D for a configuration.

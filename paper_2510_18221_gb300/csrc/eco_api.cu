@@ -88,7 +88,19 @@ static int validate(const eco_config *c, char *msg, size_t n) {
   if (c->patch_k < 1 || (c->patch_k & 1) == 0 || c->patch_k > 31) return snprintf(msg, n, "patch_k must be odd in [1, 31]"), ECO_EINVAL;
   if (c->n_scalars != 4 && c->n_scalars != 8) return snprintf(msg, n, "n_scalars must be 4 or 8"), ECO_EINVAL;
   if (c->hidden != 32 && c->hidden != 64 && c->hidden != 128) return snprintf(msg, n, "hidden must be 32, 64 or 128"), ECO_EINVAL;
-  if (c->n_actions != 6 && c->n_actions != 9) return snprintf(msg, n, "n_actions must be 6 or 9"), ECO_EINVAL;
+  if (c->rules != ECO_RULES_SIMPLE && c->rules != ECO_RULES_PAPER) return snprintf(msg, n, "bad rules"), ECO_EINVAL;
+  if (c->rules == ECO_RULES_SIMPLE && c->n_actions != 6 && c->n_actions != 9)
+    return snprintf(msg, n, "n_actions must be 6 or 9 under the simple rules"), ECO_EINVAL;
+  if (c->rules == ECO_RULES_PAPER) {
+    if (c->n_actions != PA_N) return snprintf(msg, n, "n_actions must be 7 under the paper rules"), ECO_EINVAL;
+    if (c->flags & ECO_AUTO_EAT) return snprintf(msg, n, "the paper rules eat only by the eat action"), ECO_EINVAL;
+    if (c->hp_max < 1 || c->hp_child < 1 || c->hp_child > c->hp_max || c->attack_damage < 0 ||
+        c->heal_rate < 0 || c->heal_cost < 0 || c->age_div < 1 || c->starve_damage < 0 || c->e_act < 0)
+      return snprintf(msg, n, "bad HP constants"), ECO_EINVAL;
+    if (c->e_food < 1 || c->e_init < 0 || c->e_cap < 1 || c->e_cap < c->e_init || c->e_child < 1 ||
+        c->e_child > c->e_repro)
+      return snprintf(msg, n, "bad energy constants for the paper rules"), ECO_EINVAL;
+  }
   if (c->precision < ECO_FP32 || c->precision > ECO_FP8_E4M3) return snprintf(msg, n, "bad precision"), ECO_EINVAL;
   if (c->e_repro <= 0 || c->attack_den <= 0 || c->attack_num < 0 || c->e_metab < 0)
     return snprintf(msg, n, "bad energy constants"), ECO_EINVAL;
@@ -226,6 +238,10 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.hist = k.take<uint32_t>((size_t)E * 65536);
   D.place_prefix = k.take<unsigned long long>(E);
   D.place_remaining = k.take<int32_t>(E);
+  D.hp = k.take<int32_t>(slots);
+  D.age = k.take<int32_t>(slots);
+  D.dmg = k.take<int32_t>(slots);
+  D.res = k.take<int32_t>(cells);
   return (k.off + 255) & ~(size_t)255;
 }
 
@@ -292,6 +308,17 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
   R.e_repro = cfg->e_repro;
   R.attack_num = cfg->attack_num;
   R.attack_den = cfg->attack_den;
+  R.rules = cfg->rules;
+  R.hp_max = cfg->hp_max;
+  R.hp_child = cfg->hp_child;
+  R.attack_damage = cfg->attack_damage;
+  R.heal_rate = cfg->heal_rate;
+  R.heal_cost = cfg->heal_cost;
+  R.age_div = cfg->age_div;
+  R.starve_damage = cfg->starve_damage;
+  R.e_act = cfg->e_act;
+  R.e_cap = cfg->e_cap;
+  R.e_child = cfg->e_child;
   h->ws = reinterpret_cast<uint8_t *>(dev_workspace);
   h->ws_bytes = bytes;
   carve(cfg, h->L, h->ws, &h->d, &h->env_dev);
@@ -608,6 +635,9 @@ extern "C" int eco_read_state(eco_handle *h, int32_t env, eco_state_view *out) {
   std::vector<int32_t> occ(N), pos(S), energy(S), parent(S), birth(S);
   long long step = 0;
   cudaStream_t s = h->stream;
+  if (out->hp) CUDA_TRY(h, cudaMemcpyAsync(out->hp, h->d.hp + ed.slot_off, 4 * (size_t)S, cudaMemcpyDeviceToHost, s));
+  if (out->age) CUDA_TRY(h, cudaMemcpyAsync(out->age, h->d.age + ed.slot_off, 4 * (size_t)S, cudaMemcpyDeviceToHost, s));
+  if (out->res) CUDA_TRY(h, cudaMemcpyAsync(out->res, h->d.res + ed.cell_off, 4 * (size_t)N, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(h, cudaMemcpyAsync(cellf.data(), h->d.cellf + ed.cell_off, N, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(h, cudaMemcpyAsync(occ.data(), h->d.occ + ed.cell_off, 4 * (size_t)N, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(h, cudaMemcpyAsync(alive.data(), h->d.alive + ed.slot_off, S, cudaMemcpyDeviceToHost, s));
@@ -647,6 +677,9 @@ extern "C" int eco_write_state(eco_handle *h, int32_t env, const eco_state_view 
   if (cells && !(in->food && in->wall && in->occ)) return fail(h, ECO_EINVAL, "food, wall and occ must be written together");
   const bool where = in->alive || in->x || in->y;
   if (where && !(in->alive && in->x && in->y)) return fail(h, ECO_EINVAL, "alive, x and y must be written together");
+  const bool paper = h->R.rules == RULES_PAPER;
+  if (paper && (cells || in->res) && !(cells && in->res))
+    return fail(h, ECO_EINVAL, "under the paper rules res is written together with food, wall and occ");
   std::vector<uint8_t> cellf, alive;
   std::vector<int32_t> occ, pos;
   if (cells) {
@@ -654,11 +687,14 @@ extern "C" int eco_write_state(eco_handle *h, int32_t env, const eco_state_view 
     occ.resize(N);
     for (int c = 0; c < N; ++c) {
       if (in->occ[c] < -1 || in->occ[c] >= S) return fail(h, ECO_EINVAL, "occ[%d] out of range", c);
-      cellf[c] = (uint8_t)((in->food[c] ? CELL_FOOD : 0) | (in->wall[c] ? CELL_WALL : 0) | (in->occ[c] >= 0 ? CELL_AGENT : 0));
+      if (paper && in->res[c] < 0) return fail(h, ECO_EINVAL, "res[%d] negative", c);
+      const bool food = paper ? in->res[c] > 0 : in->food[c] != 0;
+      cellf[c] = (uint8_t)((food ? CELL_FOOD : 0) | (in->wall[c] ? CELL_WALL : 0) | (in->occ[c] >= 0 ? CELL_AGENT : 0));
       occ[c] = in->occ[c] < 0 ? -1 : in->occ[c] + ed.slot_off;
     }
     CUDA_TRY(h, cudaMemcpyAsync(h->d.cellf + ed.cell_off, cellf.data(), N, cudaMemcpyHostToDevice, s));
     CUDA_TRY(h, cudaMemcpyAsync(h->d.occ + ed.cell_off, occ.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s));
+    if (paper) CUDA_TRY(h, cudaMemcpyAsync(h->d.res + ed.cell_off, in->res, 4 * (size_t)N, cudaMemcpyHostToDevice, s));
   }
   if (where) {
     alive.assign(in->alive, in->alive + S);
@@ -675,6 +711,8 @@ extern "C" int eco_write_state(eco_handle *h, int32_t env, const eco_state_view 
   if (in->energy) CUDA_TRY(h, cudaMemcpyAsync(h->d.energy + ed.slot_off, in->energy, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
   if (in->parent) CUDA_TRY(h, cudaMemcpyAsync(h->d.parent + ed.slot_off, in->parent, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
   if (in->birth_step) CUDA_TRY(h, cudaMemcpyAsync(h->d.birth + ed.slot_off, in->birth_step, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
+  if (in->hp) CUDA_TRY(h, cudaMemcpyAsync(h->d.hp + ed.slot_off, in->hp, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
+  if (in->age) CUDA_TRY(h, cudaMemcpyAsync(h->d.age + ed.slot_off, in->age, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
   if (in->step) {
     // all environments share one step counter
     long long st = *in->step;

@@ -132,7 +132,24 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
       }
     }
     const int a = d.act[slot];
-    if ((R.flags & F_AUTO_EAT) || (n_actions > ACT_EAT && a == ACT_EAT)) {
+    if (R.rules == RULES_PAPER) {
+      // one bite: min(e_food, energy on the cell, room in the stomach)
+      if (a == PA_EAT) {
+        const int gpos = ed.cell_off + pos;
+        const int r = d.res[gpos];
+        const int bite = min(min(R.e_food, r), R.e_cap - d.energy[slot]);
+        if (bite > 0) {
+          d.res[gpos] = r - bite;
+          d.energy[slot] += bite;
+          stat_add(d.stats_step, e, ST_EATEN, 1);
+          stat_add(d.stats_step, e, ST_EATEN_ENERGY, bite);
+          if (r == bite) {
+            d.cellf[gpos] &= (uint8_t)~CELL_FOOD;
+            stat_add(d.stats_step, e, ST_FOOD_EMPTIED, 1);
+          }
+        }
+      }
+    } else if ((R.flags & F_AUTO_EAT) || (n_actions > ACT_EAT && a == ACT_EAT)) {
       const int gpos = ed.cell_off + pos;
       const uint8_t cf = d.cellf[gpos];
       if (cf & CELL_FOOD) {
@@ -145,7 +162,9 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
 }
 
 // A8 (part 1): clear this step's move claims; attackers claim the agent on
-// the faced cell (post-move occupancy).
+// the faced cell (post-move occupancy).  Paper rules: an attacker adds
+// attack_damage to every agent in the 3x3 square in front of it (1..3 cells
+// ahead, one to either side); damage from several attackers adds up.
 __device__ void ph_attack_claim(const Dev &d, const Rules &R, int g0, int gs) {
   const int n = d.counters[CNT_N_ALIVE];
   const uint32_t t = (uint32_t)d.step[0];
@@ -159,7 +178,28 @@ __device__ void ph_attack_claim(const Dev &d, const Rules &R, int g0, int gs) {
       if (R.flags & F_CANCEL_ALL) d.cnt_move[ed.cell_off + tc] = 0u;
     }
     int victim = -1;
-    if (d.act[slot] == ACT_ATTACK) {
+    if (R.rules == RULES_PAPER) {
+      if (d.act[slot] == PA_ATTACK) {
+        const int side = ed.side;
+        const int pos = d.pos[slot];
+        const int px = pos % side, py = pos / side;
+        const int f = d.facing[slot], rt = (f + 1) & 3;
+        int hits = 0;
+        for (int fw = 1; fw <= 3; ++fw) {
+          for (int lat = -1; lat <= 1; ++lat) {
+            const int cx = wrapi(px + fw * dir_dx(f) + lat * dir_dx(rt), side);
+            const int cy = wrapi(py + fw * dir_dy(f) + lat * dir_dy(rt), side);
+            const int v = d.occ[ed.cell_off + cy * side + cx];
+            if (v >= 0) {
+              atomicAdd(&d.dmg[v], R.attack_damage);
+              ++hits;
+            }
+          }
+        }
+        stat_add(d.stats_step, e, ST_ATTACK_HITS, hits);
+        stat_add(d.stats_step, e, ST_DAMAGE, hits * R.attack_damage);
+      }
+    } else if (d.act[slot] == ACT_ATTACK) {
       const int c = step_cell(d.pos[slot], d.facing[slot], ed.side);
       const int v = d.occ[ed.cell_off + c];
       if (v >= 0) {
@@ -176,6 +216,7 @@ __device__ void ph_attack_claim(const Dev &d, const Rules &R, int g0, int gs) {
 // A8 (part 2): the winning attacker of each victim takes floor(e * num /
 // den) of the victim's post-eat energy (read here, written only later).
 __device__ void ph_attack_gain(const Dev &d, const Rules &R, int g0, int gs) {
+  if (R.rules == RULES_PAPER) return;  // damage is applied in the health phase
   const int n = d.counters[CNT_N_ALIVE];
   for (int i = g0; i < n; i += gs) {
     const int slot = d.alive_list[i];
@@ -194,11 +235,72 @@ __device__ void ph_attack_gain(const Dev &d, const Rules &R, int g0, int gs) {
   }
 }
 
-// A8 (part 3) + A9: apply the transfer, pay metabolism, die at e <= 0.
+// Paper rules, one agent: pay the action's cost (starving when it exceeds
+// the energy), take the attack and age damage, heal from energy, and die at
+// HP <= 0, dropping the energy on the cell; survivors age by one step.
+__device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int slot) {
+  int en = d.energy[slot];
+  int hp = d.hp[slot];
+  const int age = d.age[slot];
+  const int cost = R.e_metab + (d.act[slot] != PA_REST ? R.e_act : 0);
+  int paid = cost, starved = 0, healed = 0;
+  if (en >= cost) {
+    en -= cost;
+  } else {
+    paid = en;
+    en = 0;
+    hp -= R.starve_damage;
+    starved = 1;
+  }
+  hp -= d.dmg[slot];
+  d.dmg[slot] = 0;
+  hp -= age / R.age_div;
+  if (hp > 0 && hp < R.hp_max && R.heal_rate > 0 && en >= R.heal_cost) {
+    hp = min(hp + R.heal_rate, R.hp_max);
+    en -= R.heal_cost;
+    healed = 1;
+  }
+  const int e = d.env_of[slot];
+  stat_add(d.stats_step, e, ST_METAB_PAID, paid);
+  stat_add(d.stats_step, e, ST_STARVED, starved);
+  stat_add(d.stats_step, e, ST_HEALS, healed);
+  if (hp <= 0) {
+    // one agent per cell, so the cell's energy and flags are this agent's
+    // to change here
+    const int gpos = d.env[e].cell_off + d.pos[slot];
+    uint8_t cf = (uint8_t)(d.cellf[gpos] & ~CELL_AGENT);
+    if (en > 0) {
+      const int r = d.res[gpos];
+      d.res[gpos] = r + en;
+      if (r == 0) {
+        cf |= (uint8_t)CELL_FOOD;
+        stat_add(d.stats_step, e, ST_FOOD_REFILLED, 1);
+      }
+    }
+    d.cellf[gpos] = cf;
+    d.occ[gpos] = -1;
+    d.alive[slot] = 0;
+    stat_add(d.stats_step, e, ST_DEATHS, 1);
+    stat_add(d.stats_step, e, ST_DEAD_ENERGY, en);
+    en = 0;
+    hp = 0;
+  } else {
+    d.age[slot] = age + 1;
+  }
+  d.hp[slot] = hp;
+  d.energy[slot] = en;
+}
+
+// A8 (part 3) + A9: apply the transfer, pay metabolism, die at e <= 0
+// (paper rules: health_paper).
 __device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs) {
   const int n = d.counters[CNT_N_ALIVE];
   for (int i = g0; i < n; i += gs) {
     const int slot = d.alive_list[i];
+    if (R.rules == RULES_PAPER) {
+      health_paper(d, R, slot);
+      continue;
+    }
     int en = d.energy[slot];
     const unsigned long long ca = d.claim_att[slot];
     const int loss = ca ? (int)(((long long)en * R.attack_num) / R.attack_den) : 0;
@@ -218,15 +320,17 @@ __device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs) {
   }
 }
 
-// A10 (part 1): agents with e >= e_repro claim the free non-wall cell
-// behind them and join their environment's contender list.
+// A10 (part 1): agents with e >= e_repro (paper rules: that chose to
+// reproduce) claim the free non-wall cell behind them and join their
+// environment's contender list.
 __device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs) {
   const int n = d.counters[CNT_N_ALIVE];
   const uint32_t t = (uint32_t)d.step[0];
   for (int i = g0; i < n; i += gs) {
     const int slot = d.alive_list[i];
     int bt = -1;
-    if (d.alive[slot] && d.energy[slot] >= R.e_repro) {
+    if (d.alive[slot] && d.energy[slot] >= R.e_repro &&
+        (R.rules != RULES_PAPER || d.act[slot] == PA_REPRODUCE)) {
       const int e = d.env_of[slot];
       const EnvDesc ed = d.env[e];
       const int c = step_cell(d.pos[slot], (d.facing[slot] + 2) & 3, ed.side);
@@ -247,8 +351,8 @@ __device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs) {
 // ---------------------------------------------------------------------------
 // A10 (part 2): slot assignment, one CTA per environment.  Cell winners in
 // ascending slot order take the free slots in ascending order; the child
-// gets floor(e/2) of the parent's energy, the parent's facing, and the cell
-// behind.  Winners (at most kBirthCap per step) are sorted in shared memory
+// gets floor(e/2) of the parent's energy (paper rules: e_child, and hp_child
+// HP), the parent's facing, and the cell behind.  Winners (at most kBirthCap per step) are sorted in shared memory
 // and only the first n_winners free slots are searched for; more
 // contenders than kBirthCap fall back to a full scan of the slots.
 // ---------------------------------------------------------------------------
@@ -261,12 +365,15 @@ struct BirthSmem {
   int nwin;
 };
 
-__device__ __forceinline__ void make_child(const Dev &d, const EnvDesc &ed, int p, int c, int bt,
-                                           uint32_t t) {
+__device__ __forceinline__ void make_child(const Dev &d, const Rules &R, const EnvDesc &ed, int p,
+                                           int c, int bt, uint32_t t) {
+  const bool paper = R.rules == RULES_PAPER;
   const int en = d.energy[p];
-  const int ce = en / 2;
+  const int ce = paper ? R.e_child : en / 2;
   d.energy[p] = en - ce;
   d.energy[c] = ce;
+  d.hp[c] = paper ? R.hp_child : 0;
+  d.age[c] = 0;
   d.alive[c] = 1;
   d.pos[c] = bt;
   d.facing[c] = d.facing[p];
@@ -278,7 +385,7 @@ __device__ __forceinline__ void make_child(const Dev &d, const EnvDesc &ed, int 
   d.births[b] = make_int2(p, c);
 }
 
-__device__ void birth_assign_env(const Dev &d, int e, BirthSmem &S) {
+__device__ void birth_assign_env(const Dev &d, const Rules &R, int e, BirthSmem &S) {
   const int nc = d.birth_contenders[e];
   if (nc == 0) return;  // uniform across the CTA
   const EnvDesc ed = d.env[e];
@@ -356,7 +463,7 @@ __device__ void birth_assign_env(const Dev &d, int e, BirthSmem &S) {
       const int bt = d.tgt[p];
       d.claim_birth[ed.cell_off + bt] = 0ull;
       if (i < nfree) {
-        make_child(d, ed, p, ed.slot_off + S.free_[i], bt, t);
+        make_child(d, R, ed, p, ed.slot_off + S.free_[i], bt, t);
         ++born;
       } else {
         ++failed;
@@ -399,7 +506,7 @@ __device__ void birth_assign_env(const Dev &d, int e, BirthSmem &S) {
         ++failed;
         continue;
       }
-      make_child(d, ed, p, ed.slot_off + d.free_list[ed.slot_off + r], bt, t);
+      make_child(d, R, ed, p, ed.slot_off + d.free_list[ed.slot_off + r], bt, t);
       ++born;
     }
   }
@@ -409,8 +516,8 @@ __device__ void birth_assign_env(const Dev &d, int e, BirthSmem &S) {
   __syncthreads();  // S is reused by the next environment of this CTA
 }
 
-__device__ void ph_birth_assign(const Dev &d, int b0, int bs, BirthSmem &S) {
-  for (int e = b0; e < d.n_envs; e += bs) birth_assign_env(d, e, S);
+__device__ void ph_birth_assign(const Dev &d, const Rules &R, int b0, int bs, BirthSmem &S) {
+  for (int e = b0; e < d.n_envs; e += bs) birth_assign_env(d, R, e, S);
 }
 
 // ---------------------------------------------------------------------------
@@ -568,11 +675,18 @@ __device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs) {
                        (cf.z & (CELL_WALL | CELL_FOOD)) && (cf.w & (CELL_WALL | CELL_FOOD)));
     if (any) {
       const U4 r = philox(t, (uint32_t)((c0 - ed.cell_off) >> 2), 0u, 0u, ed.seed, S_REGROW);
-      if (!(cf.x & (CELL_WALL | CELL_FOOD)) && r.x < R.thr_regrow) { cf.x |= CELL_FOOD; ++grown; }
-      if (!(cf.y & (CELL_WALL | CELL_FOOD)) && r.y < R.thr_regrow) { cf.y |= CELL_FOOD; ++grown; }
-      if (!(cf.z & (CELL_WALL | CELL_FOOD)) && r.z < R.thr_regrow) { cf.z |= CELL_FOOD; ++grown; }
-      if (!(cf.w & (CELL_WALL | CELL_FOOD)) && r.w < R.thr_regrow) { cf.w |= CELL_FOOD; ++grown; }
-      if (grown) reinterpret_cast<uchar4 *>(d.cellf)[g] = cf;
+      int mask = 0;
+      if (!(cf.x & (CELL_WALL | CELL_FOOD)) && r.x < R.thr_regrow) { cf.x |= CELL_FOOD; mask |= 1; }
+      if (!(cf.y & (CELL_WALL | CELL_FOOD)) && r.y < R.thr_regrow) { cf.y |= CELL_FOOD; mask |= 2; }
+      if (!(cf.z & (CELL_WALL | CELL_FOOD)) && r.z < R.thr_regrow) { cf.z |= CELL_FOOD; mask |= 4; }
+      if (!(cf.w & (CELL_WALL | CELL_FOOD)) && r.w < R.thr_regrow) { cf.w |= CELL_FOOD; mask |= 8; }
+      grown = __popc(mask);
+      if (grown) {
+        reinterpret_cast<uchar4 *>(d.cellf)[g] = cf;
+        if (R.rules == RULES_PAPER)  // one bite of energy on each regrown cell
+          for (int k = 0; k < 4; ++k)
+            if (mask & (1 << k)) d.res[c0 + k] = R.e_food;
+      }
     }
     stat_add(d.stats_step, e, ST_REGROWN, grown);
   }
@@ -588,7 +702,7 @@ __device__ void ph_finish(const Dev &d, const Rules &R) {
     long long as = 0;
     for (int a = 0; a < 16; ++a) as += st[ST_ACT0 + a];
     st[ST_AGENT_STEPS] = as;
-    st[ST_ATTACKS] = st[ST_ACT0 + ACT_ATTACK];
+    st[ST_ATTACKS] = st[ST_ACT0 + (R.rules == RULES_PAPER ? PA_ATTACK : ACT_ATTACK)];
   }
   __syncthreads();
   for (int i = threadIdx.x; i < d.n_envs * N_ST; i += blockDim.x) {
@@ -602,10 +716,18 @@ __device__ void ph_finish(const Dev &d, const Rules &R) {
     } else if (k == ST_ALIVE) {
       v = tot[k] + st[ST_BIRTHS] - st[ST_DEATHS];
     } else if (k == ST_FOOD_TOTAL) {
-      v = tot[k] + st[ST_REGROWN] - st[ST_EATEN];
+      v = R.rules == RULES_PAPER ? tot[k] + st[ST_REGROWN] - st[ST_FOOD_EMPTIED] + st[ST_FOOD_REFILLED]
+                                 : tot[k] + st[ST_REGROWN] - st[ST_EATEN];
     } else if (k == ST_ENERGY_TOTAL) {
-      v = tot[k] + (long long)R.e_food * st[ST_EATEN] - (long long)R.e_metab * st[ST_AGENT_STEPS] -
-          st[ST_DEAD_ENERGY];
+      v = R.rules == RULES_PAPER
+              ? tot[k] + st[ST_EATEN_ENERGY] - st[ST_METAB_PAID] - (long long)R.heal_cost * st[ST_HEALS] -
+                    st[ST_DEAD_ENERGY]
+              : tot[k] + (long long)R.e_food * st[ST_EATEN] - (long long)R.e_metab * st[ST_AGENT_STEPS] -
+                    st[ST_DEAD_ENERGY];
+    } else if (k == ST_RES_TOTAL) {
+      v = R.rules == RULES_PAPER
+              ? tot[k] + (long long)R.e_food * st[ST_REGROWN] - st[ST_EATEN_ENERGY] + st[ST_DEAD_ENERGY]
+              : 0;
     } else {
       last[k] = st[k];
       tot[k] += st[k];
@@ -641,9 +763,9 @@ __global__ void k_attack_claim(Dev d, Rules R) { ph_attack_claim(d, R, GRID_ARGS
 __global__ void k_attack_gain(Dev d, Rules R) { ph_attack_gain(d, R, GRID_ARGS); }
 __global__ void k_metab_death(Dev d, Rules R) { ph_metab_death(d, R, GRID_ARGS); }
 __global__ void k_birth_claim(Dev d, Rules R) { ph_birth_claim(d, R, GRID_ARGS); }
-__global__ void __launch_bounds__(1024) k_birth_assign(Dev d) {
+__global__ void __launch_bounds__(1024) k_birth_assign(Dev d, Rules R) {
   __shared__ BirthSmem S;
-  ph_birth_assign(d, blockIdx.x, gridDim.x, S);
+  ph_birth_assign(d, R, blockIdx.x, gridDim.x, S);
 }
 __global__ void __launch_bounds__(256) k_mutate(Dev d, Layout L, Rules R) {
   extern __shared__ __align__(16) float msm[];
@@ -711,7 +833,7 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   if (!grid_sync(d, nb, &s_flag)) return;
   ph_birth_claim(d, R, g0, gs);
   if (!grid_sync(d, nb, &s_flag)) return;
-  ph_birth_assign(d, blockIdx.x, gridDim.x, S);
+  ph_birth_assign(d, R, blockIdx.x, gridDim.x, S);
   if (!grid_sync(d, nb, &s_flag)) return;
   ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale);
   ph_regrow(d, R, g0, gs);
@@ -774,7 +896,7 @@ cudaError_t launch_env_phases(const Dev &d, const Layout &L, const Rules &R, con
   k_attack_gain<<<g.slot_blocks, T, 0, s>>>(d, R);
   k_metab_death<<<g.slot_blocks, T, 0, s>>>(d, R);
   k_birth_claim<<<g.slot_blocks, T, 0, s>>>(d, R);
-  k_birth_assign<<<d.n_envs, 1024, 0, s>>>(d);
+  k_birth_assign<<<d.n_envs, 1024, 0, s>>>(d, R);
   k_mutate<<<g.birth_blocks, 256, msmem, s>>>(d, L, R);
   k_regrow<<<g.cell_blocks, T, 0, s>>>(d, R);
   k_finish<<<1, 1024, 0, s>>>(d, R);

@@ -20,7 +20,8 @@ __device__ __forceinline__ unsigned long long place_key(const EnvDesc &ed, int l
   return ((unsigned long long)word_of(r, local_cell & 3) << 32) | (unsigned long long)(uint32_t)local_cell;
 }
 
-// Walls, food, empty occupancy, cleared claims.
+// Walls, food, empty occupancy, cleared claims.  Paper rules: a food cell
+// holds one bite, e_food energy.
 __global__ void k_init_cells(Dev d, Rules R) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.total_cells; c += gridDim.x * blockDim.x) {
     const int e = env_of_cell(d.env, d.n_envs, c);
@@ -31,6 +32,7 @@ __global__ void k_init_cells(Dev d, Rules R) {
     const U4 rf = philox((uint32_t)(lc >> 2), 0u, 0u, 0u, ed.seed, S_FOOD_INIT);
     const bool food = !wall && word_of(rf, lc & 3) < R.thr_food;
     d.cellf[c] = (uint8_t)((wall ? CELL_WALL : 0u) | (food ? CELL_FOOD : 0u));
+    d.res[c] = (R.rules == RULES_PAPER && food) ? R.e_food : 0;
     d.occ[c] = -1;
     d.claim_move[c] = 0ull;
     d.cnt_move[c] = 0u;
@@ -63,7 +65,23 @@ __global__ void k_init_agents(Dev d, Rules R) {
     d.tgt[s] = -1;
     d.gain[s] = 0;
     d.claim_att[s] = 0ull;
+    d.hp[s] = (founder && R.rules == RULES_PAPER) ? R.hp_max : 0;
+    d.age[s] = 0;
+    d.dmg[s] = 0;
   }
+}
+
+// Sum of a 64-bit value over the CTA (every thread gets the total).
+__device__ long long block_sum_ll(long long v, unsigned long long *acc) {
+  if (threadIdx.x == 0) *acc = 0ull;
+  __syncthreads();
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+  if ((threadIdx.x & 31) == 0) atomicAdd(acc, (unsigned long long)v);
+  __syncthreads();
+  const long long total = (long long)*acc;
+  __syncthreads();
+  return total;
 }
 
 // Radix-select round: histogram of the 16-bit digit at `shift` among the
@@ -242,7 +260,8 @@ __global__ void k_requant_fp8(Dev d, Layout L, int slot0, int n) {
   }
 }
 
-// Initial statistics: alive = K, food count, energy = K * e_init, step 0.
+// Initial statistics: alive = K, food count, energy = K * e_init, step 0;
+// paper rules: energy on cells = food count * e_food.
 __global__ void __launch_bounds__(1024) k_init_stats(Dev d, Rules R) {
   __shared__ int sh[33];
   const int e = blockIdx.x;
@@ -257,6 +276,7 @@ __global__ void __launch_bounds__(1024) k_init_stats(Dev d, Rules R) {
     if (k == ST_ALIVE) v = ed.init_alive;
     else if (k == ST_FOOD_TOTAL) v = total;
     else if (k == ST_ENERGY_TOTAL) v = (long long)ed.init_alive * R.e_init;
+    else if (k == ST_RES_TOTAL && R.rules == RULES_PAPER) v = (long long)total * R.e_food;
     d.stats_total[e * N_ST + k] = v;
     d.stats_last[e * N_ST + k] = v;
     d.stats_step[e * N_ST + k] = 0;
@@ -278,15 +298,19 @@ __global__ void k_init_static(Dev d) {
     d.occ[c] = -1;
 }
 
-// One CTA per environment: alive count, food count and energy sum of the
-// current state become the "now" statistics; the step counter is copied.
-__global__ void __launch_bounds__(1024) k_recount(Dev d) {
-  __shared__ int sh[33];
+// One CTA per environment: alive count, food count, energy sum (and, under
+// the paper rules, the energy lying on cells) of the current state become
+// the "now" statistics; the step counter is copied.
+__global__ void __launch_bounds__(1024) k_recount(Dev d, Rules R) {
+  __shared__ unsigned long long acc;
   const int e = blockIdx.x;
   const EnvDesc ed = d.env[e];
   const int n = ed.side * ed.side;
-  int food = 0, alive = 0, energy = 0;
-  for (int c = threadIdx.x; c < n; c += blockDim.x) food += (d.cellf[ed.cell_off + c] & CELL_FOOD) ? 1 : 0;
+  long long food = 0, alive = 0, energy = 0, res = 0;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    food += (d.cellf[ed.cell_off + c] & CELL_FOOD) ? 1 : 0;
+    res += d.res[ed.cell_off + c];
+  }
   for (int s = threadIdx.x; s < ed.n_slots; s += blockDim.x) {
     const int g = ed.slot_off + s;
     if (d.alive[g]) {
@@ -294,16 +318,17 @@ __global__ void __launch_bounds__(1024) k_recount(Dev d) {
       energy += d.energy[g];
     }
   }
-  int ft, at, et;
-  block_exclusive_scan(food, &ft, sh);
-  block_exclusive_scan(alive, &at, sh);
-  block_exclusive_scan(energy, &et, sh);
+  const long long ft = block_sum_ll(food, &acc);
+  const long long at = block_sum_ll(alive, &acc);
+  const long long et = block_sum_ll(energy, &acc);
+  const long long rt = block_sum_ll(res, &acc);
   if (threadIdx.x == 0) {
     const long long t = d.step[0];
     long long *tot = d.stats_total + e * N_ST, *last = d.stats_last + e * N_ST;
     tot[ST_ALIVE] = last[ST_ALIVE] = at;
     tot[ST_FOOD_TOTAL] = last[ST_FOOD_TOTAL] = ft;
     tot[ST_ENERGY_TOTAL] = last[ST_ENERGY_TOTAL] = et;
+    tot[ST_RES_TOTAL] = last[ST_RES_TOTAL] = R.rules == RULES_PAPER ? rt : 0;
     tot[ST_STEP] = last[ST_STEP] = t;
   }
 }
@@ -315,8 +340,7 @@ cudaError_t launch_init_static(const Dev &d, const EnvGrid &g, cudaStream_t s) {
 }
 
 cudaError_t launch_recount(const Dev &d, const Rules &R, cudaStream_t s) {
-  (void)R;
-  k_recount<<<d.n_envs, 1024, 0, s>>>(d);
+  k_recount<<<d.n_envs, 1024, 0, s>>>(d, R);
   return cudaGetLastError();
 }
 

@@ -7,7 +7,10 @@
 //     cnt_move u32, claim_birth u64;
 //   per slot (all environments concatenated): alive u8, pos i32 (env-local
 //     cell y*L+x), facing u8, energy i32, parent i32 (env-local), birth i32,
-//     act u8, env u16, tgt i32, gain i32, claim_att u64, logits f32[A];
+//     act u8, env u16, tgt i32, gain i32, claim_att u64, logits f32[A],
+//     hp i32, age i32, dmg i32 (paper rules);
+//   per cell, paper rules: res i32 (energy lying on the cell; the food bit
+//     of cellf is res > 0);
 //   weights: FP32 masters [slot][mstride] and, for BF16/FP8, the streamed
 //     copy [slot][stride], both in the kernel's tiled block layout below.
 //
@@ -62,6 +65,23 @@ enum : int {
   ACT_EAT = 8,
 };
 
+// Paper rule set (Sec. 3.2 "Actions", one resource).
+enum : int {
+  PA_REST = 0,
+  PA_CW = 1,
+  PA_CCW = 2,
+  PA_FORWARD = 3,
+  PA_ATTACK = 4,
+  PA_EAT = 5,
+  PA_REPRODUCE = 6,
+  PA_N = 7,
+};
+
+enum : int {
+  RULES_SIMPLE = 0,
+  RULES_PAPER = 1,
+};
+
 enum : int {
   PREC_FP32 = 0,
   PREC_BF16 = 1,
@@ -95,6 +115,14 @@ enum : int {
   ST_ALIVE,
   ST_FOOD_TOTAL,
   ST_ENERGY_TOTAL,
+  ST_RES_TOTAL,
+  ST_EATEN_ENERGY,
+  ST_METAB_PAID,
+  ST_HEALS,
+  ST_STARVED,
+  ST_DAMAGE,
+  ST_FOOD_EMPTIED,
+  ST_FOOD_REFILLED,
   N_ST
 };
 
@@ -188,6 +216,9 @@ struct Rules {
   float sigma;
   uint32_t thr_food, thr_regrow, thr_wall;
   int e_init, e_metab, e_food, e_repro, attack_num, attack_den;
+  int rules;  // RULES_SIMPLE / RULES_PAPER; the rest is paper rules only
+  int hp_max, hp_child, attack_damage, heal_rate, heal_cost, age_div, starve_damage;
+  int e_act, e_cap, e_child;
 };
 
 // Device pointers (all inside the caller's workspace).
@@ -231,6 +262,10 @@ struct Dev {
   unsigned long long *place_prefix;  // [n_envs] (prefix, remaining)
   int32_t *place_remaining; // [n_envs] placement radix select
   uint8_t *bflag;          // [total_slots] birth pass flags
+  int32_t *hp;             // [total_slots] paper rules: HP (quarter points)
+  int32_t *age;            // [total_slots] paper rules: steps survived
+  int32_t *dmg;            // [total_slots] paper rules: attack damage this step
+  int32_t *res;            // [total_cells] paper rules: energy on the cell
 };
 
 enum : int {

@@ -255,11 +255,26 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
       xs[3 * c + 2] = (cf & CELL_WALL) ? 1.0f : 0.0f;
     }
     if (lane < R.n_scalars) {
+      // [e / e_repro, one-hot facing (8-scalar form), zeros]; the paper
+      // rules fill the zeros with HP / hp_max, age / (age + age_div) and
+      // r / (r + e_food), r the energy lying on the agent's cell
       float v = 0.0f;
       if (lane == 0)
         v = (float)d.energy[slot] / (float)R.e_repro;
       else if (R.n_scalars >= 8 && lane == 1 + f)
         v = 1.0f;
+      if (R.rules == RULES_PAPER) {
+        const int extra = lane - (R.n_scalars >= 8 ? 5 : 1);
+        if (extra == 0) {
+          v = (float)d.hp[slot] / (float)R.hp_max;
+        } else if (extra == 1) {
+          const float a = (float)d.age[slot];
+          v = a / (a + (float)R.age_div);
+        } else if (extra == 2) {
+          const float r = (float)d.res[ed.cell_off + pos];
+          v = r / (r + (float)R.e_food);
+        }
+      }
       xs[3 * kk + lane] = v;
     }
     }
@@ -343,8 +358,21 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
         const int f = d.facing[slot];
         const uint8_t *cellf = d.cellf + ed.cell_off;
         int nf = f, tc = -1;
-        if (best >= ACT_N && best <= ACT_W) {
+        bool move = false;
+        if (R.rules == RULES_PAPER) {
+          // rotate clockwise / counter-clockwise, or one cell forward
+          if (best == PA_CW) nf = (f + 1) & 3;
+          else if (best == PA_CCW) nf = (f + 3) & 3;
+          move = best == PA_FORWARD;
+        } else if (best >= ACT_N && best <= ACT_W) {
           nf = (best == ACT_N) ? 0 : (best == ACT_S) ? 2 : (best == ACT_E) ? 1 : 3;
+          move = true;
+        } else if (best == ACT_LEFT) {
+          nf = (f + 3) & 3;
+        } else if (best == ACT_RIGHT) {
+          nf = (f + 1) & 3;
+        }
+        if (move) {
           const int c = step_cell(pos, nf, side);
           if (cellf[c] & (CELL_WALL | CELL_AGENT)) {
             blk = 1;
@@ -355,10 +383,6 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
             if (R.flags & F_CANCEL_ALL) atomicAdd(&d.cnt_move[ed.cell_off + c], 1u);
             tc = c;
           }
-        } else if (best == ACT_LEFT) {
-          nf = (f + 3) & 3;
-        } else if (best == ACT_RIGHT) {
-          nf = (f + 1) & 3;
         }
         d.facing[slot] = (uint8_t)nf;
         d.tgt[slot] = tc;

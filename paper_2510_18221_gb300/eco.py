@@ -21,20 +21,26 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libeco.so")
 
-ECO_ABI_VERSION = 1
+ECO_ABI_VERSION = 2
 ECO_OK, ECO_EINVAL, ECO_ENOMEM, ECO_ECUDA, ECO_ETIMEOUT, ECO_EABI = 0, -1, -2, -3, -4, -5
 ECO_FP32, ECO_BF16, ECO_FP8_E4M3 = 0, 1, 2
 ECO_AUTO_EAT, ECO_ROTATE_OBS, ECO_CANCEL_ALL, ECO_GREEDY = 1, 2, 4, 8
 PRECISIONS = {"fp32": ECO_FP32, "bf16": ECO_BF16, "fp8": ECO_FP8_E4M3}
 ECO_POLICY_PLAIN, ECO_POLICY_PAPER = 0, 1
 POLICY_FORMS = {"plain": ECO_POLICY_PLAIN, "paper": ECO_POLICY_PAPER}
+ECO_RULES_SIMPLE, ECO_RULES_PAPER = 0, 1
+RULES = {"simple": ECO_RULES_SIMPLE, "paper": ECO_RULES_PAPER}
+PAPER_RULE_FIELDS = ("hp_max", "hp_child", "attack_damage", "heal_rate", "heal_cost",
+                     "age_div", "starve_damage", "e_act", "e_cap", "e_child")
 FLAGS = {"auto_eat": ECO_AUTO_EAT, "rotate_obs": ECO_ROTATE_OBS,
          "cancel_all": ECO_CANCEL_ALL, "greedy": ECO_GREEDY}
 
 STAT_NAMES = (["step", "agent_steps"] + ["act%d" % i for i in range(16)] +
               ["moves", "move_blocked", "move_lost", "eaten", "attacks", "attack_hits",
                "energy_transferred", "deaths", "dead_energy", "births", "failed_births",
-               "regrown", "alive", "food_total", "energy_total"])
+               "regrown", "alive", "food_total", "energy_total",
+               "res_total", "eaten_energy", "metab_paid", "heals", "starved", "damage",
+               "food_emptied", "food_refilled"])
 ECO_N_STATS = len(STAT_NAMES)
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -57,7 +63,8 @@ class eco_config(ctypes.Structure):
         ("attack_num", ctypes.c_int32), ("attack_den", ctypes.c_int32),
         ("policy_variant", ctypes.c_int32), ("launch_mode", ctypes.c_int32),
         ("policy_form", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
-    ]
+        ("rules", ctypes.c_int32),
+    ] + [(k, ctypes.c_int32) for k in PAPER_RULE_FIELDS]
 
 
 class eco_stats(ctypes.Structure):
@@ -66,7 +73,8 @@ class eco_stats(ctypes.Structure):
 
 class eco_state_view(ctypes.Structure):
     _fields_ = [(n, _vp) for n in ("food", "wall", "occ", "alive", "x", "y", "facing",
-                                   "energy", "parent", "birth_step", "step")]
+                                   "energy", "parent", "birth_step", "step", "hp", "age",
+                                   "res")]
 
 
 _lib = None
@@ -226,7 +234,8 @@ def eco_move_claims_noalloc(side: int, n_agents: int, pos: int, act: int, facing
 
 _SHARED = ("patch_k", "n_scalars", "hidden", "n_actions", "precision", "flags", "sigma",
            "food_density", "regrow_p", "wall_density", "e_init", "e_metab", "e_food",
-           "e_repro", "attack_num", "attack_den", "policy_form", "n_hidden")
+           "e_repro", "attack_num", "attack_den", "policy_form", "n_hidden",
+           "rules") + PAPER_RULE_FIELDS
 
 
 def make_config(envs: Sequence[dict], policy_variant: int = 0, launch_mode: int = 0):
@@ -255,7 +264,9 @@ def make_config(envs: Sequence[dict], policy_variant: int = 0, launch_mode: int 
         wall_density=w0["wall_density"], e_init=w0["e_init"], e_metab=w0["e_metab"],
         e_food=w0["e_food"], e_repro=w0["e_repro"], attack_num=w0["attack_num"],
         attack_den=w0["attack_den"], policy_variant=policy_variant, launch_mode=launch_mode,
-        policy_form=POLICY_FORMS[w0.get("policy_form", "plain")], n_hidden=w0.get("n_hidden", 1))
+        policy_form=POLICY_FORMS[w0.get("policy_form", "plain")], n_hidden=w0.get("n_hidden", 1),
+        rules=RULES[w0.get("rules", "simple")],
+        **{k: int(w0.get(k, 0)) for k in PAPER_RULE_FIELDS})
     return cfg, (side, slots, alive, seed)
 
 
@@ -332,7 +343,8 @@ class Env:
                "x": np.zeros(S, np.int32), "y": np.zeros(S, np.int32),
                "facing": np.zeros(S, np.uint8), "energy": np.zeros(S, np.int32),
                "parent": np.zeros(S, np.int32), "birth_step": np.zeros(S, np.int32),
-               "step": np.zeros(1, np.int64)}
+               "step": np.zeros(1, np.int64), "hp": np.zeros(S, np.int32),
+               "age": np.zeros(S, np.int32), "res": np.zeros(N, np.int32)}
         v = eco_state_view(**{k: _p(a) for k, a in out.items()})
         _check(lib().eco_read_state(self.h, int(env), ctypes.byref(v)), self.h)
         return out
@@ -345,7 +357,8 @@ class Env:
             if name in arrays and arrays[name] is not None:
                 dt = {"food": np.uint8, "wall": np.uint8, "occ": np.int32, "alive": np.uint8,
                       "x": np.int32, "y": np.int32, "facing": np.uint8, "energy": np.int32,
-                      "parent": np.int32, "birth_step": np.int32, "step": np.int64}[name]
+                      "parent": np.int32, "birth_step": np.int32, "step": np.int64,
+                      "hp": np.int32, "age": np.int32, "res": np.int32}[name]
                 a = np.ascontiguousarray(arrays[name], dtype=dt)
                 keep[name] = a
                 kw[name] = _p(a)

@@ -22,7 +22,7 @@ import numpy as np
 import oracle
 
 STATE_KEYS = ("food", "wall", "occ", "alive", "x", "y", "facing", "energy", "parent",
-              "birth_step")
+              "birth_step", "hp", "age", "res")
 LOGIT_RTOL = 1e-5
 GAP_TOL = 1e-3
 PARAM_RTOL = 2.0 ** -19
@@ -31,7 +31,9 @@ PARAM_RTOL = 2.0 ** -19
 STEP_STATS = (["agent_steps"] + ["act%d" % i for i in range(16)] +
               ["moves", "move_blocked", "move_lost", "eaten", "attacks", "attack_hits",
                "energy_transferred", "deaths", "dead_energy", "births", "failed_births",
-               "regrown", "alive", "food_total", "energy_total"])
+               "regrown", "alive", "food_total", "energy_total",
+               "res_total", "eaten_energy", "metab_paid", "heals", "starved", "damage",
+               "food_emptied", "food_refilled"])
 
 
 def runs(slots):

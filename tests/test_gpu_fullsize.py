@@ -130,3 +130,11 @@ def test_paperform_workload_lockstep():
     rep = _lockstep(workloads.get("paperform"), 3, sample=256)
     assert rep["steps"] == 3
     print("paper-form paper-scale lock-step:", rep)
+
+
+def test_ecology_workload_lockstep():
+    """The paper's rules and policy form at paper scale (1024x1024, 65,536
+    slots, 50,000 founders, RCV+A, 371-64-64-64-7 BF16)."""
+    rep = _lockstep(workloads.get("ecology"), 3, sample=256)
+    assert rep["steps"] == 3
+    print("ecology paper-scale lock-step:", rep)

@@ -239,3 +239,87 @@ def test_paper_form_quantised_copy_bit_exact():
             assert scales[s, r] == np.float32(oracle.fp8_row_scale(row))
             r += 1
     env.close()
+
+
+def _ecology(side, slots, k, **kw):
+    """The paper's rule set (HP, 3x3 attack, eat / reproduce actions, drops)
+    with the paper's policy form, on a reduced world; founders start with
+    little energy and a low reproduction threshold so that births,
+    starvation, kills, drops and healing all happen within a short run."""
+    over = dict(e_init=60, e_repro=50, e_child=20)
+    over.update(kw)
+    return workloads.scaled("ecology", side, slots, k, **over)
+
+
+def _run_totals(w, steps, **kw):
+    env, orc = _pair(w, **kw)
+    try:
+        harness.start_pair(env, orc)
+        rep = harness.lockstep(env, orc, steps, where=w["name"])
+        return rep, env.stats()[0]
+    finally:
+        env.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+def test_paper_rules_lockstep(prec):
+    """Sec. 3.2 "Resources and Agent Health" / "Actions", App. F.7-F.8."""
+    rep, tot = _run_totals(_ecology(128, 2048, 1500, precision=prec), 30)
+    assert rep["births"] > 50
+    for k in ("deaths", "food_refilled", "heals", "starved", "eaten", "food_emptied", "damage"):
+        assert tot[k] > 0, k
+
+
+@pytest.mark.parametrize("over", [
+    dict(policy_form="plain", n_hidden=1, n_scalars=4, patch_k=5, hidden=32),
+    dict(flags=("rotate_obs", "cancel_all"), attack_damage=10, age_div=5),
+    dict(flags=(), heal_rate=0, e_cap=70),
+    dict(slots=1200, e_repro=40, e_child=10),      # slot exhaustion: failed births
+])
+def test_paper_rules_variants(over):
+    over = dict(over)
+    slots = over.pop("slots", 600)
+    rep, tot = _run_totals(_ecology(64, slots, 500, **over), 15)
+    assert rep["steps"] == 15 and tot["deaths"] > 0
+
+
+def test_paper_rules_launch_forms_bit_identical():
+    from paper_2510_18221_gb300 import eco
+    w = _ecology(128, 2048, 1500, precision="fp8")
+    a, b = eco.Env(w, launch_mode=0), eco.Env(w, launch_mode=1)
+    a.reset()
+    b.reset()
+    for t in range(25):
+        a.step(1)
+        b.step(1)
+        sa, sb = a.read_state(0), b.read_state(0)
+        for k in harness.STATE_KEYS:
+            assert np.array_equal(sa[k], sb[k]), (t, k)
+        assert a.stats()[0] == b.stats()[0]
+    assert a.stats()[0]["births"] > 0
+    a.close()
+    b.close()
+
+
+def test_paper_rules_state_roundtrip():
+    """eco_write_state / eco_read_state carry HP, age and the energy on
+    cells; the food bits follow the energy."""
+    from paper_2510_18221_gb300 import eco
+    w = _ecology(32, 64, 40)
+    env = eco.Env(w)
+    orc = oracle.Oracle(w)
+    orc.reset()
+    for _ in range(5):
+        orc.step_once()
+    rng = np.random.default_rng(5)
+    orc.hp[orc.alive == 1] = rng.integers(1, 41, int(orc.alive.sum()))
+    orc.age[:] = rng.integers(0, 5000, orc.S)
+    orc.res[:] = np.where(orc.wall == 1, 0, rng.integers(0, 3, orc.res.size) * 7)
+    orc.food[:] = (orc.res > 0).astype(np.uint8)
+    env.reset()
+    env.write_state(0, orc.arrays())
+    gs = env.read_state(0)
+    harness.compare_state(gs, orc, "roundtrip")
+    st = env.stats()[0]
+    assert st["res_total"] == int(orc.res.sum()) and st["food_total"] == int(orc.food.sum())
+    env.close()
