@@ -49,6 +49,9 @@ P_REST, P_ROT_CW, P_ROT_CCW, P_FORWARD, P_ATTACK, P_EAT, P_REPRODUCE = range(7)
 
 # Constants of the paper rule set, read from the workload dictionary (0 when
 # absent: the simple rule set ignores them).
+# Vision (Sec. 3.2 "Sensors") and viewing configuration (App. F.6).
+VISIONS = {"channels": 0, "rgb": 1}
+VIEWS = {"around": 0, "front": 1}
 PAPER_RULE_FIELDS = ("hp_max", "hp_child", "attack_damage", "heal_rate", "heal_cost",
                      "age_div", "starve_damage", "e_act", "e_cap", "e_child")
 
@@ -85,6 +88,7 @@ class Config(ctypes.Structure):
         ("age_div", ctypes.c_int32), ("starve_damage", ctypes.c_int32),
         ("e_act", ctypes.c_int32), ("e_cap", ctypes.c_int32),
         ("e_child", ctypes.c_int32),
+        ("vision", ctypes.c_int32), ("view", ctypes.c_int32),
     ]
 
 
@@ -94,7 +98,7 @@ _P = ctypes.c_void_p
 class State(ctypes.Structure):
     _fields_ = [(n, _P) for n in ("food", "wall", "occ", "alive", "x", "y", "facing",
                                   "energy", "parent", "birth_step", "master", "step",
-                                  "hp", "age", "res")]
+                                  "hp", "age", "res", "colour")]
 
 
 STAT_FIELDS = ["agent_steps"] + ["act%d" % i for i in range(16)] + [
@@ -146,6 +150,7 @@ def lib():
             L.orc_mlp.argtypes = [cfgp, _P, _P, _P]
             L.orc_policy.argtypes = [cfgp, stp, ctypes.c_int, ctypes.c_double, _P, _P, _P, _P]
             L.orc_mutate.argtypes = [cfgp, ctypes.c_int64, ctypes.c_int32, _P, _P]
+            L.orc_mutate_colour.argtypes = [cfgp, ctypes.c_int64, ctypes.c_int32, _P, _P]
             L.orc_transition.argtypes = [cfgp, stp, _P, ctypes.POINTER(Stats), _P, _P]
             _lib = L
     return _lib
@@ -240,6 +245,8 @@ def make_config(cfg: dict) -> Config:
         if isinstance(cfg.get("policy_form", "plain"), str) else int(cfg["policy_form"]),
         n_hidden=cfg.get("n_hidden", 1),
         rules=RULES[cfg.get("rules", "simple")],
+        vision=VISIONS[cfg.get("vision", "channels")],
+        view=VIEWS[cfg.get("view", "around")],
         **{k: int(cfg.get(k, 0)) for k in PAPER_RULE_FIELDS})
 
 
@@ -247,7 +254,7 @@ class Oracle:
     """One environment held as numpy arrays, stepped by the C oracle."""
 
     ARRAYS = ("food", "wall", "occ", "alive", "x", "y", "facing", "energy",
-              "parent", "birth_step", "master", "step", "hp", "age", "res")
+              "parent", "birth_step", "master", "step", "hp", "age", "res", "colour")
 
     def __init__(self, cfg: dict, allocate: bool = True):
         self.cfg = dict(cfg)
@@ -276,6 +283,7 @@ class Oracle:
             self.hp = np.zeros(S, np.int32)
             self.age = np.zeros(S, np.int32)
             self.res = np.zeros(N, np.int32)
+            self.colour = np.zeros((S, 3), np.float32)
 
     # -- plumbing ----------------------------------------------------------
     def _state(self) -> State:
@@ -326,6 +334,13 @@ class Oracle:
         child = np.zeros(self.P, np.float32)
         lib().orc_mutate(ctypes.byref(self.c), int(step), int(parent_slot),
                          _ptr(parent_row), _ptr(child))
+        return child
+
+    def mutate_colour(self, step: int, parent_slot: int, parent_rgb) -> np.ndarray:
+        parent_rgb = np.ascontiguousarray(parent_rgb, np.float32)
+        child = np.zeros(3, np.float32)
+        lib().orc_mutate_colour(ctypes.byref(self.c), int(step), int(parent_slot),
+                                _ptr(parent_rgb), _ptr(child))
         return child
 
     def policy(self, use_master: bool = False, tol: float = 1e-3) -> dict:

@@ -76,7 +76,20 @@ enum {
   ST_CLAIM_ATTACK = 8,
   ST_CLAIM_BIRTH = 9,
   ST_MUTATE = 10,
-  ST_REGROW = 11
+  ST_REGROW = 11,
+  ST_COLOUR = 12   /* colour trait: initial colour, and its mutation */
+};
+
+/* Vision (Sec. 3.2 "Sensors"; App. F.6 viewing configurations). */
+enum {
+  ORC_VISION_CHANNELS = 0, /* one-hot channels (food, agent, wall)          */
+  ORC_VISION_RGB = 1       /* rendered colours: an agent shows its colour   */
+                           /* trait, a wall grey, food green, empty black   */
+};
+enum {
+  ORC_VIEW_AROUND = 0,     /* the window is centred on the agent             */
+  ORC_VIEW_FRONT = 1       /* the window lies ahead: the agent in the middle */
+                           /* of its bottom row, nothing behind it visible   */
 };
 
 /* Rule sets.  Simple: the workloads' rules (death at zero energy, a
@@ -148,6 +161,8 @@ typedef struct {
   int32_t e_act;         /* extra energy cost of any action but rest       */
   int32_t e_cap;         /* stomach capacity: eating stops at this energy  */
   int32_t e_child;       /* energy a parent hands to its child             */
+  int32_t vision;        /* ORC_VISION_CHANNELS or ORC_VISION_RGB          */
+  int32_t view;          /* ORC_VIEW_AROUND or ORC_VIEW_FRONT              */
 } orc_config;
 
 enum {
@@ -172,6 +187,7 @@ typedef struct {
   int32_t *age;        /* [S] paper rules: steps survived                 */
   int32_t *res;        /* [L*L] paper rules: energy lying on the cell;    */
                        /*   food[c] == (res[c] > 0)                       */
+  float *colour;       /* [S][3] colour trait (Sec. 3.3), RGB in [0, 1]   */
 } orc_state;
 
 typedef struct {
@@ -563,6 +579,7 @@ int orc_reset(const orc_config *c, orc_state *s) {
     s->birth_step[slot] = -1;
     s->hp[slot] = 0;
     s->age[slot] = 0;
+    s->colour[3 * slot + 0] = s->colour[3 * slot + 1] = s->colour[3 * slot + 2] = 0.0f;
   }
   for (i = 0; i < K; i++) {
     cell = chosen[i];
@@ -573,6 +590,11 @@ int orc_reset(const orc_config *c, orc_state *s) {
     s->facing[i] = (uint8_t)(r[i & 3] >> 30);
     s->energy[i] = c->e_init;
     s->hp[i] = c->rules == ORC_RULES_PAPER ? c->hp_max : 0;
+    /* colour trait: three uniforms of COLOUR at counter (slot, 0, 0, 0) */
+    draw4(c, ST_COLOUR, (uint32_t)i, 0u, 0u, r);
+    s->colour[3 * i + 0] = (float)orc_uniform(r[0]);
+    s->colour[3 * i + 1] = (float)orc_uniform(r[1]);
+    s->colour[3 * i + 2] = (float)orc_uniform(r[2]);
     s->occ[cell] = i;
   }
 #pragma omp parallel for schedule(dynamic, 16)
@@ -597,6 +619,11 @@ int orc_reset(const orc_config *c, orc_state *s) {
 /* paper rules the zeros become the internal and external sensors: HP /     */
 /* hp_max, age / (age + age_div), and the energy r lying on the agent's     */
 /* cell as r / (r + e_food), all in [0, 1).                                 */
+/* Front view (App. F.6): the window lies ahead of the agent, which sits in  */
+/* the middle of its bottom row.  RGB vision (Sec. 3.2: a rendered patch     */
+/* with three colour channels): a cell with an agent shows that agent's      */
+/* colour trait, otherwise a wall is grey (0.5, 0.5, 0.5), food is green     */
+/* (0, 1, 0) and an empty cell black.                                        */
 /* ------------------------------------------------------------------------ */
 
 void orc_observe(const orc_config *c, const orc_state *s, int32_t slot, double *x) {
@@ -608,7 +635,9 @@ void orc_observe(const orc_config *c, const orc_state *s, int32_t slot, double *
     for (col = 0; col < k; col++) {
       int dx, dy, cell, idx = (r * k + col) * 3;
       if (c->flags & ORC_ROTATE_OBS) {
-        int fwd = R - r, rt = col - R;
+        /* rows run from far ahead (top) to behind (Around) or to the
+         * agent's own row (Front); columns from its left to its right */
+        int fwd = (c->view == ORC_VIEW_FRONT ? k - 1 : R) - r, rt = col - R;
         dx = fwd * DIR_DX[f] + rt * DIR_DX[right];
         dy = fwd * DIR_DY[f] + rt * DIR_DY[right];
       } else {
@@ -616,6 +645,16 @@ void orc_observe(const orc_config *c, const orc_state *s, int32_t slot, double *
         dy = r - R;
       }
       cell = cell_of(wrap(s->x[slot] + dx, L), wrap(s->y[slot] + dy, L), L);
+      if (c->vision == ORC_VISION_RGB) {
+        int who = s->occ[cell], ch;
+        for (ch = 0; ch < 3; ch++) {
+          if (who >= 0) x[idx + ch] = (double)s->colour[3 * who + ch];
+          else if (s->wall[cell]) x[idx + ch] = 0.5;
+          else if (s->food[cell]) x[idx + ch] = ch == 1 ? 1.0 : 0.0;
+          else x[idx + ch] = 0.0;
+        }
+        continue;
+      }
       x[idx + 0] = s->food[cell] ? 1.0 : 0.0;
       x[idx + 1] = s->occ[cell] >= 0 ? 1.0 : 0.0;
       x[idx + 2] = s->wall[cell] ? 1.0 : 0.0;
@@ -797,6 +836,22 @@ void orc_mutate(const orc_config *c, int64_t step, int32_t parent_slot,
       orc_normals4(r, n);
     }
     child_row[p] = (float)((double)parent_row[p] + (double)c->sigma * n[p & 3]);
+  }
+}
+
+/* Colour trait (Sec. 3.3: a 3-channel colour that mutates like the network
+ * weights): child = clamp(fl32(parent + sigma * n), 0, 1) per channel, with
+ * n the first three normals of COLOUR at counter (step, parent slot, 1, 0). */
+void orc_mutate_colour(const orc_config *c, int64_t step, int32_t parent_slot,
+                       const float *parent_rgb, float *child_rgb) {
+  uint32_t r[4];
+  double n[4];
+  int ch;
+  draw4(c, ST_COLOUR, (uint32_t)step, (uint32_t)parent_slot, 1u, r);
+  orc_normals4(r, n);
+  for (ch = 0; ch < 3; ch++) {
+    float v = (float)((double)parent_rgb[ch] + (double)c->sigma * n[ch]);
+    child_rgb[ch] = v < 0.0f ? 0.0f : (v > 1.0f ? 1.0f : v);
   }
 }
 
@@ -1109,6 +1164,7 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
     s->birth_step[ch] = (int32_t)t;
     s->occ[tc] = ch;
     orc_mutate(c, t, p, s->master + (size_t)p * (size_t)P, s->master + (size_t)ch * (size_t)P);
+    orc_mutate_colour(c, t, p, s->colour + 3 * p, s->colour + 3 * ch);
     if (birth_parent) birth_parent[st->births] = p;
     if (birth_child) birth_child[st->births] = ch;
     st->births++;
