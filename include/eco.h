@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define ECO_ABI_VERSION 2
+#define ECO_ABI_VERSION 3
 
 /* Status codes. */
 #define ECO_OK 0
@@ -99,6 +99,20 @@ extern "C" {
 #define ECO_RULES_SIMPLE 0
 #define ECO_RULES_PAPER 1
 
+/* Vision (Sec. 3.2 "Sensors": a top-down patch with three colour channels)
+ * and viewing configuration (App. F.6).  Channels: per cell (food, agent,
+ * wall) as 0/1.  RGB: a cell holding an agent shows that agent's colour
+ * trait; otherwise a wall is (0.5, 0.5, 0.5), food (0, 1, 0), an empty cell
+ * (0, 0, 0).  Around: the k x k window is centred on the agent.  Front
+ * (needs ECO_ROTATE_OBS): the window lies ahead, the agent in the middle of
+ * its bottom row, so nothing behind it is visible.
+ * Every agent carries a colour trait (Sec. 3.3), RGB in [0, 1]: uniform at
+ * reset, and at birth clamp(parent + sigma * n, 0, 1) per channel. */
+#define ECO_VISION_CHANNELS 0
+#define ECO_VISION_RGB 1
+#define ECO_VIEW_AROUND 0
+#define ECO_VIEW_FRONT 1
+
 /* Action codes.  Simple rules: 0 stay, 1 north, 2 south, 3 east, 4 west,
  * 5 attack; nine-action sets add 6 turn-left, 7 turn-right, 8 eat.  Paper
  * rules (7 actions): 0 rest, 1 rotate clockwise, 2 rotate counter-
@@ -154,6 +168,8 @@ typedef struct {
   int32_t e_act;                 /* extra cost of any action but rest, >= 0  */
   int32_t e_cap;                 /* stomach capacity, >= max(e_init, 1)      */
   int32_t e_child;               /* energy handed to a child, in [1, e_repro] */
+  int32_t vision;                /* ECO_VISION_CHANNELS or ECO_VISION_RGB    */
+  int32_t view;                  /* ECO_VIEW_AROUND or ECO_VIEW_FRONT        */
 } eco_config;
 
 /* Statistics, one record per environment (App. E measurement API).
@@ -217,6 +233,7 @@ typedef struct {
   int32_t *res;        /* [L*L] paper rules: energy lying on the cell; on
                           write, food is taken as res > 0 (the food array
                           is then ignored)                                  */
+  float *colour;       /* [slots][3] colour trait, RGB in [0, 1]            */
 } eco_state_view;
 
 /* Parameter count P and observation size D for a configuration.

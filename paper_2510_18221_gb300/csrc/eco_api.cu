@@ -89,6 +89,10 @@ static int validate(const eco_config *c, char *msg, size_t n) {
   if (c->n_scalars != 4 && c->n_scalars != 8) return snprintf(msg, n, "n_scalars must be 4 or 8"), ECO_EINVAL;
   if (c->hidden != 32 && c->hidden != 64 && c->hidden != 128) return snprintf(msg, n, "hidden must be 32, 64 or 128"), ECO_EINVAL;
   if (c->rules != ECO_RULES_SIMPLE && c->rules != ECO_RULES_PAPER) return snprintf(msg, n, "bad rules"), ECO_EINVAL;
+  if (c->vision != ECO_VISION_CHANNELS && c->vision != ECO_VISION_RGB) return snprintf(msg, n, "bad vision"), ECO_EINVAL;
+  if (c->view != ECO_VIEW_AROUND && c->view != ECO_VIEW_FRONT) return snprintf(msg, n, "bad view"), ECO_EINVAL;
+  if (c->view == ECO_VIEW_FRONT && !(c->flags & ECO_ROTATE_OBS))
+    return snprintf(msg, n, "the front view needs ECO_ROTATE_OBS"), ECO_EINVAL;
   if (c->rules == ECO_RULES_SIMPLE && c->n_actions != 6 && c->n_actions != 9)
     return snprintf(msg, n, "n_actions must be 6 or 9 under the simple rules"), ECO_EINVAL;
   if (c->rules == ECO_RULES_PAPER) {
@@ -242,6 +246,7 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.age = k.take<int32_t>(slots);
   D.dmg = k.take<int32_t>(slots);
   D.res = k.take<int32_t>(cells);
+  D.colour = k.take<float4>(slots);
   return (k.off + 255) & ~(size_t)255;
 }
 
@@ -319,6 +324,8 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
   R.e_act = cfg->e_act;
   R.e_cap = cfg->e_cap;
   R.e_child = cfg->e_child;
+  R.vision = cfg->vision;
+  R.view = cfg->view;
   h->ws = reinterpret_cast<uint8_t *>(dev_workspace);
   h->ws_bytes = bytes;
   carve(cfg, h->L, h->ws, &h->d, &h->env_dev);
@@ -638,6 +645,10 @@ extern "C" int eco_read_state(eco_handle *h, int32_t env, eco_state_view *out) {
   if (out->hp) CUDA_TRY(h, cudaMemcpyAsync(out->hp, h->d.hp + ed.slot_off, 4 * (size_t)S, cudaMemcpyDeviceToHost, s));
   if (out->age) CUDA_TRY(h, cudaMemcpyAsync(out->age, h->d.age + ed.slot_off, 4 * (size_t)S, cudaMemcpyDeviceToHost, s));
   if (out->res) CUDA_TRY(h, cudaMemcpyAsync(out->res, h->d.res + ed.cell_off, 4 * (size_t)N, cudaMemcpyDeviceToHost, s));
+  std::vector<float4> colour(out->colour ? S : 0);
+  if (out->colour)
+    CUDA_TRY(h, cudaMemcpyAsync(colour.data(), h->d.colour + ed.slot_off, sizeof(float4) * (size_t)S,
+                                cudaMemcpyDeviceToHost, s));
   CUDA_TRY(h, cudaMemcpyAsync(cellf.data(), h->d.cellf + ed.cell_off, N, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(h, cudaMemcpyAsync(occ.data(), h->d.occ + ed.cell_off, 4 * (size_t)N, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(h, cudaMemcpyAsync(alive.data(), h->d.alive + ed.slot_off, S, cudaMemcpyDeviceToHost, s));
@@ -661,6 +672,11 @@ extern "C" int eco_read_state(eco_handle *h, int32_t env, eco_state_view *out) {
     if (out->energy) out->energy[i] = energy[i];
     if (out->parent) out->parent[i] = parent[i];
     if (out->birth_step) out->birth_step[i] = birth[i];
+    if (out->colour) {
+      out->colour[3 * i + 0] = colour[i].x;
+      out->colour[3 * i + 1] = colour[i].y;
+      out->colour[3 * i + 2] = colour[i].z;
+    }
   }
   if (out->step) *out->step = step;
   return ECO_OK;
@@ -713,6 +729,18 @@ extern "C" int eco_write_state(eco_handle *h, int32_t env, const eco_state_view 
   if (in->birth_step) CUDA_TRY(h, cudaMemcpyAsync(h->d.birth + ed.slot_off, in->birth_step, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
   if (in->hp) CUDA_TRY(h, cudaMemcpyAsync(h->d.hp + ed.slot_off, in->hp, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
   if (in->age) CUDA_TRY(h, cudaMemcpyAsync(h->d.age + ed.slot_off, in->age, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
+  std::vector<float4> colour;
+  if (in->colour) {
+    colour.resize(S);
+    for (int i = 0; i < S; ++i) {
+      const float r = in->colour[3 * i], g = in->colour[3 * i + 1], b = in->colour[3 * i + 2];
+      if (!(r >= 0.0f && r <= 1.0f && g >= 0.0f && g <= 1.0f && b >= 0.0f && b <= 1.0f))
+        return fail(h, ECO_EINVAL, "colour of slot %d outside [0, 1]", i);
+      colour[i] = make_float4(r, g, b, 0.0f);
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->d.colour + ed.slot_off, colour.data(), sizeof(float4) * (size_t)S,
+                                cudaMemcpyHostToDevice, s));
+  }
   if (in->step) {
     // all environments share one step counter
     long long st = *in->step;

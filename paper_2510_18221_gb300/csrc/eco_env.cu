@@ -374,6 +374,16 @@ __device__ __forceinline__ void make_child(const Dev &d, const Rules &R, const E
   d.energy[c] = ce;
   d.hp[c] = paper ? R.hp_child : 0;
   d.age[c] = 0;
+  {
+    // colour trait: clamp(parent + sigma * n, 0, 1), n the first three
+    // normals of COLOUR at counter (step, parent's local slot, 1, 0)
+    float n[4];
+    normals4(philox(t, (uint32_t)(p - ed.slot_off), 1u, 0u, ed.seed, S_COLOUR), n);
+    const float4 pc = d.colour[p];
+    d.colour[c] = make_float4(fminf(fmaxf(fmaf(R.sigma, n[0], pc.x), 0.0f), 1.0f),
+                              fminf(fmaxf(fmaf(R.sigma, n[1], pc.y), 0.0f), 1.0f),
+                              fminf(fmaxf(fmaf(R.sigma, n[2], pc.z), 0.0f), 1.0f), 0.0f);
+  }
   d.alive[c] = 1;
   d.pos[c] = bt;
   d.facing[c] = d.facing[p];

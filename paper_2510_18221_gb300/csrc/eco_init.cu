@@ -68,6 +68,13 @@ __global__ void k_init_agents(Dev d, Rules R) {
     d.hp[s] = (founder && R.rules == RULES_PAPER) ? R.hp_max : 0;
     d.age[s] = 0;
     d.dmg[s] = 0;
+    // colour trait (Sec. 3.3): three uniforms of COLOUR at counter (slot, 0, 0, 0)
+    float4 col = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (founder) {
+      const U4 r = philox((uint32_t)ls, 0u, 0u, 0u, ed.seed, S_COLOUR);
+      col = make_float4(uniform01(r.x), uniform01(r.y), uniform01(r.z), 0.0f);
+    }
+    d.colour[s] = col;
   }
 }
 

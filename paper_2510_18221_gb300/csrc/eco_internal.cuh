@@ -11,6 +11,7 @@
 //     hp i32, age i32, dmg i32 (paper rules);
 //   per cell, paper rules: res i32 (energy lying on the cell; the food bit
 //     of cellf is res > 0);
+//   per slot: colour f32x4 (the colour trait, RGB + padding);
 //   weights: FP32 masters [slot][mstride] and, for BF16/FP8, the streamed
 //     copy [slot][stride], both in the kernel's tiled block layout below.
 //
@@ -51,6 +52,14 @@ enum : uint32_t {
   S_CLAIM_BIRTH = 9,
   S_MUTATE = 10,
   S_REGROW = 11,
+  S_COLOUR = 12,
+};
+
+enum : int {
+  VISION_CHANNELS = 0,
+  VISION_RGB = 1,
+  VIEW_AROUND = 0,
+  VIEW_FRONT = 1,
 };
 
 enum : int {
@@ -219,6 +228,7 @@ struct Rules {
   int rules;  // RULES_SIMPLE / RULES_PAPER; the rest is paper rules only
   int hp_max, hp_child, attack_damage, heal_rate, heal_cost, age_div, starve_damage;
   int e_act, e_cap, e_child;
+  int vision, view;  // VISION_*, VIEW_*
 };
 
 // Device pointers (all inside the caller's workspace).
@@ -266,6 +276,7 @@ struct Dev {
   int32_t *age;            // [total_slots] paper rules: steps survived
   int32_t *dmg;            // [total_slots] paper rules: attack damage this step
   int32_t *res;            // [total_cells] paper rules: energy on the cell
+  float4 *colour;          // [total_slots] colour trait (x, y, z = RGB; w = 0)
 };
 
 enum : int {

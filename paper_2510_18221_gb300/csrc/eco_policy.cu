@@ -237,11 +237,14 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
     const int f = d.facing[slot];
     const int rt = (f + 1) & 3;
     const uint8_t *cellf = d.cellf + ed.cell_off;
+    // rows run from far ahead (top) to behind (Around) or to the agent's
+    // own row (Front); columns from the agent's left to its right
+    const int fw0 = R.view == VIEW_FRONT ? k - 1 : RR;
     for (int c = lane; c < kk; c += 32) {
       const int r = c / k, col = c - r * k;
       int dx, dy;
       if (rotate) {
-        const int fw = RR - r, ri = col - RR;
+        const int fw = fw0 - r, ri = col - RR;
         dx = fw * dir_dx(f) + ri * dir_dx(rt);
         dy = fw * dir_dy(f) + ri * dir_dy(rt);
       } else {
@@ -250,9 +253,21 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
       }
       const int cx = wrapi(px + dx, side), cy = wrapi(py + dy, side);
       const uint32_t cf = cellf[cy * side + cx];
-      xs[3 * c + 0] = (cf & CELL_FOOD) ? 1.0f : 0.0f;
-      xs[3 * c + 1] = (cf & CELL_AGENT) ? 1.0f : 0.0f;
-      xs[3 * c + 2] = (cf & CELL_WALL) ? 1.0f : 0.0f;
+      if (R.vision == VISION_RGB) {
+        // rendered colours: the occupant's colour trait, else grey wall,
+        // green food, black
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (cf & CELL_AGENT) v = d.colour[d.occ[ed.cell_off + cy * side + cx]];
+        else if (cf & CELL_WALL) v = make_float4(0.5f, 0.5f, 0.5f, 0.0f);
+        else if (cf & CELL_FOOD) v.y = 1.0f;
+        xs[3 * c + 0] = v.x;
+        xs[3 * c + 1] = v.y;
+        xs[3 * c + 2] = v.z;
+      } else {
+        xs[3 * c + 0] = (cf & CELL_FOOD) ? 1.0f : 0.0f;
+        xs[3 * c + 1] = (cf & CELL_AGENT) ? 1.0f : 0.0f;
+        xs[3 * c + 2] = (cf & CELL_WALL) ? 1.0f : 0.0f;
+      }
     }
     if (lane < R.n_scalars) {
       // [e / e_repro, one-hot facing (8-scalar form), zeros]; the paper

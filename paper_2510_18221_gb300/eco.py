@@ -21,7 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libeco.so")
 
-ECO_ABI_VERSION = 2
+ECO_ABI_VERSION = 3
 ECO_OK, ECO_EINVAL, ECO_ENOMEM, ECO_ECUDA, ECO_ETIMEOUT, ECO_EABI = 0, -1, -2, -3, -4, -5
 ECO_FP32, ECO_BF16, ECO_FP8_E4M3 = 0, 1, 2
 ECO_AUTO_EAT, ECO_ROTATE_OBS, ECO_CANCEL_ALL, ECO_GREEDY = 1, 2, 4, 8
@@ -30,6 +30,8 @@ ECO_POLICY_PLAIN, ECO_POLICY_PAPER = 0, 1
 POLICY_FORMS = {"plain": ECO_POLICY_PLAIN, "paper": ECO_POLICY_PAPER}
 ECO_RULES_SIMPLE, ECO_RULES_PAPER = 0, 1
 RULES = {"simple": ECO_RULES_SIMPLE, "paper": ECO_RULES_PAPER}
+VISIONS = {"channels": 0, "rgb": 1}
+VIEWS = {"around": 0, "front": 1}
 PAPER_RULE_FIELDS = ("hp_max", "hp_child", "attack_damage", "heal_rate", "heal_cost",
                      "age_div", "starve_damage", "e_act", "e_cap", "e_child")
 FLAGS = {"auto_eat": ECO_AUTO_EAT, "rotate_obs": ECO_ROTATE_OBS,
@@ -64,7 +66,8 @@ class eco_config(ctypes.Structure):
         ("policy_variant", ctypes.c_int32), ("launch_mode", ctypes.c_int32),
         ("policy_form", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
         ("rules", ctypes.c_int32),
-    ] + [(k, ctypes.c_int32) for k in PAPER_RULE_FIELDS]
+    ] + [(k, ctypes.c_int32) for k in PAPER_RULE_FIELDS] + [
+        ("vision", ctypes.c_int32), ("view", ctypes.c_int32)]
 
 
 class eco_stats(ctypes.Structure):
@@ -74,7 +77,7 @@ class eco_stats(ctypes.Structure):
 class eco_state_view(ctypes.Structure):
     _fields_ = [(n, _vp) for n in ("food", "wall", "occ", "alive", "x", "y", "facing",
                                    "energy", "parent", "birth_step", "step", "hp", "age",
-                                   "res")]
+                                   "res", "colour")]
 
 
 _lib = None
@@ -235,7 +238,7 @@ def eco_move_claims_noalloc(side: int, n_agents: int, pos: int, act: int, facing
 _SHARED = ("patch_k", "n_scalars", "hidden", "n_actions", "precision", "flags", "sigma",
            "food_density", "regrow_p", "wall_density", "e_init", "e_metab", "e_food",
            "e_repro", "attack_num", "attack_den", "policy_form", "n_hidden",
-           "rules") + PAPER_RULE_FIELDS
+           "rules", "vision", "view") + PAPER_RULE_FIELDS
 
 
 def make_config(envs: Sequence[dict], policy_variant: int = 0, launch_mode: int = 0):
@@ -266,6 +269,7 @@ def make_config(envs: Sequence[dict], policy_variant: int = 0, launch_mode: int 
         attack_den=w0["attack_den"], policy_variant=policy_variant, launch_mode=launch_mode,
         policy_form=POLICY_FORMS[w0.get("policy_form", "plain")], n_hidden=w0.get("n_hidden", 1),
         rules=RULES[w0.get("rules", "simple")],
+        vision=VISIONS[w0.get("vision", "channels")], view=VIEWS[w0.get("view", "around")],
         **{k: int(w0.get(k, 0)) for k in PAPER_RULE_FIELDS})
     return cfg, (side, slots, alive, seed)
 
@@ -344,7 +348,8 @@ class Env:
                "facing": np.zeros(S, np.uint8), "energy": np.zeros(S, np.int32),
                "parent": np.zeros(S, np.int32), "birth_step": np.zeros(S, np.int32),
                "step": np.zeros(1, np.int64), "hp": np.zeros(S, np.int32),
-               "age": np.zeros(S, np.int32), "res": np.zeros(N, np.int32)}
+               "age": np.zeros(S, np.int32), "res": np.zeros(N, np.int32),
+               "colour": np.zeros((S, 3), np.float32)}
         v = eco_state_view(**{k: _p(a) for k, a in out.items()})
         _check(lib().eco_read_state(self.h, int(env), ctypes.byref(v)), self.h)
         return out
@@ -358,7 +363,8 @@ class Env:
                 dt = {"food": np.uint8, "wall": np.uint8, "occ": np.int32, "alive": np.uint8,
                       "x": np.int32, "y": np.int32, "facing": np.uint8, "energy": np.int32,
                       "parent": np.int32, "birth_step": np.int32, "step": np.int64,
-                      "hp": np.int32, "age": np.int32, "res": np.int32}[name]
+                      "hp": np.int32, "age": np.int32, "res": np.int32,
+                      "colour": np.float32}[name]
                 a = np.ascontiguousarray(arrays[name], dtype=dt)
                 keep[name] = a
                 kw[name] = _p(a)

@@ -67,9 +67,12 @@ PAPER_RULES = dict(rules="paper", n_actions=7, hp_max=40, hp_child=20, attack_da
                    e_cap=400, e_child=100)
 
 # The paper's rules and policy form together on the paper-scale world
-# (RCV+A agents: vision, compass, internal sensors; attack enabled).
-ECOLOGY = dict(PAPER_FORM, name="ecology-1024x1024-65536slots-RCV+A-2x64-7act-bf16",
-               **PAPER_RULES)
+# (RCV+A agents: vision, compass, internal sensors; attack enabled).  The
+# vision patch is rendered in colour (Sec. 3.2), each agent showing its
+# evolvable colour trait (Sec. 3.3); the window is centred on the agent
+# ("Around", the paper's main setting, App. F.6).
+ECOLOGY = dict(PAPER_FORM, name="ecology-1024x1024-65536slots-RCV+A-rgb-2x64-7act-bf16",
+               vision="rgb", view="around", **PAPER_RULES)
 
 WORKLOADS = {"small": SMALL, "mid": MID, "paper": PAPER, "large": LARGE,
              "paperform": PAPER_FORM, "ecology": ECOLOGY}

@@ -15,7 +15,10 @@ Rules (written in the tests):
     transition taken with that valid choice (after which the GPU is reset to
     the oracle's own trajectory);
   * child parameters: |gpu - oracle| <= 2^-19 * (|parent| + |child - parent|)
-    (FP32 Box-Muller on the GPU vs FP64 in the oracle, a few ulp).
+    (FP32 Box-Muller on the GPU vs FP64 in the oracle, a few ulp);
+  * colour traits: bit-exact, except a newborn's, which is held to the
+    child-parameter bound (the same Box-Muller difference) and then
+    replaced by the oracle's.
 """
 import numpy as np
 
@@ -68,6 +71,24 @@ def compare_stats(last, st, where=""):
         assert last[k] == st[k], "%s: stat %s gpu %d oracle %d" % (where, k, last[k], st[k])
 
 
+def compare_colours(gs, orc, births=(), where=""):
+    got, want = gs["colour"], orc.colour
+    fresh = np.zeros(len(want), bool)
+    fresh[[c for _, c in births]] = True
+    if not np.array_equal(got[~fresh], want[~fresh]):
+        idx = np.flatnonzero((got != want).any(axis=1) & ~fresh)[:8]
+        raise AssertionError("%s: colour differs at %s: gpu %s oracle %s" %
+                             (where, idx.tolist(), got[idx].tolist(), want[idx].tolist()))
+    err = 0.0
+    for p, c in births:
+        err = max(err, check_params(got[c], want[c], want[p], where + " colour of child %d" % c))
+    return err
+
+
+def push_colours(env, orc, e=0):
+    env.write_state(e, {"colour": orc.colour})
+
+
 def check_params(got, want, parent=None, where=""):
     ref = np.abs(want.astype(np.float64))
     if parent is not None:
@@ -88,6 +109,7 @@ def start_pair(env, orc, e=0, check_init=True, sample=None):
     orc.reset()
     gs = env.read_state(e)
     compare_state(gs, orc, "reset")
+    compare_colours(gs, orc, (), "reset")
     K = int(orc.alive.sum())
     if check_init and K:
         slots = np.arange(K) if sample is None else np.unique(
@@ -151,6 +173,7 @@ def lockstep(env, orc, steps, e=0, where="", vs_master=False):
             st_alt, births_alt = alt.transition(alt_act)
             compare_state(gs, alt, tag + " (valid alternative)")
             compare_stats(last, st_alt, tag + " (valid alternative)")
+            compare_colours(gs, alt, births_alt, tag + " (valid alternative)")
             st, births = orc.transition(pol["action"])
             env.write_state(e, orc.arrays())
             push_params(env, orc, [c for _, c in births] + [c for _, c in births_alt], e)
@@ -158,7 +181,9 @@ def lockstep(env, orc, steps, e=0, where="", vs_master=False):
             st, births = orc.transition(pol["action"])
             compare_state(gs, orc, tag)
             compare_stats(last, st, tag)
+            rep["max_param_err"] = max(rep["max_param_err"], compare_colours(gs, orc, births, tag))
             if births:
+                push_colours(env, orc, e)
                 kids = [c for _, c in births]
                 for p, c in births:
                     got = env.read_params(e, c, 1)[0]

@@ -320,6 +320,31 @@ def test_paper_rules_state_roundtrip():
     env.write_state(0, orc.arrays())
     gs = env.read_state(0)
     harness.compare_state(gs, orc, "roundtrip")
+    harness.compare_colours(gs, orc, (), "roundtrip")
     st = env.stats()[0]
     assert st["res_total"] == int(orc.res.sum()) and st["food_total"] == int(orc.food.sum())
     env.close()
+
+
+@pytest.mark.parametrize("vision,view", [("rgb", "around"), ("channels", "front"), ("rgb", "front")])
+@pytest.mark.parametrize("rules", ["simple", "paper"])
+def test_vision_variants_lockstep(vision, view, rules):
+    """RGB vision with the colour trait (Sec. 3.2, 3.3) and the Front
+    viewing configuration (App. F.6), under both rule sets."""
+    if rules == "simple":
+        w = workloads.scaled("mid", 64, 600, 500, precision="bf16", e_init=190, sigma=0.05,
+                             vision=vision, view=view)
+    else:
+        w = _ecology(64, 600, 500, precision="bf16", vision=vision, view=view)
+    rep = _run(w, 12)
+    assert rep["births"] > 0
+
+
+@pytest.mark.parametrize("k,hidden,view", [(3, 32, "around"), (3, 32, "front"), (7, 64, "front"),
+                                           (9, 64, "around")])
+def test_vision_ranges(k, hidden, view):
+    """The paper's vision ranges 3x3, 7x7 and 9x9 (App. F.6), Around and
+    Front, RGB, paper rules and policy form."""
+    w = _ecology(64, 600, 500, patch_k=k, hidden=hidden, view=view, precision="fp8")
+    rep = _run(w, 10)
+    assert rep["steps"] == 10

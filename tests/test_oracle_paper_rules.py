@@ -360,7 +360,7 @@ def _check(o, before, st):
 
 
 @pytest.mark.parametrize("over", [
-    dict(side=48, slots=800, init_alive=500, e_repro=110, e_child=40, e_init=100),
+    dict(side=48, slots=800, init_alive=500, e_repro=60, e_child=25, e_init=60),
     dict(side=32, slots=300, init_alive=250, e_repro=90, e_child=30, precision="bf16",
          flags=("rotate_obs", "cancel_all"), attack_damage=10, age_div=20),
     dict(side=40, slots=400, init_alive=300, e_repro=70, e_child=50, n_scalars=4, patch_k=5,
