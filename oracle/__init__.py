@@ -43,9 +43,12 @@ FLAG_NAMES = {"auto_eat": AUTO_EAT, "rotate_obs": ROTATE_OBS,
 STAY, NORTH, SOUTH, EAST, WEST, ATTACK, TURN_LEFT, TURN_RIGHT, EAT = range(9)
 
 # Rule sets, and the paper rule set's action codes (Sec. 3.2 "Actions").
-RULES_SIMPLE, RULES_PAPER = 0, 1
-RULES = {"simple": RULES_SIMPLE, "paper": RULES_PAPER}
+RULES_SIMPLE, RULES_PAPER, RULES_TERRAIN = 0, 1, 2
+RULES = {"simple": RULES_SIMPLE, "paper": RULES_PAPER, "terrain": RULES_TERRAIN}
 P_REST, P_ROT_CW, P_ROT_CCW, P_FORWARD, P_ATTACK, P_EAT, P_REPRODUCE = range(7)
+T_DRINK, T_EAT_BIO = 7, 8
+TERRAIN_FIELDS = ("sea_level", "w_init", "w_metab", "w_bite", "w_cap", "w_child", "heal_water",
+                  "b_body", "b_child", "b_bite", "b_cap", "b_site")
 
 # Constants of the paper rule set, read from the workload dictionary (0 when
 # absent: the simple rule set ignores them).
@@ -89,6 +92,9 @@ class Config(ctypes.Structure):
         ("e_act", ctypes.c_int32), ("e_cap", ctypes.c_int32),
         ("e_child", ctypes.c_int32),
         ("vision", ctypes.c_int32), ("view", ctypes.c_int32),
+    ] + [(k, ctypes.c_int32) for k in TERRAIN_FIELDS] + [
+        ("biomass_density", ctypes.c_float), ("photo_q16", ctypes.c_int32),
+        ("res_cap", ctypes.c_int32),
     ]
 
 
@@ -98,7 +104,8 @@ _P = ctypes.c_void_p
 class State(ctypes.Structure):
     _fields_ = [(n, _P) for n in ("food", "wall", "occ", "alive", "x", "y", "facing",
                                   "energy", "parent", "birth_step", "master", "step",
-                                  "hp", "age", "res", "colour")]
+                                  "hp", "age", "res", "colour", "rock", "water", "bio",
+                                  "photo", "a_water", "a_bio")]
 
 
 STAT_FIELDS = ["agent_steps"] + ["act%d" % i for i in range(16)] + [
@@ -106,7 +113,9 @@ STAT_FIELDS = ["agent_steps"] + ["act%d" % i for i in range(16)] + [
     "energy_transferred", "deaths", "dead_energy", "births", "failed_births",
     "regrown", "alive", "food_total", "energy_total",
     "res_total", "eaten_energy", "metab_paid", "heals", "starved", "damage",
-    "food_emptied", "food_refilled"]
+    "food_emptied", "food_refilled",
+    "water_cells", "water_agents", "bio_cells", "bio_agents", "drunk", "water_spent",
+    "thirsty", "bio_eaten", "photo", "dead_water", "dead_bio"]
 
 
 class Stats(ctypes.Structure):
@@ -151,6 +160,7 @@ def lib():
             L.orc_policy.argtypes = [cfgp, stp, ctypes.c_int, ctypes.c_double, _P, _P, _P, _P]
             L.orc_mutate.argtypes = [cfgp, ctypes.c_int64, ctypes.c_int32, _P, _P]
             L.orc_mutate_colour.argtypes = [cfgp, ctypes.c_int64, ctypes.c_int32, _P, _P]
+            L.orc_water_flow.argtypes = [cfgp, stp]
             L.orc_transition.argtypes = [cfgp, stp, _P, ctypes.POINTER(Stats), _P, _P]
             _lib = L
     return _lib
@@ -245,16 +255,19 @@ def make_config(cfg: dict) -> Config:
         if isinstance(cfg.get("policy_form", "plain"), str) else int(cfg["policy_form"]),
         n_hidden=cfg.get("n_hidden", 1),
         rules=RULES[cfg.get("rules", "simple")],
+        biomass_density=float(cfg.get("biomass_density", 0.0)),
+        photo_q16=int(cfg.get("photo_q16", 0)), res_cap=int(cfg.get("res_cap", 0)),
         vision=VISIONS[cfg.get("vision", "channels")],
         view=VIEWS[cfg.get("view", "around")],
-        **{k: int(cfg.get(k, 0)) for k in PAPER_RULE_FIELDS})
+        **{k: int(cfg.get(k, 0)) for k in PAPER_RULE_FIELDS + TERRAIN_FIELDS})
 
 
 class Oracle:
     """One environment held as numpy arrays, stepped by the C oracle."""
 
     ARRAYS = ("food", "wall", "occ", "alive", "x", "y", "facing", "energy",
-              "parent", "birth_step", "master", "step", "hp", "age", "res", "colour")
+              "parent", "birth_step", "master", "step", "hp", "age", "res", "colour",
+              "rock", "water", "bio", "photo", "a_water", "a_bio")
 
     def __init__(self, cfg: dict, allocate: bool = True):
         self.cfg = dict(cfg)
@@ -284,6 +297,16 @@ class Oracle:
             self.age = np.zeros(S, np.int32)
             self.res = np.zeros(N, np.int32)
             self.colour = np.zeros((S, 3), np.float32)
+            # terrain: the rock layer is an input (cfg["rock"], else flat 0)
+            rock = cfg.get("rock")
+            self.rock = (np.zeros(N, np.int32) if rock is None
+                         else np.ascontiguousarray(rock, np.int32).ravel().copy())
+            assert self.rock.size == N
+            self.water = np.zeros(N, np.int32)
+            self.bio = np.zeros(N, np.int32)
+            self.photo = np.zeros(N, np.uint32)
+            self.a_water = np.zeros(S, np.int32)
+            self.a_bio = np.zeros(S, np.int32)
 
     # -- plumbing ----------------------------------------------------------
     def _state(self) -> State:
@@ -342,6 +365,12 @@ class Oracle:
         lib().orc_mutate_colour(ctypes.byref(self.c), int(step), int(parent_slot),
                                 _ptr(parent_rgb), _ptr(child))
         return child
+
+    def water_flow(self) -> None:
+        """One step of the terrain rules' water flow, alone."""
+        st = self._state()
+        if lib().orc_water_flow(ctypes.byref(self.c), ctypes.byref(st)) != 0:
+            raise RuntimeError("oracle water flow failed")
 
     def policy(self, use_master: bool = False, tol: float = 1e-3) -> dict:
         S, A = self.S, self.A

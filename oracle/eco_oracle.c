@@ -77,7 +77,8 @@ enum {
   ST_CLAIM_BIRTH = 9,
   ST_MUTATE = 10,
   ST_REGROW = 11,
-  ST_COLOUR = 12   /* colour trait: initial colour, and its mutation */
+  ST_COLOUR = 12,  /* colour trait: initial colour, and its mutation */
+  ST_BIOMASS = 13  /* terrain rules: initial biomass sites              */
 };
 
 /* Vision (Sec. 3.2 "Sensors"; App. F.6 viewing configurations). */
@@ -98,7 +99,9 @@ enum {
  * a 3x3 attack in front, eat and reproduce actions, resource drop at death. */
 enum {
   ORC_RULES_SIMPLE = 0,
-  ORC_RULES_PAPER = 1
+  ORC_RULES_PAPER = 1,
+  ORC_RULES_TERRAIN = 2  /* the paper rules plus rock, flowing water and
+                            biomass (Sec. 3.2 "Terrain", "Resources")     */
 };
 
 /* Action codes of the paper rule set (Sec. 3.2 "Actions": rest, three
@@ -112,7 +115,10 @@ enum {
   P_ATTACK = 4,
   P_EAT = 5,
   P_REPRODUCE = 6,
-  P_N_ACTIONS = 7
+  P_N_ACTIONS = 7,
+  T_DRINK = 7,      /* terrain rules: the eat action of water            */
+  T_EAT_BIO = 8,    /* terrain rules: the eat action of biomass          */
+  T_N_ACTIONS = 9
 };
 
 /* Action codes of the simple rule set.  Small config: 0..5; mid and larger
@@ -163,6 +169,20 @@ typedef struct {
   int32_t e_child;       /* energy a parent hands to its child             */
   int32_t vision;        /* ORC_VISION_CHANNELS or ORC_VISION_RGB          */
   int32_t view;          /* ORC_VIEW_AROUND or ORC_VIEW_FRONT              */
+  /* Terrain rule set only (water and biomass in whole units). */
+  int32_t sea_level;     /* reset: water depth sea_level - rock below it   */
+  int32_t w_init;        /* founders' water                                */
+  int32_t w_metab;       /* water spent per step, returned to the cell     */
+  int32_t w_bite, w_cap; /* water drunk per drink action; water capacity   */
+  int32_t w_child;       /* water a parent hands to its child              */
+  int32_t heal_water;    /* water spent (returned) per step of healing     */
+  int32_t b_body;        /* biomass of a body: founders carry it           */
+  int32_t b_child;       /* biomass a parent hands to its child            */
+  int32_t b_bite, b_cap; /* biomass per eat-biomass action; capacity       */
+  int32_t b_site;        /* biomass on an initial biomass site             */
+  float biomass_density; /* probability that a cell is a biomass site      */
+  int32_t photo_q16;     /* energy grown per biomass unit per step, 2^-16  */
+  int32_t res_cap;       /* most energy a cell holds                       */
 } orc_config;
 
 enum {
@@ -188,6 +208,12 @@ typedef struct {
   int32_t *res;        /* [L*L] paper rules: energy lying on the cell;    */
                        /*   food[c] == (res[c] > 0)                       */
   float *colour;       /* [S][3] colour trait (Sec. 3.3), RGB in [0, 1]   */
+  int32_t *rock;       /* [L*L] terrain: rock height (an input)           */
+  int32_t *water;      /* [L*L] terrain: water on the cell                */
+  int32_t *bio;        /* [L*L] terrain: free biomass on the cell         */
+  uint32_t *photo;     /* [L*L] terrain: photosynthesis remainder, 2^-16  */
+  int32_t *a_water;    /* [S] terrain: water carried                      */
+  int32_t *a_bio;      /* [S] terrain: biomass carried                    */
 } orc_state;
 
 typedef struct {
@@ -217,6 +243,19 @@ typedef struct {
   int64_t damage;             /* HP dealt by attacks                     */
   int64_t food_emptied;       /* cells emptied by eating                 */
   int64_t food_refilled;      /* empty cells that received a death drop  */
+                              /* (terrain: or grew energy)               */
+  /* terrain rules only */
+  int64_t water_cells;        /* water on cells at the end               */
+  int64_t water_agents;       /* water carried at the end                */
+  int64_t bio_cells;          /* free biomass at the end                 */
+  int64_t bio_agents;         /* biomass carried at the end              */
+  int64_t drunk;              /* water moved from cells into agents      */
+  int64_t water_spent;        /* water agents spent (back on their cell) */
+  int64_t thirsty;            /* agent-steps without the water to spend  */
+  int64_t bio_eaten;          /* biomass moved from cells into agents    */
+  int64_t photo;              /* energy grown on free biomass            */
+  int64_t dead_water;         /* water dropped by agents that died       */
+  int64_t dead_bio;           /* biomass dropped by agents that died     */
 } orc_stats;
 
 /* ------------------------------------------------------------------------ */
@@ -231,8 +270,14 @@ typedef struct {
 /* (+ compass with 8 scalars), L = n_hidden, ReLU, unbiased head, tau.      */
 /* ------------------------------------------------------------------------ */
 
+/* Channels per patch cell: 3, or 4 under the terrain rules (Sec. 3.2:
+ * three colour channels and the local difference in elevation). */
+static int patch_channels(const orc_config *c) {
+  return c->rules == ORC_RULES_TERRAIN ? 4 : 3;
+}
+
 int orc_obs_dim(const orc_config *c) {
-  return 3 * c->patch_k * c->patch_k + c->n_scalars;
+  return patch_channels(c) * c->patch_k * c->patch_k + c->n_scalars;
 }
 
 typedef struct {
@@ -296,7 +341,7 @@ static int is_weight(const orc_shape *s, int p) {
  * internal scalars (energy and the reserved zeros).  The plain form treats
  * the whole observation as one input. */
 static int sensor_fan_in(const orc_config *c, const orc_shape *s, int j) {
-  int patch = 3 * c->patch_k * c->patch_k;
+  int patch = patch_channels(c) * c->patch_k * c->patch_k;
   if (c->policy_form != ORC_PAPER_FORM) return s->D;
   if (j < patch) return patch;
   if (c->n_scalars >= 8 && j >= patch + 1 && j < patch + 5) return 4;
@@ -535,6 +580,8 @@ int orc_reset(const orc_config *c, orc_state *s) {
   int P = orc_n_params(c);
   uint32_t thr_wall = orc_threshold(c->wall_density);
   uint32_t thr_food = orc_threshold(c->food_density);
+  uint32_t thr_bio = orc_threshold(c->biomass_density);
+  int terrain = c->rules == ORC_RULES_TERRAIN;
   uint64_t *keys;
   int32_t *chosen;
   int cell, nfree = 0, i, slot;
@@ -547,8 +594,19 @@ int orc_reset(const orc_config *c, orc_state *s) {
     draw4(c, ST_FOOD_INIT, (uint32_t)(cell >> 2), 0u, 0u, r);
     s->food[cell] = (uint8_t)(!s->wall[cell] && r[cell & 3] < thr_food);
     /* paper rules: a food cell holds one bite, e_food energy */
-    s->res[cell] = (c->rules == ORC_RULES_PAPER && s->food[cell]) ? c->e_food : 0;
+    s->res[cell] = (c->rules != ORC_RULES_SIMPLE && s->food[cell]) ? c->e_food : 0;
     s->occ[cell] = -1;
+    /* terrain rules: water fills the cells whose rock lies below sea level
+     * (Sec. 3.2 "Terrain"); a Bernoulli(biomass_density) site (stream
+     * BIOMASS) holds b_site biomass.  The rock itself is an input. */
+    s->water[cell] = 0;
+    s->bio[cell] = 0;
+    s->photo[cell] = 0;
+    if (terrain && !s->wall[cell]) {
+      if (s->rock[cell] < c->sea_level) s->water[cell] = c->sea_level - s->rock[cell];
+      draw4(c, ST_BIOMASS, (uint32_t)(cell >> 2), 0u, 0u, r);
+      if (r[cell & 3] < thr_bio) s->bio[cell] = c->b_site;
+    }
   }
 
   /* Founders: the K non-wall cells with the smallest (PLACE draw, cell)
@@ -579,6 +637,8 @@ int orc_reset(const orc_config *c, orc_state *s) {
     s->birth_step[slot] = -1;
     s->hp[slot] = 0;
     s->age[slot] = 0;
+    s->a_water[slot] = 0;
+    s->a_bio[slot] = 0;
     s->colour[3 * slot + 0] = s->colour[3 * slot + 1] = s->colour[3 * slot + 2] = 0.0f;
   }
   for (i = 0; i < K; i++) {
@@ -589,7 +649,9 @@ int orc_reset(const orc_config *c, orc_state *s) {
     draw4(c, ST_FACING_INIT, (uint32_t)(i >> 2), 0u, 0u, r);
     s->facing[i] = (uint8_t)(r[i & 3] >> 30);
     s->energy[i] = c->e_init;
-    s->hp[i] = c->rules == ORC_RULES_PAPER ? c->hp_max : 0;
+    s->hp[i] = c->rules != ORC_RULES_SIMPLE ? c->hp_max : 0;
+    s->a_water[i] = terrain ? c->w_init : 0;
+    s->a_bio[i] = terrain ? c->b_body : 0;
     /* colour trait: three uniforms of COLOUR at counter (slot, 0, 0, 0) */
     draw4(c, ST_COLOUR, (uint32_t)i, 0u, 0u, r);
     s->colour[3 * i + 0] = (float)orc_uniform(r[0]);
@@ -626,14 +688,25 @@ int orc_reset(const orc_config *c, orc_state *s) {
 /* (0, 1, 0) and an empty cell black.                                        */
 /* ------------------------------------------------------------------------ */
 
+/* Terrain rules: 4 channels per cell.  RGB as above, except that a cell
+ * with neither agent nor wall shows its resources: (B / (B + b_bite),
+ * r / (r + e_food), W / (W + w_bite)) for its biomass B, energy r and water
+ * W; the fourth channel is the rock height difference d to the agent's own
+ * cell as d / (|d| + 16).  16 scalars: [e / e_repro, compass x4, HP, age,
+ * r, carried water / w_cap, carried biomass / b_cap, W / (W + w_bite),
+ * B / (B + b_bite) of the agent's cell, zeros]. */
+static double ratio(double v, double scale) { return v / (v + scale); }
+
 void orc_observe(const orc_config *c, const orc_state *s, int32_t slot, double *x) {
-  int L = c->side, k = c->patch_k, R = k / 2;
+  int L = c->side, k = c->patch_k, R = k / 2, nch = patch_channels(c);
+  int terrain = c->rules == ORC_RULES_TERRAIN;
   int f = s->facing[slot];
   int right = (f + 1) & 3;
-  int r, col, i, base = 3 * k * k;
+  int here = cell_of(s->x[slot], s->y[slot], L);
+  int r, col, i, base = nch * k * k;
   for (r = 0; r < k; r++) {
     for (col = 0; col < k; col++) {
-      int dx, dy, cell, idx = (r * k + col) * 3;
+      int dx, dy, cell, idx = (r * k + col) * nch;
       if (c->flags & ORC_ROTATE_OBS) {
         /* rows run from far ahead (top) to behind (Around) or to the
          * agent's own row (Front); columns from its left to its right */
@@ -650,8 +723,16 @@ void orc_observe(const orc_config *c, const orc_state *s, int32_t slot, double *
         for (ch = 0; ch < 3; ch++) {
           if (who >= 0) x[idx + ch] = (double)s->colour[3 * who + ch];
           else if (s->wall[cell]) x[idx + ch] = 0.5;
+          else if (terrain)
+            x[idx + ch] = ch == 0 ? ratio(s->bio[cell], c->b_bite)
+                        : ch == 1 ? ratio(s->res[cell], c->e_food)
+                                  : ratio(s->water[cell], c->w_bite);
           else if (s->food[cell]) x[idx + ch] = ch == 1 ? 1.0 : 0.0;
           else x[idx + ch] = 0.0;
+        }
+        if (terrain) {
+          double d = (double)s->rock[cell] - (double)s->rock[here];
+          x[idx + 3] = d / (fabs(d) + 16.0);
         }
         continue;
       }
@@ -663,13 +744,18 @@ void orc_observe(const orc_config *c, const orc_state *s, int32_t slot, double *
   for (i = 0; i < c->n_scalars; i++) x[base + i] = 0.0;
   x[base] = (double)s->energy[slot] / (double)c->e_repro;
   if (c->n_scalars >= 8) x[base + 1 + f] = 1.0;
-  if (c->rules == ORC_RULES_PAPER) {
+  if (c->rules != ORC_RULES_SIMPLE) {
     int extra = c->n_scalars >= 8 ? base + 5 : base + 1;
-    int here = cell_of(s->x[slot], s->y[slot], L);
-    double age = (double)s->age[slot], res = (double)s->res[here];
+    double age = (double)s->age[slot];
     x[extra + 0] = (double)s->hp[slot] / (double)c->hp_max;
     x[extra + 1] = age / (age + (double)c->age_div);
-    x[extra + 2] = res / (res + (double)c->e_food);
+    x[extra + 2] = ratio(s->res[here], c->e_food);
+  }
+  if (terrain) {
+    x[base + 8] = (double)s->a_water[slot] / (double)c->w_cap;
+    x[base + 9] = (double)s->a_bio[slot] / (double)c->b_cap;
+    x[base + 10] = ratio(s->water[here], c->w_bite);
+    x[base + 11] = ratio(s->bio[here], c->b_bite);
   }
 }
 
@@ -882,11 +968,62 @@ static int cell_ahead(int x, int y, int f, int fwd, int lat, int L) {
   return cell_of(wrap(x + dx, L), wrap(y + dy, L), L);
 }
 
+/* One step of the water flow (Sec. 3.2 "Terrain": water flows downhill
+ * over the rock layer in a discrete flow simulation).  Reading: each
+ * non-wall cell holding water compares its surface, rock + water, with the
+ * surfaces of its four non-wall neighbours; the lowest (the first of N, E,
+ * S, W on ties) receives min(water, floor((surface - lowest) / 5)) when it
+ * is strictly lower.  Every transfer is computed from the surfaces before
+ * the step, so no order of the cells matters.  Sending at most a fifth of
+ * the drop (one more than the number of neighbours) keeps a cell that
+ * receives from all four neighbours from rising above them. */
+int orc_water_flow(const orc_config *c, orc_state *s) {
+  int L = c->side, N = L * L, cell, d;
+  int32_t *out = (int32_t *)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+  int32_t *to = (int32_t *)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+  if (!out || !to) {
+    free(out);
+    free(to);
+    return -1;
+  }
+  for (cell = 0; cell < N; cell++) {
+    int64_t here, lowest = 0;
+    int best = -1;
+    out[cell] = 0;
+    to[cell] = -1;
+    if (s->wall[cell] || s->water[cell] <= 0) continue;
+    here = (int64_t)s->rock[cell] + s->water[cell];
+    for (d = 0; d < 4; d++) {
+      int n = neighbour(cell % L, cell / L, d, L);
+      int64_t h;
+      if (s->wall[n]) continue;
+      h = (int64_t)s->rock[n] + s->water[n];
+      if (best < 0 || h < lowest) {
+        best = n;
+        lowest = h;
+      }
+    }
+    if (best >= 0 && lowest < here) {
+      int64_t amount = (here - lowest) / 5;
+      if (amount > s->water[cell]) amount = s->water[cell];
+      out[cell] = (int32_t)amount;
+      to[cell] = best;
+    }
+  }
+  for (cell = 0; cell < N; cell++) s->water[cell] -= out[cell];
+  for (cell = 0; cell < N; cell++)
+    if (to[cell] >= 0) s->water[to[cell]] += out[cell];
+  free(out);
+  free(to);
+  return 0;
+}
+
 int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
                    orc_stats *st, int32_t *birth_parent, int32_t *birth_child) {
   int L = c->side, N = L * L, S = c->slots, A = c->n_actions;
   int P = orc_n_params(c);
-  int paper = c->rules == ORC_RULES_PAPER;
+  int paper = c->rules != ORC_RULES_SIMPLE;  /* the paper or the terrain rules */
+  int terrain = c->rules == ORC_RULES_TERRAIN;
   int64_t t = *s->step;
   uint32_t thr_regrow = orc_threshold(c->regrow_p);
   uint64_t *best_cell = (uint64_t *)calloc((size_t)N, sizeof(uint64_t));
@@ -976,11 +1113,36 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
   /* 3. Eat.  Simple rules: the food on the agent's cell (automatic in the
    *    small rule set, the eat action otherwise) becomes e_food energy.
    *    Paper rules: the eat action moves one bite, min(e_food, energy on
-   *    the cell, e_cap - energy), from the cell into the stomach. */
+   *    the cell, e_cap - energy), from the cell into the stomach.  Terrain
+   *    rules add the eat actions of the other two resources: drink moves
+   *    min(w_bite, water on the cell, w_cap - water carried), eat-biomass
+   *    min(b_bite, biomass on the cell, b_cap - biomass carried). */
   for (slot = 0; slot < S; slot++) {
     int here;
     if (!s->alive[slot]) continue;
     here = cell_of(s->x[slot], s->y[slot], L);
+    if (terrain && action[slot] == T_DRINK) {
+      int32_t sip = c->w_bite;
+      if (s->water[here] < sip) sip = s->water[here];
+      if (c->w_cap - s->a_water[slot] < sip) sip = c->w_cap - s->a_water[slot];
+      if (sip > 0) {
+        s->water[here] -= sip;
+        s->a_water[slot] += sip;
+        st->drunk += sip;
+      }
+      continue;
+    }
+    if (terrain && action[slot] == T_EAT_BIO) {
+      int32_t bite = c->b_bite;
+      if (s->bio[here] < bite) bite = s->bio[here];
+      if (c->b_cap - s->a_bio[slot] < bite) bite = c->b_cap - s->a_bio[slot];
+      if (bite > 0) {
+        s->bio[here] -= bite;
+        s->a_bio[slot] += bite;
+        st->bio_eaten += bite;
+      }
+      continue;
+    }
     if (paper) {
       int32_t bite = c->e_food;
       if (action[slot] != P_EAT) continue;
@@ -1061,7 +1223,13 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
    *    HP.  A survivor below hp_max with at least heal_cost energy heals
    *    heal_rate HP (capped at hp_max) for heal_cost energy.  At HP <= 0 the
    *    agent dies and its energy is dropped on its cell; otherwise it ages
-   *    by one step. */
+   *    by one step.
+   *    Terrain rules: after the energy, every agent spends w_metab water,
+   *    which goes back onto its cell (Sec. 3.2: spent water returns to the
+   *    landscape); without enough water it spends what it has and loses
+   *    starve_damage HP.  Healing also needs, and spends onto the cell,
+   *    heal_water water.  A dying agent drops its energy, water and
+   *    biomass on its cell. */
   for (slot = 0; slot < S; slot++) {
     int here;
     if (!s->alive[slot]) continue;
@@ -1078,18 +1246,43 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
         hp -= c->starve_damage;
         st->starved++;
       }
+      if (terrain) {
+        int32_t spend = c->w_metab;
+        if (s->a_water[slot] < spend) {
+          spend = s->a_water[slot];
+          hp -= c->starve_damage;
+          st->thirsty++;
+        }
+        s->a_water[slot] -= spend;
+        s->water[here] += spend;
+        st->water_spent += spend;
+      }
       hp -= dmg[slot];
       hp -= s->age[slot] / c->age_div;
-      if (hp > 0 && hp < c->hp_max && c->heal_rate > 0 && s->energy[slot] >= c->heal_cost) {
+      if (hp > 0 && hp < c->hp_max && c->heal_rate > 0 && s->energy[slot] >= c->heal_cost &&
+          (!terrain || s->a_water[slot] >= c->heal_water)) {
         hp += c->heal_rate;
         if (hp > c->hp_max) hp = c->hp_max;
         s->energy[slot] -= c->heal_cost;
+        if (terrain) {
+          s->a_water[slot] -= c->heal_water;
+          s->water[here] += c->heal_water;
+          st->water_spent += c->heal_water;
+        }
         st->heals++;
       }
       if (hp <= 0) {
         int32_t e = s->energy[slot];
         st->deaths++;
         st->dead_energy += e;
+        if (terrain) {
+          s->water[here] += s->a_water[slot];
+          s->bio[here] += s->a_bio[slot];
+          st->dead_water += s->a_water[slot];
+          st->dead_bio += s->a_bio[slot];
+          s->a_water[slot] = 0;
+          s->a_bio[slot] = 0;
+        }
         if (e > 0 && s->res[here] == 0) {
           s->food[here] = 1;
           st->food_refilled++;
@@ -1123,7 +1316,10 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
    *    ascending order; winners left without a slot keep their energy.
    *    Simple rules: the child gets floor(e/2), the parent keeps the rest.
    *    Paper rules: the parent hands e_child to the child, which starts at
-   *    hp_child HP and age 0.  The child faces as the parent did and
+   *    hp_child HP and age 0.  Terrain rules: the parent must also carry
+   *    b_body + b_child biomass (its own body and the child's: Sec. 3.2,
+   *    biomass is needed to exist) and w_child water, and hands b_child and
+   *    w_child to the child.  The child faces as the parent did and
    *    carries the parent's parameters mutated by sigma * N(0,1). */
   for (i = 0; i < N; i++) best_cell[i] = 0;
   for (slot = 0; slot < S; slot++) {
@@ -1132,6 +1328,7 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
     target[slot] = -1;
     if (!s->alive[slot] || s->energy[slot] < c->e_repro) continue;
     if (paper && action[slot] != P_REPRODUCE) continue;
+    if (terrain && (s->a_bio[slot] < c->b_body + c->b_child || s->a_water[slot] < c->w_child)) continue;
     tc = neighbour(s->x[slot], s->y[slot], (s->facing[slot] + 2) & 3, L);
     if (s->wall[tc] || s->occ[tc] != -1) continue;
     target[slot] = tc;
@@ -1156,6 +1353,12 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
     s->energy[ch] = ce;
     s->hp[ch] = paper ? c->hp_child : 0;
     s->age[ch] = 0;
+    if (terrain) {
+      s->a_water[p] -= c->w_child;
+      s->a_water[ch] = c->w_child;
+      s->a_bio[p] -= c->b_child;
+      s->a_bio[ch] = c->b_child;
+    }
     s->alive[ch] = 1;
     s->x[ch] = tc % L;
     s->y[ch] = tc / L;
@@ -1184,14 +1387,48 @@ int orc_transition(const orc_config *c, orc_state *s, const uint8_t *action,
     }
   }
 
+  /* 8. Terrain rules: energy grows on free biomass (Sec. 3.2; App. F.2
+   *    "biomass photosynthesis rate"), then the water flows one step. */
+  if (terrain) {
+    for (cell = 0; cell < N; cell++) {
+      uint64_t acc;
+      int64_t gain, room;
+      if (s->wall[cell] || s->bio[cell] <= 0) continue;
+      acc = (uint64_t)s->photo[cell] + (uint64_t)s->bio[cell] * (uint64_t)c->photo_q16;
+      gain = (int64_t)(acc >> 16);
+      s->photo[cell] = (uint32_t)(acc & 0xFFFFu);
+      room = (int64_t)c->res_cap - s->res[cell];
+      if (gain > room) gain = room;
+      if (gain <= 0) continue;
+      if (s->res[cell] == 0) {
+        s->food[cell] = 1;
+        st->food_refilled++;
+      }
+      s->res[cell] += (int32_t)gain;
+      st->photo += gain;
+    }
+    if (orc_water_flow(c, s) != 0) {
+      rc = -1;
+      goto done;
+    }
+  }
+
   for (slot = 0; slot < S; slot++) {
     if (!s->alive[slot]) continue;
     st->alive++;
     st->energy_total += s->energy[slot];
+    if (terrain) {
+      st->water_agents += s->a_water[slot];
+      st->bio_agents += s->a_bio[slot];
+    }
   }
   for (cell = 0; cell < N; cell++) {
     st->food_total += s->food[cell];
     if (paper) st->res_total += s->res[cell];
+    if (terrain) {
+      st->water_cells += s->water[cell];
+      st->bio_cells += s->bio[cell];
+    }
   }
   *s->step = t + 1;
 

@@ -74,14 +74,73 @@ PAPER_RULES = dict(rules="paper", n_actions=7, hp_max=40, hp_child=20, attack_da
 ECOLOGY = dict(PAPER_FORM, name="ecology-1024x1024-65536slots-RCV+A-rgb-2x64-7act-bf16",
                vision="rgb", view="around", **PAPER_RULES)
 
+# The terrain rules (Sec. 3.2 "Terrain", "Resources and Agent Health"; App.
+# F.2): the paper rules plus a rock layer with sea level 32, water that
+# flows downhill, and biomass.  Agents carry water (60 at birth of a
+# founder, 1 spent per step back onto their cell, drinks of 10, capacity
+# 100) and biomass (a body of 10; children get a body of 10 from their
+# parent; bites of 5, capacity 50).  A quarter of the cells start as
+# biomass sites of 20 (App. F.2: initial site density 1/4), on which energy
+# grows at 0.01 per biomass unit per step (App. F.2: photosynthesis rate
+# 0.01; 655 / 2^16), up to 100 per cell; there is no random regrowth.
+# Vision: RGB plus the elevation channel; 16 scalars (internal and
+# external sensors of all three resources).
+TERRAIN_RULES = dict(PAPER_RULES, rules="terrain", n_actions=9, n_scalars=16, vision="rgb",
+                     sea_level=32, w_init=60, w_metab=1, w_bite=10, w_cap=100, w_child=30,
+                     heal_water=1, b_body=10, b_child=10, b_bite=5, b_cap=50, b_site=20,
+                     biomass_density=0.25, photo_q16=655, res_cap=100, regrow_p=0.0)
+
+# The terrain rules on the paper-scale world, "beach" terrain.
+TERRAIN = dict(ECOLOGY, name="terrain-beach-1024x1024-65536slots-RCV+A-2x64-9act-bf16",
+               terrain="beach", **TERRAIN_RULES)
+
 WORKLOADS = {"small": SMALL, "mid": MID, "paper": PAPER, "large": LARGE,
-             "paperform": PAPER_FORM, "ecology": ECOLOGY}
+             "paperform": PAPER_FORM, "ecology": ECOLOGY, "terrain": TERRAIN}
+
+TERRAINS = ("ocean", "beach", "island", "lake", "isthmus", "channel")
+
+
+def terrain(preset: str, side: int, seed: int = 0) -> np.ndarray:
+    """A synthetic rock layer (int32 heights, [side * side], row-major) for
+    the paper's named terrains (Sec. 3.2 "Terrain": Ocean, Beach, Island,
+    Lake, Isthmus, Channel), whose generator the paper does not give.  A
+    base shape in [0, 64] against sea level 32 -- ocean: all below; beach:
+    rising from west to east; island: a central hill; lake: a central
+    basin; isthmus: a north-south ridge between two seas; channel: an
+    east-west trough through land -- plus value noise of amplitude 8
+    (uniform draws of numpy's seeded generator on a 16-cell lattice,
+    bilinearly interpolated), rounded and clipped to [0, 96].  An input
+    generator: none of the simulator's arithmetic."""
+    u = (np.arange(side) + 0.5) / side
+    X, Y = np.meshgrid(u, u)           # X: column (east), Y: row (south)
+    r = np.hypot(X - 0.5, Y - 0.5)
+    base = {
+        "ocean": np.full_like(X, 16.0),
+        "beach": 64.0 * X,
+        "island": 64.0 - 128.0 * r,
+        "lake": 128.0 * r,
+        "isthmus": 64.0 - 256.0 * np.abs(X - 0.5),
+        "channel": 256.0 * np.abs(Y - 0.5),
+    }[preset]
+    rng = np.random.default_rng(seed)
+    n = side // 16 + 2
+    lattice = rng.uniform(-8.0, 8.0, size=(n, n))
+    g = np.arange(side) / 16.0
+    i0 = np.floor(g).astype(int)
+    f = g - i0
+    rows = lattice[i0] * (1 - f)[:, None] + lattice[i0 + 1] * f[:, None]
+    noise = rows[:, i0] * (1 - f)[None, :] + rows[:, i0 + 1] * f[None, :]
+    rock = np.clip(np.rint(np.maximum(base, 0.0) + noise), 0, 96).astype(np.int32)
+    return rock.ravel()
 
 
 def get(key: str, **overrides) -> dict:
-    """A copy of a named workload with fields overridden."""
+    """A copy of a named workload with fields overridden.  A workload with a
+    terrain preset gets its rock layer (key "rock") for its side and seed."""
     w = copy.deepcopy(WORKLOADS[key])
     w.update(overrides)
+    if w.get("terrain") and "rock" not in overrides:
+        w["rock"] = terrain(w["terrain"], w["side"], w.get("seed", 0))
     return w
 
 
@@ -90,6 +149,8 @@ def scaled(base: str, side: int, slots: int, init_alive: int, **overrides) -> di
     w = get(base, side=side, slots=slots, init_alive=init_alive)
     w["name"] = "%s-%dx%d-%dslots" % (base, side, side, slots)
     w.update(overrides)
+    if w.get("terrain") and "rock" not in overrides:
+        w["rock"] = terrain(w["terrain"], w["side"], w.get("seed", 0))
     return w
 
 
