@@ -191,7 +191,8 @@ class ClockSampler:
 def mlp_shape(w) -> str:
     """Layer widths of the policy: input, H per hidden activation, actions."""
     layers = w.get("n_hidden", 1) if w.get("policy_form", "plain") == "paper" else 1
-    return "-".join(str(v) for v in [3 * w["patch_k"] ** 2 + w["n_scalars"]]
+    nch = 4 if w.get("rules") == "terrain" else 3     # terrain: + elevation channel
+    return "-".join(str(v) for v in [nch * w["patch_k"] ** 2 + w["n_scalars"]]
                     + [w["hidden"]] * (1 + layers) + [w["n_actions"]])
 
 

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define ECO_ABI_VERSION 3
+#define ECO_ABI_VERSION 4
 
 /* Status codes. */
 #define ECO_OK 0
@@ -98,6 +98,33 @@ extern "C" {
  *     regrow_p. */
 #define ECO_RULES_SIMPLE 0
 #define ECO_RULES_PAPER 1
+/* Terrain rules (Sec. 3.2 "Terrain", "Resources and Agent Health"; App.
+ * F.2): the paper rules plus
+ *   - a rock layer (eco_set_rock) and water: eco_reset fills every non-wall
+ *     cell below sea_level to the sea level; each step the water flows: a
+ *     cell with water sends min(water, floor(drop / 5)) to its lowest open
+ *     neighbour (first of N, E, S, W) when that neighbour's surface
+ *     (rock + water) lies `drop` below its own, all computed from the
+ *     surfaces before the step;
+ *   - biomass: a Bernoulli(biomass_density) site holds b_site at reset;
+ *     free biomass grows energy at photo_q16 / 2^16 per unit per step (a
+ *     per-cell fixed-point remainder keeps the sum exact), up to res_cap
+ *     energy per cell;
+ *   - agents carry water and biomass: founders w_init and b_body; every step
+ *     spends w_metab water onto the agent's cell (not enough: it spends what
+ *     it has and loses starve_damage HP); healing also needs and spends
+ *     heal_water; drink / eat-biomass take min(bite, on the cell, room);
+ *     reproduction also needs b_body + b_child biomass and w_child water and
+ *     hands b_child and w_child to the child; a dying agent drops its
+ *     energy, water and biomass on its cell;
+ *   - vision: RGB (needs ECO_VISION_RGB) with 4 channels per cell -- an
+ *     agent's colour, a wall's grey, else (B/(B+b_bite), r/(r+e_food),
+ *     W/(W+w_bite)) of the cell's biomass, energy and water -- and the rock
+ *     difference d to the agent's cell as d/(|d|+16); 16 scalars:
+ *     [e/e_repro, compass x4, HP/hp_max, age/(age+age_div), r/(r+e_food),
+ *     water/w_cap, biomass/b_cap, W/(W+w_bite), B/(B+b_bite) of its own
+ *     cell, 0, 0, 0, 0]. */
+#define ECO_RULES_TERRAIN 2
 
 /* Vision (Sec. 3.2 "Sensors": a top-down patch with three colour channels)
  * and viewing configuration (App. F.6).  Channels: per cell (food, agent,
@@ -116,7 +143,8 @@ extern "C" {
 /* Action codes.  Simple rules: 0 stay, 1 north, 2 south, 3 east, 4 west,
  * 5 attack; nine-action sets add 6 turn-left, 7 turn-right, 8 eat.  Paper
  * rules (7 actions): 0 rest, 1 rotate clockwise, 2 rotate counter-
- * clockwise, 3 forward, 4 attack, 5 eat, 6 reproduce. */
+ * clockwise, 3 forward, 4 attack, 5 eat, 6 reproduce.  Terrain rules (9):
+ * those and 7 drink, 8 eat biomass. */
 
 typedef struct eco_handle eco_handle;
 
@@ -131,7 +159,7 @@ typedef struct {
   const int32_t *env_init_alive; /* [n_envs] founders placed by eco_reset    */
   const uint32_t *env_seed;      /* [n_envs] Philox seed                     */
   int32_t patch_k;               /* odd patch side k: D = 3k^2 + n_scalars   */
-  int32_t n_scalars;             /* 4 or 8                                   */
+  int32_t n_scalars;             /* 4 or 8; 16 under the terrain rules       */
   int32_t hidden;                /* H in {32, 64, 128}                       */
   int32_t n_actions;             /* A in {6, 9}; 7 under the paper rules     */
   int32_t precision;             /* ECO_FP32 / ECO_BF16 / ECO_FP8_E4M3       */
@@ -170,6 +198,20 @@ typedef struct {
   int32_t e_child;               /* energy handed to a child, in [1, e_repro] */
   int32_t vision;                /* ECO_VISION_CHANNELS or ECO_VISION_RGB    */
   int32_t view;                  /* ECO_VIEW_AROUND or ECO_VIEW_FRONT        */
+  /* Terrain rules only (whole units of water and biomass). */
+  int32_t sea_level;             /* water level at reset                     */
+  int32_t w_init;                /* founders' water, in [0, w_cap]           */
+  int32_t w_metab;               /* water spent per step, >= 0               */
+  int32_t w_bite, w_cap;         /* drink amount, water capacity, >= 1       */
+  int32_t w_child;               /* water handed to a child, >= 0            */
+  int32_t heal_water;            /* water per step of healing, >= 0          */
+  int32_t b_body;                /* founders' biomass, in [0, b_cap]         */
+  int32_t b_child;               /* biomass handed to a child, >= 0          */
+  int32_t b_bite, b_cap;         /* eat-biomass amount, capacity, >= 1       */
+  int32_t b_site;                /* biomass on an initial site, >= 0         */
+  float biomass_density;         /* initial biomass site probability         */
+  int32_t photo_q16;             /* energy per biomass unit per step, 2^-16  */
+  int32_t res_cap;               /* most energy a cell holds, >= e_food      */
 } eco_config;
 
 /* Statistics, one record per environment (App. E measurement API).
@@ -206,7 +248,20 @@ enum {
   ECO_STAT_STARVED,           /* (sum) agent-steps whose cost exceeded e    */
   ECO_STAT_DAMAGE,            /* (sum) HP dealt by attacks                  */
   ECO_STAT_FOOD_EMPTIED,      /* (sum) cells emptied by eating              */
-  ECO_STAT_FOOD_REFILLED,     /* (sum) empty cells that received a drop     */
+  ECO_STAT_FOOD_REFILLED,     /* (sum) empty cells that received a drop
+                                 (terrain: or grew energy)                  */
+  /* terrain rules only (0 otherwise) */
+  ECO_STAT_WATER_CELLS,       /* (now) water on cells                       */
+  ECO_STAT_WATER_AGENTS,      /* (now) water carried                        */
+  ECO_STAT_BIO_CELLS,         /* (now) free biomass                         */
+  ECO_STAT_BIO_AGENTS,        /* (now) biomass carried                      */
+  ECO_STAT_DRUNK,             /* (sum) water moved from cells into agents   */
+  ECO_STAT_WATER_SPENT,       /* (sum) water agents spent onto their cells  */
+  ECO_STAT_THIRSTY,           /* (sum) agent-steps without w_metab water    */
+  ECO_STAT_BIO_EATEN,         /* (sum) biomass moved from cells into agents */
+  ECO_STAT_PHOTO,             /* (sum) energy grown on free biomass         */
+  ECO_STAT_DEAD_WATER,        /* (sum) water dropped by agents that died    */
+  ECO_STAT_DEAD_BIO,          /* (sum) biomass dropped by agents that died  */
   ECO_N_STATS
 };
 
@@ -234,6 +289,11 @@ typedef struct {
                           write, food is taken as res > 0 (the food array
                           is then ignored)                                  */
   float *colour;       /* [slots][3] colour trait, RGB in [0, 1]            */
+  int32_t *water;      /* [L*L] terrain rules: water on the cell            */
+  int32_t *bio;        /* [L*L] terrain rules: free biomass on the cell     */
+  uint32_t *photo;     /* [L*L] terrain rules: photosynthesis remainder     */
+  int32_t *a_water;    /* [slots] terrain rules: water carried              */
+  int32_t *a_bio;      /* [slots] terrain rules: biomass carried            */
 } eco_state_view;
 
 /* Parameter count P and observation size D for a configuration.
@@ -273,6 +333,17 @@ int eco_read_stats(eco_handle *h, eco_stats *total, eco_stats *last, int32_t n_e
  * y), then re-derives the derived device tables.  Both synchronise. */
 int eco_read_state(eco_handle *h, int32_t env, eco_state_view *out);
 int eco_write_state(eco_handle *h, int32_t env, const eco_state_view *in);
+
+/* Terrain rules: the rock layer of env (Sec. 3.2 "Terrain": each map has a
+ * rock layer defining the height of each cell), host array rock[L*L] of
+ * heights in [0, 65535], cells indexed y * L + x.  The paper gives no
+ * generator for its terrains: the caller supplies the heights.  Kept until
+ * the next eco_set_rock (eco_create starts from a flat 0 layer); the next
+ * eco_reset fills the cells below sea_level, and the flow and the vision's
+ * elevation channel use it at once.  ECO_EINVAL under the other rule sets
+ * or for heights out of range.  Synchronises. */
+int eco_set_rock(eco_handle *h, int32_t env, const int32_t *rock);
+int eco_get_rock(eco_handle *h, int32_t env, int32_t *rock);
 
 /* FP32 master parameters of slots [slot0, slot0 + n) of env, logical
  * order, host array [n][P].  Writing also re-derives the streamed

@@ -86,17 +86,21 @@ static int validate(const eco_config *c, char *msg, size_t n) {
   if (!c->env_side || !c->env_slots || !c->env_init_alive || !c->env_seed)
     return snprintf(msg, n, "null per-environment array"), ECO_EINVAL;
   if (c->patch_k < 1 || (c->patch_k & 1) == 0 || c->patch_k > 31) return snprintf(msg, n, "patch_k must be odd in [1, 31]"), ECO_EINVAL;
-  if (c->n_scalars != 4 && c->n_scalars != 8) return snprintf(msg, n, "n_scalars must be 4 or 8"), ECO_EINVAL;
+  const bool terrain = c->rules == ECO_RULES_TERRAIN;
+  if (terrain ? c->n_scalars != 16 : (c->n_scalars != 4 && c->n_scalars != 8))
+    return snprintf(msg, n, "n_scalars must be 4 or 8 (16 under the terrain rules)"), ECO_EINVAL;
   if (c->hidden != 32 && c->hidden != 64 && c->hidden != 128) return snprintf(msg, n, "hidden must be 32, 64 or 128"), ECO_EINVAL;
-  if (c->rules != ECO_RULES_SIMPLE && c->rules != ECO_RULES_PAPER) return snprintf(msg, n, "bad rules"), ECO_EINVAL;
+  if (c->rules != ECO_RULES_SIMPLE && c->rules != ECO_RULES_PAPER && c->rules != ECO_RULES_TERRAIN)
+    return snprintf(msg, n, "bad rules"), ECO_EINVAL;
   if (c->vision != ECO_VISION_CHANNELS && c->vision != ECO_VISION_RGB) return snprintf(msg, n, "bad vision"), ECO_EINVAL;
   if (c->view != ECO_VIEW_AROUND && c->view != ECO_VIEW_FRONT) return snprintf(msg, n, "bad view"), ECO_EINVAL;
   if (c->view == ECO_VIEW_FRONT && !(c->flags & ECO_ROTATE_OBS))
     return snprintf(msg, n, "the front view needs ECO_ROTATE_OBS"), ECO_EINVAL;
   if (c->rules == ECO_RULES_SIMPLE && c->n_actions != 6 && c->n_actions != 9)
     return snprintf(msg, n, "n_actions must be 6 or 9 under the simple rules"), ECO_EINVAL;
-  if (c->rules == ECO_RULES_PAPER) {
-    if (c->n_actions != PA_N) return snprintf(msg, n, "n_actions must be 7 under the paper rules"), ECO_EINVAL;
+  if (c->rules != ECO_RULES_SIMPLE) {
+    if (c->n_actions != (terrain ? TA_N : PA_N))
+      return snprintf(msg, n, "n_actions must be 7 under the paper rules, 9 under the terrain rules"), ECO_EINVAL;
     if (c->flags & ECO_AUTO_EAT) return snprintf(msg, n, "the paper rules eat only by the eat action"), ECO_EINVAL;
     if (c->hp_max < 1 || c->hp_child < 1 || c->hp_child > c->hp_max || c->attack_damage < 0 ||
         c->heal_rate < 0 || c->heal_cost < 0 || c->age_div < 1 || c->starve_damage < 0 || c->e_act < 0)
@@ -114,7 +118,19 @@ static int validate(const eco_config *c, char *msg, size_t n) {
     return snprintf(msg, n, "bad policy_form"), ECO_EINVAL;
   if (c->policy_form == ECO_POLICY_PAPER && (c->n_hidden < 1 || c->n_hidden > 4))
     return snprintf(msg, n, "n_hidden must be in [1, 4] for the paper form"), ECO_EINVAL;
-  if (3 * c->patch_k * c->patch_k + c->n_scalars < c->hidden)
+  if (terrain) {
+    if (c->vision != ECO_VISION_RGB) return snprintf(msg, n, "the terrain rules need RGB vision"), ECO_EINVAL;
+    if (c->sea_level < 0 || c->sea_level > 1024) return snprintf(msg, n, "sea_level must be in [0, 1024]"), ECO_EINVAL;
+    if (c->w_bite < 1 || c->w_cap < 1 || c->b_bite < 1 || c->b_cap < 1 || c->w_init < 0 || c->w_init > c->w_cap ||
+        c->b_body < 0 || c->b_body > c->b_cap || c->w_metab < 0 || c->w_child < 0 || c->heal_water < 0 ||
+        c->b_child < 0 || c->b_site < 0 || c->photo_q16 < 0 || c->photo_q16 > 65536 || c->res_cap < c->e_food ||
+        !(c->biomass_density >= 0.0f && c->biomass_density <= 1.0f))
+      return snprintf(msg, n, "bad terrain constants"), ECO_EINVAL;
+    if (c->w_child > c->w_cap || c->b_child > c->b_cap)
+      return snprintf(msg, n, "a child's water and biomass must fit its capacities"), ECO_EINVAL;
+  }
+  const int nch = terrain ? 4 : 3;
+  if (nch * c->patch_k * c->patch_k + c->n_scalars < c->hidden)
     return snprintf(msg, n, "observation smaller than the hidden width"), ECO_EINVAL;
   if (c->policy_variant < 0 || c->policy_variant > policy_variant_count())
     return snprintf(msg, n, "policy_variant out of range"), ECO_EINVAL;
@@ -128,6 +144,9 @@ static int validate(const eco_config *c, char *msg, size_t n) {
       return snprintf(msg, n, "env %d: init_alive out of range", e), ECO_EINVAL;
     cells += (long long)L * L;
     slots += c->env_slots[e];
+    // terrain: all water of an environment must fit one int32 cell
+    if (terrain && (long long)L * L * (c->sea_level + 1) + (long long)c->env_slots[e] * c->w_cap > (1ll << 30))
+      return snprintf(msg, n, "env %d: too much water for int32 cells", e), ECO_EINVAL;
   }
   if (cells > (1ll << 30) || slots > (1ll << 28)) return snprintf(msg, n, "too many cells or slots"), ECO_EINVAL;
   return ECO_OK;
@@ -135,10 +154,11 @@ static int validate(const eco_config *c, char *msg, size_t n) {
 
 static Layout make_layout(const eco_config *c) {
   Layout L;
-  L.D = 3 * c->patch_k * c->patch_k + c->n_scalars;
+  L.nch = c->rules == ECO_RULES_TERRAIN ? 4 : 3;
+  L.D = L.nch * c->patch_k * c->patch_k + c->n_scalars;
   L.H = c->hidden;
   L.A = c->n_actions;
-  L.patch = 3 * c->patch_k * c->patch_k;
+  L.patch = L.nch * c->patch_k * c->patch_k;
   L.n_scalars = c->n_scalars;
   if (c->policy_form == ECO_POLICY_PAPER) {
     L.L = c->n_hidden;
@@ -247,6 +267,13 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.dmg = k.take<int32_t>(slots);
   D.res = k.take<int32_t>(cells);
   D.colour = k.take<float4>(slots);
+  D.rock = k.take<int32_t>(cells);
+  D.water = k.take<int32_t>(cells);
+  D.bio = k.take<int32_t>(cells);
+  D.photo = k.take<uint32_t>(cells);
+  D.flow = k.take<uint32_t>(cells);
+  D.a_water = k.take<int32_t>(slots);
+  D.a_bio = k.take<int32_t>(slots);
   return (k.off + 255) & ~(size_t)255;
 }
 
@@ -326,6 +353,21 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
   R.e_child = cfg->e_child;
   R.vision = cfg->vision;
   R.view = cfg->view;
+  R.sea_level = cfg->sea_level;
+  R.w_init = cfg->w_init;
+  R.w_metab = cfg->w_metab;
+  R.w_bite = cfg->w_bite;
+  R.w_cap = cfg->w_cap;
+  R.w_child = cfg->w_child;
+  R.heal_water = cfg->heal_water;
+  R.b_body = cfg->b_body;
+  R.b_child = cfg->b_child;
+  R.b_bite = cfg->b_bite;
+  R.b_cap = cfg->b_cap;
+  R.b_site = cfg->b_site;
+  R.thr_bio = threshold_of(cfg->biomass_density);
+  R.photo_q16 = cfg->photo_q16;
+  R.res_cap = cfg->res_cap;
   h->ws = reinterpret_cast<uint8_t *>(dev_workspace);
   h->ws_bytes = bytes;
   carve(cfg, h->L, h->ws, &h->d, &h->env_dev);
@@ -645,6 +687,11 @@ extern "C" int eco_read_state(eco_handle *h, int32_t env, eco_state_view *out) {
   if (out->hp) CUDA_TRY(h, cudaMemcpyAsync(out->hp, h->d.hp + ed.slot_off, 4 * (size_t)S, cudaMemcpyDeviceToHost, s));
   if (out->age) CUDA_TRY(h, cudaMemcpyAsync(out->age, h->d.age + ed.slot_off, 4 * (size_t)S, cudaMemcpyDeviceToHost, s));
   if (out->res) CUDA_TRY(h, cudaMemcpyAsync(out->res, h->d.res + ed.cell_off, 4 * (size_t)N, cudaMemcpyDeviceToHost, s));
+  if (out->water) CUDA_TRY(h, cudaMemcpyAsync(out->water, h->d.water + ed.cell_off, 4 * (size_t)N, cudaMemcpyDeviceToHost, s));
+  if (out->bio) CUDA_TRY(h, cudaMemcpyAsync(out->bio, h->d.bio + ed.cell_off, 4 * (size_t)N, cudaMemcpyDeviceToHost, s));
+  if (out->photo) CUDA_TRY(h, cudaMemcpyAsync(out->photo, h->d.photo + ed.cell_off, 4 * (size_t)N, cudaMemcpyDeviceToHost, s));
+  if (out->a_water) CUDA_TRY(h, cudaMemcpyAsync(out->a_water, h->d.a_water + ed.slot_off, 4 * (size_t)S, cudaMemcpyDeviceToHost, s));
+  if (out->a_bio) CUDA_TRY(h, cudaMemcpyAsync(out->a_bio, h->d.a_bio + ed.slot_off, 4 * (size_t)S, cudaMemcpyDeviceToHost, s));
   std::vector<float4> colour(out->colour ? S : 0);
   if (out->colour)
     CUDA_TRY(h, cudaMemcpyAsync(colour.data(), h->d.colour + ed.slot_off, sizeof(float4) * (size_t)S,
@@ -693,7 +740,7 @@ extern "C" int eco_write_state(eco_handle *h, int32_t env, const eco_state_view 
   if (cells && !(in->food && in->wall && in->occ)) return fail(h, ECO_EINVAL, "food, wall and occ must be written together");
   const bool where = in->alive || in->x || in->y;
   if (where && !(in->alive && in->x && in->y)) return fail(h, ECO_EINVAL, "alive, x and y must be written together");
-  const bool paper = h->R.rules == RULES_PAPER;
+  const bool paper = h->R.rules != RULES_SIMPLE;
   if (paper && (cells || in->res) && !(cells && in->res))
     return fail(h, ECO_EINVAL, "under the paper rules res is written together with food, wall and occ");
   std::vector<uint8_t> cellf, alive;
@@ -729,6 +776,24 @@ extern "C" int eco_write_state(eco_handle *h, int32_t env, const eco_state_view 
   if (in->birth_step) CUDA_TRY(h, cudaMemcpyAsync(h->d.birth + ed.slot_off, in->birth_step, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
   if (in->hp) CUDA_TRY(h, cudaMemcpyAsync(h->d.hp + ed.slot_off, in->hp, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
   if (in->age) CUDA_TRY(h, cudaMemcpyAsync(h->d.age + ed.slot_off, in->age, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
+  if (h->R.rules == RULES_TERRAIN) {
+    // terrain arrays: counts must be non-negative
+    const int32_t *cellv[2] = {in->water, in->bio};
+    for (int q = 0; q < 2; ++q)
+      if (cellv[q])
+        for (int c = 0; c < N; ++c)
+          if (cellv[q][c] < 0) return fail(h, ECO_EINVAL, "negative water or biomass at cell %d", c);
+    const int32_t *slotv[2] = {in->a_water, in->a_bio};
+    for (int q = 0; q < 2; ++q)
+      if (slotv[q])
+        for (int i = 0; i < S; ++i)
+          if (slotv[q][i] < 0) return fail(h, ECO_EINVAL, "negative carried water or biomass at slot %d", i);
+    if (in->water) CUDA_TRY(h, cudaMemcpyAsync(h->d.water + ed.cell_off, in->water, 4 * (size_t)N, cudaMemcpyHostToDevice, s));
+    if (in->bio) CUDA_TRY(h, cudaMemcpyAsync(h->d.bio + ed.cell_off, in->bio, 4 * (size_t)N, cudaMemcpyHostToDevice, s));
+    if (in->photo) CUDA_TRY(h, cudaMemcpyAsync(h->d.photo + ed.cell_off, in->photo, 4 * (size_t)N, cudaMemcpyHostToDevice, s));
+    if (in->a_water) CUDA_TRY(h, cudaMemcpyAsync(h->d.a_water + ed.slot_off, in->a_water, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
+    if (in->a_bio) CUDA_TRY(h, cudaMemcpyAsync(h->d.a_bio + ed.slot_off, in->a_bio, 4 * (size_t)S, cudaMemcpyHostToDevice, s));
+  }
   std::vector<float4> colour;
   if (in->colour) {
     colour.resize(S);
@@ -750,6 +815,31 @@ extern "C" int eco_write_state(eco_handle *h, int32_t env, const eco_state_view 
   CUDA_TRY(h, launch_recount(h->d, h->R, s));
   CUDA_TRY(h, launch_compact(h->d, s));
   CUDA_TRY(h, cudaStreamSynchronize(s));
+  return ECO_OK;
+}
+
+extern "C" int eco_set_rock(eco_handle *h, int32_t env, const int32_t *rock) {
+  int rc = check_env(h, env);
+  if (rc) return rc;
+  if (h->R.rules != RULES_TERRAIN) return fail(h, ECO_EINVAL, "a rock layer needs the terrain rules");
+  if (!rock) return fail(h, ECO_EINVAL, "null rock");
+  const EnvDesc &ed = h->env_host[env];
+  const int N = ed.side * ed.side;
+  for (int c = 0; c < N; ++c)
+    if (rock[c] < 0 || rock[c] > 65535) return fail(h, ECO_EINVAL, "rock[%d] outside [0, 65535]", c);
+  CUDA_TRY(h, cudaMemcpyAsync(h->d.rock + ed.cell_off, rock, 4 * (size_t)N, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return ECO_OK;
+}
+
+extern "C" int eco_get_rock(eco_handle *h, int32_t env, int32_t *rock) {
+  int rc = check_env(h, env);
+  if (rc) return rc;
+  if (!rock) return fail(h, ECO_EINVAL, "null rock");
+  const EnvDesc &ed = h->env_host[env];
+  CUDA_TRY(h, cudaMemcpyAsync(rock, h->d.rock + ed.cell_off, 4 * (size_t)ed.side * ed.side, cudaMemcpyDeviceToHost,
+                              h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return ECO_OK;
 }
 

@@ -132,7 +132,27 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
       }
     }
     const int a = d.act[slot];
-    if (R.rules == RULES_PAPER) {
+    if (R.rules == RULES_TERRAIN && (a == TA_DRINK || a == TA_EAT_BIO)) {
+      // terrain rules: drink or eat biomass, min(bite, on the cell, room)
+      const int gpos = ed.cell_off + pos;
+      if (a == TA_DRINK) {
+        const int w = d.water[gpos];
+        const int sip = min(min(R.w_bite, w), R.w_cap - d.a_water[slot]);
+        if (sip > 0) {
+          d.water[gpos] = w - sip;
+          d.a_water[slot] += sip;
+          stat_add(d.stats_step, e, ST_DRUNK, sip);
+        }
+      } else {
+        const int b = d.bio[gpos];
+        const int bite = min(min(R.b_bite, b), R.b_cap - d.a_bio[slot]);
+        if (bite > 0) {
+          d.bio[gpos] = b - bite;
+          d.a_bio[slot] += bite;
+          stat_add(d.stats_step, e, ST_BIO_EATEN, bite);
+        }
+      }
+    } else if (R.rules != RULES_SIMPLE) {
       // one bite: min(e_food, energy on the cell, room in the stomach)
       if (a == PA_EAT) {
         const int gpos = ed.cell_off + pos;
@@ -178,7 +198,7 @@ __device__ void ph_attack_claim(const Dev &d, const Rules &R, int g0, int gs) {
       if (R.flags & F_CANCEL_ALL) d.cnt_move[ed.cell_off + tc] = 0u;
     }
     int victim = -1;
-    if (R.rules == RULES_PAPER) {
+    if (R.rules != RULES_SIMPLE) {
       if (d.act[slot] == PA_ATTACK) {
         const int side = ed.side;
         const int pos = d.pos[slot];
@@ -216,7 +236,7 @@ __device__ void ph_attack_claim(const Dev &d, const Rules &R, int g0, int gs) {
 // A8 (part 2): the winning attacker of each victim takes floor(e * num /
 // den) of the victim's post-eat energy (read here, written only later).
 __device__ void ph_attack_gain(const Dev &d, const Rules &R, int g0, int gs) {
-  if (R.rules == RULES_PAPER) return;  // damage is applied in the health phase
+  if (R.rules != RULES_SIMPLE) return;  // damage is applied in the health phase
   const int n = d.counters[CNT_N_ALIVE];
   for (int i = g0; i < n; i += gs) {
     const int slot = d.alive_list[i];
@@ -238,6 +258,10 @@ __device__ void ph_attack_gain(const Dev &d, const Rules &R, int g0, int gs) {
 // Paper rules, one agent: pay the action's cost (starving when it exceeds
 // the energy), take the attack and age damage, heal from energy, and die at
 // HP <= 0, dropping the energy on the cell; survivors age by one step.
+// Terrain rules: also spend w_metab water onto the cell (thirst: what there
+// is, and starve_damage HP), heal only with heal_water water (spent onto the
+// cell too), and drop water and biomass at death.  One agent per cell, so
+// the cell's counters are this agent's to change here.
 __device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int slot) {
   int en = d.energy[slot];
   int hp = d.hp[slot];
@@ -252,22 +276,51 @@ __device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int s
     hp -= R.starve_damage;
     starved = 1;
   }
+  const bool terrain = R.rules == RULES_TERRAIN;
+  const int e = d.env_of[slot];
+  const int gpos = d.env[e].cell_off + d.pos[slot];
+  int aw = terrain ? d.a_water[slot] : 0, spent = 0, thirsty = 0;
+  if (terrain) {
+    spent = R.w_metab;
+    if (aw < spent) {
+      spent = aw;
+      hp -= R.starve_damage;
+      thirsty = 1;
+    }
+    aw -= spent;
+  }
   hp -= d.dmg[slot];
   d.dmg[slot] = 0;
   hp -= age / R.age_div;
-  if (hp > 0 && hp < R.hp_max && R.heal_rate > 0 && en >= R.heal_cost) {
+  if (hp > 0 && hp < R.hp_max && R.heal_rate > 0 && en >= R.heal_cost && (!terrain || aw >= R.heal_water)) {
     hp = min(hp + R.heal_rate, R.hp_max);
     en -= R.heal_cost;
+    if (terrain) {
+      aw -= R.heal_water;
+      spent += R.heal_water;
+    }
     healed = 1;
   }
-  const int e = d.env_of[slot];
+  if (terrain) {
+    int back = spent;  // spent water, and at death everything carried
+    if (hp <= 0) {
+      back += aw;
+      const int ab = d.a_bio[slot];
+      d.bio[gpos] += ab;
+      d.a_bio[slot] = 0;
+      stat_add(d.stats_step, e, ST_DEAD_WATER, aw);
+      stat_add(d.stats_step, e, ST_DEAD_BIO, ab);
+      aw = 0;
+    }
+    d.water[gpos] += back;
+    d.a_water[slot] = aw;
+    stat_add(d.stats_step, e, ST_WATER_SPENT, spent);
+    stat_add(d.stats_step, e, ST_THIRSTY, thirsty);
+  }
   stat_add(d.stats_step, e, ST_METAB_PAID, paid);
   stat_add(d.stats_step, e, ST_STARVED, starved);
   stat_add(d.stats_step, e, ST_HEALS, healed);
   if (hp <= 0) {
-    // one agent per cell, so the cell's energy and flags are this agent's
-    // to change here
-    const int gpos = d.env[e].cell_off + d.pos[slot];
     uint8_t cf = (uint8_t)(d.cellf[gpos] & ~CELL_AGENT);
     if (en > 0) {
       const int r = d.res[gpos];
@@ -297,7 +350,7 @@ __device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs) {
   const int n = d.counters[CNT_N_ALIVE];
   for (int i = g0; i < n; i += gs) {
     const int slot = d.alive_list[i];
-    if (R.rules == RULES_PAPER) {
+    if (R.rules != RULES_SIMPLE) {
       health_paper(d, R, slot);
       continue;
     }
@@ -321,7 +374,8 @@ __device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs) {
 }
 
 // A10 (part 1): agents with e >= e_repro (paper rules: that chose to
-// reproduce) claim the free non-wall cell behind them and join their
+// reproduce; terrain rules: that also carry b_body + b_child biomass and
+// w_child water) claim the free non-wall cell behind them and join their
 // environment's contender list.
 __device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs) {
   const int n = d.counters[CNT_N_ALIVE];
@@ -330,7 +384,9 @@ __device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs) {
     const int slot = d.alive_list[i];
     int bt = -1;
     if (d.alive[slot] && d.energy[slot] >= R.e_repro &&
-        (R.rules != RULES_PAPER || d.act[slot] == PA_REPRODUCE)) {
+        (R.rules == RULES_SIMPLE || d.act[slot] == PA_REPRODUCE) &&
+        (R.rules != RULES_TERRAIN ||
+         (d.a_bio[slot] >= R.b_body + R.b_child && d.a_water[slot] >= R.w_child))) {
       const int e = d.env_of[slot];
       const EnvDesc ed = d.env[e];
       const int c = step_cell(d.pos[slot], (d.facing[slot] + 2) & 3, ed.side);
@@ -367,13 +423,19 @@ struct BirthSmem {
 
 __device__ __forceinline__ void make_child(const Dev &d, const Rules &R, const EnvDesc &ed, int p,
                                            int c, int bt, uint32_t t) {
-  const bool paper = R.rules == RULES_PAPER;
+  const bool paper = R.rules != RULES_SIMPLE;
   const int en = d.energy[p];
   const int ce = paper ? R.e_child : en / 2;
   d.energy[p] = en - ce;
   d.energy[c] = ce;
   d.hp[c] = paper ? R.hp_child : 0;
   d.age[c] = 0;
+  if (R.rules == RULES_TERRAIN) {  // the child's water and body
+    d.a_water[p] -= R.w_child;
+    d.a_water[c] = R.w_child;
+    d.a_bio[p] -= R.b_child;
+    d.a_bio[c] = R.b_child;
+  }
   {
     // colour trait: clamp(parent + sigma * n, 0, 1), n the first three
     // normals of COLOUR at counter (step, parent's local slot, 1, 0)
@@ -691,14 +753,90 @@ __device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs) {
       if (!(cf.z & (CELL_WALL | CELL_FOOD)) && r.z < R.thr_regrow) { cf.z |= CELL_FOOD; mask |= 4; }
       if (!(cf.w & (CELL_WALL | CELL_FOOD)) && r.w < R.thr_regrow) { cf.w |= CELL_FOOD; mask |= 8; }
       grown = __popc(mask);
-      if (grown) {
-        reinterpret_cast<uchar4 *>(d.cellf)[g] = cf;
-        if (R.rules == RULES_PAPER)  // one bite of energy on each regrown cell
-          for (int k = 0; k < 4; ++k)
-            if (mask & (1 << k)) d.res[c0 + k] = R.e_food;
+      if (grown && R.rules != RULES_SIMPLE)  // one bite of energy on each regrown cell
+        for (int k = 0; k < 4; ++k)
+          if (mask & (1 << k)) d.res[c0 + k] = R.e_food;
+    }
+    bool changed = grown != 0;
+    if (R.rules == RULES_TERRAIN) {
+      // energy grows on free biomass: a 2^-16 fixed-point remainder per cell
+      // makes the sum over steps exact; at most res_cap energy per cell
+      uint8_t *cfb = reinterpret_cast<uint8_t *>(&cf);
+      int refilled = 0;
+      long long grew = 0;
+      for (int k = 0; k < 4; ++k) {
+        const int c = c0 + k;
+        const int b = d.bio[c];
+        if ((cfb[k] & CELL_WALL) || b <= 0) continue;
+        const unsigned long long acc = (unsigned long long)d.photo[c] + (unsigned long long)b * (unsigned)R.photo_q16;
+        d.photo[c] = (uint32_t)(acc & 0xFFFFull);
+        const int r = d.res[c];
+        const long long gain = min((long long)(acc >> 16), (long long)R.res_cap - r);
+        if (gain <= 0) continue;
+        if (r == 0) {
+          cfb[k] |= (uint8_t)CELL_FOOD;
+          ++refilled;
+          changed = true;
+        }
+        d.res[c] = r + (int)gain;
+        grew += gain;
+      }
+      stat_add(d.stats_step, e, ST_FOOD_REFILLED, refilled);
+      stat_add(d.stats_step, e, ST_PHOTO, (int)grew);
+    }
+    if (changed) reinterpret_cast<uchar4 *>(d.cellf)[g] = cf;
+    stat_add(d.stats_step, e, ST_REGROWN, grown);
+  }
+}
+
+// Terrain rules, water flow (Sec. 3.2 "Terrain"), part 1: each cell's
+// transfer from the surfaces (rock + water) before the step.  A wet
+// non-wall cell sends min(water, floor(drop / 5)) to its lowest non-wall
+// neighbour (the first of N, E, S, W on ties) when that one lies `drop`
+// below it.  Stored as amount << 2 | direction (amount 0: none); the total
+// water of an environment is below 2^30, so the amount fits.
+__device__ void ph_flow_out(const Dev &d, int g0, int gs) {
+  for (int c = g0; c < d.total_cells; c += gs) {
+    const int w = d.water[c];
+    uint32_t f = 0u;
+    if (w > 0 && !(d.cellf[c] & CELL_WALL)) {
+      const EnvDesc ed = d.env[env_of_cell(d.env, d.n_envs, c)];
+      const int lc = c - ed.cell_off;
+      const long long here = (long long)d.rock[c] + w;
+      long long lowest = 0;
+      int best = -1;
+      for (int dir = 0; dir < 4; ++dir) {
+        const int n = ed.cell_off + step_cell(lc, dir, ed.side);
+        if (d.cellf[n] & CELL_WALL) continue;
+        const long long h = (long long)d.rock[n] + d.water[n];
+        if (best < 0 || h < lowest) {
+          best = dir;
+          lowest = h;
+        }
+      }
+      if (best >= 0 && lowest < here) {
+        const long long amount = min((here - lowest) / 5, (long long)w);
+        f = ((uint32_t)amount << 2) | (uint32_t)best;
       }
     }
-    stat_add(d.stats_step, e, ST_REGROWN, grown);
+    d.flow[c] = f;
+  }
+}
+
+// Part 2: every cell gives its transfer and takes those of the neighbours
+// that point at it (a neighbour in direction dir points back with dir + 2).
+// Only this cell's water is written, from the transfers alone.
+__device__ void ph_flow_in(const Dev &d, int g0, int gs) {
+  for (int c = g0; c < d.total_cells; c += gs) {
+    if (d.cellf[c] & CELL_WALL) continue;
+    const EnvDesc ed = d.env[env_of_cell(d.env, d.n_envs, c)];
+    const int lc = c - ed.cell_off;
+    int w = d.water[c] - (int)(d.flow[c] >> 2);
+    for (int dir = 0; dir < 4; ++dir) {
+      const uint32_t fn = d.flow[ed.cell_off + step_cell(lc, dir, ed.side)];
+      if ((fn >> 2) && (int)(fn & 3u) == ((dir + 2) & 3)) w += (int)(fn >> 2);
+    }
+    d.water[c] = w;
   }
 }
 
@@ -712,7 +850,7 @@ __device__ void ph_finish(const Dev &d, const Rules &R) {
     long long as = 0;
     for (int a = 0; a < 16; ++a) as += st[ST_ACT0 + a];
     st[ST_AGENT_STEPS] = as;
-    st[ST_ATTACKS] = st[ST_ACT0 + (R.rules == RULES_PAPER ? PA_ATTACK : ACT_ATTACK)];
+    st[ST_ATTACKS] = st[ST_ACT0 + (R.rules != RULES_SIMPLE ? PA_ATTACK : ACT_ATTACK)];
   }
   __syncthreads();
   for (int i = threadIdx.x; i < d.n_envs * N_ST; i += blockDim.x) {
@@ -726,18 +864,25 @@ __device__ void ph_finish(const Dev &d, const Rules &R) {
     } else if (k == ST_ALIVE) {
       v = tot[k] + st[ST_BIRTHS] - st[ST_DEATHS];
     } else if (k == ST_FOOD_TOTAL) {
-      v = R.rules == RULES_PAPER ? tot[k] + st[ST_REGROWN] - st[ST_FOOD_EMPTIED] + st[ST_FOOD_REFILLED]
+      v = R.rules != RULES_SIMPLE ? tot[k] + st[ST_REGROWN] - st[ST_FOOD_EMPTIED] + st[ST_FOOD_REFILLED]
                                  : tot[k] + st[ST_REGROWN] - st[ST_EATEN];
     } else if (k == ST_ENERGY_TOTAL) {
-      v = R.rules == RULES_PAPER
+      v = R.rules != RULES_SIMPLE
               ? tot[k] + st[ST_EATEN_ENERGY] - st[ST_METAB_PAID] - (long long)R.heal_cost * st[ST_HEALS] -
                     st[ST_DEAD_ENERGY]
               : tot[k] + (long long)R.e_food * st[ST_EATEN] - (long long)R.e_metab * st[ST_AGENT_STEPS] -
                     st[ST_DEAD_ENERGY];
     } else if (k == ST_RES_TOTAL) {
-      v = R.rules == RULES_PAPER
-              ? tot[k] + (long long)R.e_food * st[ST_REGROWN] - st[ST_EATEN_ENERGY] + st[ST_DEAD_ENERGY]
-              : 0;
+      v = R.rules != RULES_SIMPLE ? tot[k] + (long long)R.e_food * st[ST_REGROWN] - st[ST_EATEN_ENERGY] +
+                                        st[ST_DEAD_ENERGY] + st[ST_PHOTO]
+                                  : 0;
+    } else if (k == ST_WATER_CELLS || k == ST_WATER_AGENTS) {
+      // the flow moves water between cells only
+      const long long to_cells = st[ST_WATER_SPENT] + st[ST_DEAD_WATER] - st[ST_DRUNK];
+      v = tot[k] + (k == ST_WATER_CELLS ? to_cells : -to_cells);
+    } else if (k == ST_BIO_CELLS || k == ST_BIO_AGENTS) {
+      const long long to_cells = st[ST_DEAD_BIO] - st[ST_BIO_EATEN];
+      v = tot[k] + (k == ST_BIO_CELLS ? to_cells : -to_cells);
     } else {
       last[k] = st[k];
       tot[k] += st[k];
@@ -783,6 +928,8 @@ __global__ void __launch_bounds__(256) k_mutate(Dev d, Layout L, Rules R) {
   ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale);
 }
 __global__ void k_regrow(Dev d, Rules R) { ph_regrow(d, R, GRID_ARGS); }
+__global__ void k_flow_out(Dev d) { ph_flow_out(d, GRID_ARGS); }
+__global__ void k_flow_in(Dev d) { ph_flow_in(d, GRID_ARGS); }
 __global__ void k_finish(Dev d, Rules R) { ph_finish(d, R); }
 
 // ---------------------------------------------------------------------------
@@ -847,8 +994,10 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   if (!grid_sync(d, nb, &s_flag)) return;
   ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale);
   ph_regrow(d, R, g0, gs);
+  if (R.rules == RULES_TERRAIN) ph_flow_out(d, g0, gs);
   ph_compact_count(d, blockIdx.x, gridDim.x, S.sh);
   if (!grid_sync(d, nb, &s_flag)) return;
+  if (R.rules == RULES_TERRAIN) ph_flow_in(d, g0, gs);
   ph_compact_scatter(d, blockIdx.x, gridDim.x, S.sh);
   if (blockIdx.x == gridDim.x - 1) ph_finish(d, R);
 }
@@ -909,6 +1058,11 @@ cudaError_t launch_env_phases(const Dev &d, const Layout &L, const Rules &R, con
   k_birth_assign<<<d.n_envs, 1024, 0, s>>>(d, R);
   k_mutate<<<g.birth_blocks, 256, msmem, s>>>(d, L, R);
   k_regrow<<<g.cell_blocks, T, 0, s>>>(d, R);
+  if (R.rules == RULES_TERRAIN) {
+    const int fb = grid_for(d.total_cells, T, g.sms * 8);
+    k_flow_out<<<fb, T, 0, s>>>(d);
+    k_flow_in<<<fb, T, 0, s>>>(d);
+  }
   k_finish<<<1, 1024, 0, s>>>(d, R);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -32,8 +32,21 @@ __global__ void k_init_cells(Dev d, Rules R) {
     const U4 rf = philox((uint32_t)(lc >> 2), 0u, 0u, 0u, ed.seed, S_FOOD_INIT);
     const bool food = !wall && word_of(rf, lc & 3) < R.thr_food;
     d.cellf[c] = (uint8_t)((wall ? CELL_WALL : 0u) | (food ? CELL_FOOD : 0u));
-    d.res[c] = (R.rules == RULES_PAPER && food) ? R.e_food : 0;
+    d.res[c] = (R.rules != RULES_SIMPLE && food) ? R.e_food : 0;
     d.occ[c] = -1;
+    // terrain rules: water fills the cells whose rock lies below sea level;
+    // a Bernoulli(biomass_density) site (stream BIOMASS) holds b_site
+    int water = 0, bio = 0;
+    if (R.rules == RULES_TERRAIN && !wall) {
+      const int rk = d.rock[c];
+      if (rk < R.sea_level) water = R.sea_level - rk;
+      const U4 rb = philox((uint32_t)(lc >> 2), 0u, 0u, 0u, ed.seed, S_BIOMASS);
+      if (word_of(rb, lc & 3) < R.thr_bio) bio = R.b_site;
+    }
+    d.water[c] = water;
+    d.bio[c] = bio;
+    d.photo[c] = 0u;
+    d.flow[c] = 0u;
     d.claim_move[c] = 0ull;
     d.cnt_move[c] = 0u;
     d.claim_birth[c] = 0ull;
@@ -65,7 +78,9 @@ __global__ void k_init_agents(Dev d, Rules R) {
     d.tgt[s] = -1;
     d.gain[s] = 0;
     d.claim_att[s] = 0ull;
-    d.hp[s] = (founder && R.rules == RULES_PAPER) ? R.hp_max : 0;
+    d.hp[s] = (founder && R.rules != RULES_SIMPLE) ? R.hp_max : 0;
+    d.a_water[s] = (founder && R.rules == RULES_TERRAIN) ? R.w_init : 0;
+    d.a_bio[s] = (founder && R.rules == RULES_TERRAIN) ? R.b_body : 0;
     d.age[s] = 0;
     d.dmg[s] = 0;
     // colour trait (Sec. 3.3): three uniforms of COLOUR at counter (slot, 0, 0, 0)
@@ -268,22 +283,33 @@ __global__ void k_requant_fp8(Dev d, Layout L, int slot0, int n) {
 }
 
 // Initial statistics: alive = K, food count, energy = K * e_init, step 0;
-// paper rules: energy on cells = food count * e_food.
+// paper rules: energy on cells = food count * e_food; terrain rules: water
+// and biomass on cells (summed) and carried (K * w_init, K * b_body).
 __global__ void __launch_bounds__(1024) k_init_stats(Dev d, Rules R) {
-  __shared__ int sh[33];
+  __shared__ unsigned long long acc;
   const int e = blockIdx.x;
   const EnvDesc ed = d.env[e];
   const int n = ed.side * ed.side;
-  int cnt = 0;
-  for (int c = threadIdx.x; c < n; c += blockDim.x) cnt += (d.cellf[ed.cell_off + c] & CELL_FOOD) ? 1 : 0;
-  int total;
-  block_exclusive_scan(cnt, &total, sh);
+  long long cnt = 0, water = 0, bio = 0;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    cnt += (d.cellf[ed.cell_off + c] & CELL_FOOD) ? 1 : 0;
+    water += d.water[ed.cell_off + c];
+    bio += d.bio[ed.cell_off + c];
+  }
+  const long long total = block_sum_ll(cnt, &acc);
+  const long long wt = block_sum_ll(water, &acc);
+  const long long bt = block_sum_ll(bio, &acc);
+  const bool terrain = R.rules == RULES_TERRAIN;
   for (int k = threadIdx.x; k < N_ST; k += blockDim.x) {
     long long v = 0;
     if (k == ST_ALIVE) v = ed.init_alive;
     else if (k == ST_FOOD_TOTAL) v = total;
     else if (k == ST_ENERGY_TOTAL) v = (long long)ed.init_alive * R.e_init;
-    else if (k == ST_RES_TOTAL && R.rules == RULES_PAPER) v = (long long)total * R.e_food;
+    else if (k == ST_RES_TOTAL && R.rules != RULES_SIMPLE) v = total * R.e_food;
+    else if (k == ST_WATER_CELLS && terrain) v = wt;
+    else if (k == ST_BIO_CELLS && terrain) v = bt;
+    else if (k == ST_WATER_AGENTS && terrain) v = (long long)ed.init_alive * R.w_init;
+    else if (k == ST_BIO_AGENTS && terrain) v = (long long)ed.init_alive * R.b_body;
     d.stats_total[e * N_ST + k] = v;
     d.stats_last[e * N_ST + k] = v;
     d.stats_step[e * N_ST + k] = 0;
@@ -313,18 +339,25 @@ __global__ void __launch_bounds__(1024) k_recount(Dev d, Rules R) {
   const int e = blockIdx.x;
   const EnvDesc ed = d.env[e];
   const int n = ed.side * ed.side;
-  long long food = 0, alive = 0, energy = 0, res = 0;
+  long long food = 0, alive = 0, energy = 0, res = 0, wc = 0, bc = 0, wa = 0, ba = 0;
   for (int c = threadIdx.x; c < n; c += blockDim.x) {
     food += (d.cellf[ed.cell_off + c] & CELL_FOOD) ? 1 : 0;
     res += d.res[ed.cell_off + c];
+    wc += d.water[ed.cell_off + c];
+    bc += d.bio[ed.cell_off + c];
   }
   for (int s = threadIdx.x; s < ed.n_slots; s += blockDim.x) {
     const int g = ed.slot_off + s;
     if (d.alive[g]) {
       ++alive;
       energy += d.energy[g];
+      wa += d.a_water[g];
+      ba += d.a_bio[g];
     }
   }
+  const bool terrain = R.rules == RULES_TERRAIN;
+  const long long wct = block_sum_ll(wc, &acc), bct = block_sum_ll(bc, &acc);
+  const long long wat = block_sum_ll(wa, &acc), bat = block_sum_ll(ba, &acc);
   const long long ft = block_sum_ll(food, &acc);
   const long long at = block_sum_ll(alive, &acc);
   const long long et = block_sum_ll(energy, &acc);
@@ -335,7 +368,11 @@ __global__ void __launch_bounds__(1024) k_recount(Dev d, Rules R) {
     tot[ST_ALIVE] = last[ST_ALIVE] = at;
     tot[ST_FOOD_TOTAL] = last[ST_FOOD_TOTAL] = ft;
     tot[ST_ENERGY_TOTAL] = last[ST_ENERGY_TOTAL] = et;
-    tot[ST_RES_TOTAL] = last[ST_RES_TOTAL] = R.rules == RULES_PAPER ? rt : 0;
+    tot[ST_RES_TOTAL] = last[ST_RES_TOTAL] = R.rules != RULES_SIMPLE ? rt : 0;
+    tot[ST_WATER_CELLS] = last[ST_WATER_CELLS] = terrain ? wct : 0;
+    tot[ST_BIO_CELLS] = last[ST_BIO_CELLS] = terrain ? bct : 0;
+    tot[ST_WATER_AGENTS] = last[ST_WATER_AGENTS] = terrain ? wat : 0;
+    tot[ST_BIO_AGENTS] = last[ST_BIO_AGENTS] = terrain ? bat : 0;
     tot[ST_STEP] = last[ST_STEP] = t;
   }
 }

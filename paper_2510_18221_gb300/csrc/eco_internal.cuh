@@ -12,6 +12,8 @@
 //   per cell, paper rules: res i32 (energy lying on the cell; the food bit
 //     of cellf is res > 0);
 //   per slot: colour f32x4 (the colour trait, RGB + padding);
+//   terrain rules: per cell rock, water, bio, flow i32 and photo u32; per
+//     slot a_water, a_bio i32;
 //   weights: FP32 masters [slot][mstride] and, for BF16/FP8, the streamed
 //     copy [slot][stride], both in the kernel's tiled block layout below.
 //
@@ -53,6 +55,7 @@ enum : uint32_t {
   S_MUTATE = 10,
   S_REGROW = 11,
   S_COLOUR = 12,
+  S_BIOMASS = 13,
 };
 
 enum : int {
@@ -84,11 +87,15 @@ enum : int {
   PA_EAT = 5,
   PA_REPRODUCE = 6,
   PA_N = 7,
+  TA_DRINK = 7,      // terrain rules
+  TA_EAT_BIO = 8,
+  TA_N = 9,
 };
 
 enum : int {
   RULES_SIMPLE = 0,
   RULES_PAPER = 1,
+  RULES_TERRAIN = 2,  // the paper rules plus rock, water and biomass
 };
 
 enum : int {
@@ -132,6 +139,17 @@ enum : int {
   ST_DAMAGE,
   ST_FOOD_EMPTIED,
   ST_FOOD_REFILLED,
+  ST_WATER_CELLS,
+  ST_WATER_AGENTS,
+  ST_BIO_CELLS,
+  ST_BIO_AGENTS,
+  ST_DRUNK,
+  ST_WATER_SPENT,
+  ST_THIRSTY,
+  ST_BIO_EATEN,
+  ST_PHOTO,
+  ST_DEAD_WATER,
+  ST_DEAD_BIO,
   N_ST
 };
 
@@ -161,8 +179,9 @@ struct Layout {
   int relu;           // 1: ReLU, 0: tanh
   int out_bias;       // head has a bias
   int temp;           // a log-temperature parameter follows the biases
-  int patch;          // 3 k^2: inputs of the vision sensor
-  int n_scalars;      // 4 or 8
+  int patch;          // nch k^2: inputs of the vision sensor
+  int nch;            // channels per patch cell: 3, or 4 under the terrain rules
+  int n_scalars;      // 4, 8 or 16
   int nW, nB;         // weight elements, bias (+ tau) elements
   int es;             // bytes per streamed weight element
   int64_t stride;     // bytes per slot, streamed copy
@@ -229,6 +248,11 @@ struct Rules {
   int hp_max, hp_child, attack_damage, heal_rate, heal_cost, age_div, starve_damage;
   int e_act, e_cap, e_child;
   int vision, view;  // VISION_*, VIEW_*
+  // terrain rules
+  int sea_level, w_init, w_metab, w_bite, w_cap, w_child, heal_water;
+  int b_body, b_child, b_bite, b_cap, b_site;
+  uint32_t thr_bio;
+  int photo_q16, res_cap;
 };
 
 // Device pointers (all inside the caller's workspace).
@@ -277,6 +301,14 @@ struct Dev {
   int32_t *dmg;            // [total_slots] paper rules: attack damage this step
   int32_t *res;            // [total_cells] paper rules: energy on the cell
   float4 *colour;          // [total_slots] colour trait (x, y, z = RGB; w = 0)
+  // terrain rules
+  int32_t *rock;           // [total_cells] rock height (caller's input)
+  int32_t *water;          // [total_cells] water on the cell
+  int32_t *bio;            // [total_cells] free biomass
+  uint32_t *photo;         // [total_cells] photosynthesis remainder (2^-16)
+  uint32_t *flow;          // [total_cells] this step's transfer: amount << 2 | direction
+  int32_t *a_water;        // [total_slots] water carried
+  int32_t *a_bio;          // [total_slots] biomass carried
 };
 
 enum : int {

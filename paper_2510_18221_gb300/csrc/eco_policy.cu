@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
       flush();
       e_cur = env;
     }
-    // -- observation: k x k x 3 patch (row, column, channel), then scalars.
+    // -- observation: k x k x nch patch (row, column, channel), then scalars.
     // Its locals end with this scope so that they do not stay live (in
     // registers) through the weight stream below.
     {
@@ -240,6 +240,9 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
     // rows run from far ahead (top) to behind (Around) or to the agent's
     // own row (Front); columns from the agent's left to its right
     const int fw0 = R.view == VIEW_FRONT ? k - 1 : RR;
+    const int nch = L.nch;
+    const bool terrain = R.rules == RULES_TERRAIN;
+    const int rock0 = terrain ? d.rock[ed.cell_off + pos] : 0;
     for (int c = lane; c < kk; c += 32) {
       const int r = c / k, col = c - r * k;
       int dx, dy;
@@ -252,17 +255,29 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
         dy = r - RR;
       }
       const int cx = wrapi(px + dx, side), cy = wrapi(py + dy, side);
+      const int gc = ed.cell_off + cy * side + cx;
       const uint32_t cf = cellf[cy * side + cx];
       if (R.vision == VISION_RGB) {
         // rendered colours: the occupant's colour trait, else grey wall,
-        // green food, black
+        // else green food (terrain: the cell's biomass, energy and water)
         float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (cf & CELL_AGENT) v = d.colour[d.occ[ed.cell_off + cy * side + cx]];
-        else if (cf & CELL_WALL) v = make_float4(0.5f, 0.5f, 0.5f, 0.0f);
-        else if (cf & CELL_FOOD) v.y = 1.0f;
-        xs[3 * c + 0] = v.x;
-        xs[3 * c + 1] = v.y;
-        xs[3 * c + 2] = v.z;
+        if (cf & CELL_AGENT) {
+          v = d.colour[d.occ[gc]];
+        } else if (cf & CELL_WALL) {
+          v = make_float4(0.5f, 0.5f, 0.5f, 0.0f);
+        } else if (terrain) {
+          const float b = (float)d.bio[gc], r = (float)d.res[gc], w = (float)d.water[gc];
+          v = make_float4(b / (b + (float)R.b_bite), r / (r + (float)R.e_food), w / (w + (float)R.w_bite), 0.0f);
+        } else if (cf & CELL_FOOD) {
+          v.y = 1.0f;
+        }
+        xs[nch * c + 0] = v.x;
+        xs[nch * c + 1] = v.y;
+        xs[nch * c + 2] = v.z;
+        if (terrain) {  // elevation: rock difference d as d / (|d| + 16)
+          const float dz = (float)(d.rock[gc] - rock0);
+          xs[nch * c + 3] = dz / (fabsf(dz) + 16.0f);
+        }
       } else {
         xs[3 * c + 0] = (cf & CELL_FOOD) ? 1.0f : 0.0f;
         xs[3 * c + 1] = (cf & CELL_AGENT) ? 1.0f : 0.0f;
@@ -278,7 +293,7 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
         v = (float)d.energy[slot] / (float)R.e_repro;
       else if (R.n_scalars >= 8 && lane == 1 + f)
         v = 1.0f;
-      if (R.rules == RULES_PAPER) {
+      if (R.rules != RULES_SIMPLE) {
         const int extra = lane - (R.n_scalars >= 8 ? 5 : 1);
         if (extra == 0) {
           v = (float)d.hp[slot] / (float)R.hp_max;
@@ -290,7 +305,20 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
           v = r / (r + (float)R.e_food);
         }
       }
-      xs[3 * kk + lane] = v;
+      if (terrain) {  // carried water and biomass; the cell's water and biomass
+        if (lane == 8) {
+          v = (float)d.a_water[slot] / (float)R.w_cap;
+        } else if (lane == 9) {
+          v = (float)d.a_bio[slot] / (float)R.b_cap;
+        } else if (lane == 10) {
+          const float w = (float)d.water[ed.cell_off + pos];
+          v = w / (w + (float)R.w_bite);
+        } else if (lane == 11) {
+          const float b = (float)d.bio[ed.cell_off + pos];
+          v = b / (b + (float)R.b_bite);
+        }
+      }
+      xs[nch * kk + lane] = v;
     }
     }
     __syncwarp();
@@ -374,7 +402,7 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
         const uint8_t *cellf = d.cellf + ed.cell_off;
         int nf = f, tc = -1;
         bool move = false;
-        if (R.rules == RULES_PAPER) {
+        if (R.rules != RULES_SIMPLE) {
           // rotate clockwise / counter-clockwise, or one cell forward
           if (best == PA_CW) nf = (f + 1) & 3;
           else if (best == PA_CCW) nf = (f + 3) & 3;

@@ -21,15 +21,17 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libeco.so")
 
-ECO_ABI_VERSION = 3
+ECO_ABI_VERSION = 4
 ECO_OK, ECO_EINVAL, ECO_ENOMEM, ECO_ECUDA, ECO_ETIMEOUT, ECO_EABI = 0, -1, -2, -3, -4, -5
 ECO_FP32, ECO_BF16, ECO_FP8_E4M3 = 0, 1, 2
 ECO_AUTO_EAT, ECO_ROTATE_OBS, ECO_CANCEL_ALL, ECO_GREEDY = 1, 2, 4, 8
 PRECISIONS = {"fp32": ECO_FP32, "bf16": ECO_BF16, "fp8": ECO_FP8_E4M3}
 ECO_POLICY_PLAIN, ECO_POLICY_PAPER = 0, 1
 POLICY_FORMS = {"plain": ECO_POLICY_PLAIN, "paper": ECO_POLICY_PAPER}
-ECO_RULES_SIMPLE, ECO_RULES_PAPER = 0, 1
-RULES = {"simple": ECO_RULES_SIMPLE, "paper": ECO_RULES_PAPER}
+ECO_RULES_SIMPLE, ECO_RULES_PAPER, ECO_RULES_TERRAIN = 0, 1, 2
+RULES = {"simple": ECO_RULES_SIMPLE, "paper": ECO_RULES_PAPER, "terrain": ECO_RULES_TERRAIN}
+TERRAIN_FIELDS = ("sea_level", "w_init", "w_metab", "w_bite", "w_cap", "w_child", "heal_water",
+                  "b_body", "b_child", "b_bite", "b_cap", "b_site")
 VISIONS = {"channels": 0, "rgb": 1}
 VIEWS = {"around": 0, "front": 1}
 PAPER_RULE_FIELDS = ("hp_max", "hp_child", "attack_damage", "heal_rate", "heal_cost",
@@ -42,7 +44,9 @@ STAT_NAMES = (["step", "agent_steps"] + ["act%d" % i for i in range(16)] +
                "energy_transferred", "deaths", "dead_energy", "births", "failed_births",
                "regrown", "alive", "food_total", "energy_total",
                "res_total", "eaten_energy", "metab_paid", "heals", "starved", "damage",
-               "food_emptied", "food_refilled"])
+               "food_emptied", "food_refilled",
+               "water_cells", "water_agents", "bio_cells", "bio_agents", "drunk", "water_spent",
+               "thirsty", "bio_eaten", "photo", "dead_water", "dead_bio"])
 ECO_N_STATS = len(STAT_NAMES)
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -67,7 +71,10 @@ class eco_config(ctypes.Structure):
         ("policy_form", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
         ("rules", ctypes.c_int32),
     ] + [(k, ctypes.c_int32) for k in PAPER_RULE_FIELDS] + [
-        ("vision", ctypes.c_int32), ("view", ctypes.c_int32)]
+        ("vision", ctypes.c_int32), ("view", ctypes.c_int32)] + [
+        (k, ctypes.c_int32) for k in TERRAIN_FIELDS] + [
+        ("biomass_density", ctypes.c_float), ("photo_q16", ctypes.c_int32),
+        ("res_cap", ctypes.c_int32)]
 
 
 class eco_stats(ctypes.Structure):
@@ -77,7 +84,8 @@ class eco_stats(ctypes.Structure):
 class eco_state_view(ctypes.Structure):
     _fields_ = [(n, _vp) for n in ("food", "wall", "occ", "alive", "x", "y", "facing",
                                    "energy", "parent", "birth_step", "step", "hp", "age",
-                                   "res", "colour")]
+                                   "res", "colour", "water", "bio", "photo", "a_water",
+                                   "a_bio")]
 
 
 _lib = None
@@ -109,6 +117,8 @@ def lib() -> ctypes.CDLL:
         L.eco_read_stats.argtypes = [H, _vp, _vp, ctypes.c_int32]
         L.eco_read_state.argtypes = [H, ctypes.c_int32, ctypes.POINTER(eco_state_view)]
         L.eco_write_state.argtypes = [H, ctypes.c_int32, ctypes.POINTER(eco_state_view)]
+        L.eco_set_rock.argtypes = [H, ctypes.c_int32, _vp]
+        L.eco_get_rock.argtypes = [H, ctypes.c_int32, _vp]
         L.eco_read_params.argtypes = [H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp]
         L.eco_write_params.argtypes = [H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp]
         L.eco_read_streamed.argtypes = [H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
@@ -238,7 +248,8 @@ def eco_move_claims_noalloc(side: int, n_agents: int, pos: int, act: int, facing
 _SHARED = ("patch_k", "n_scalars", "hidden", "n_actions", "precision", "flags", "sigma",
            "food_density", "regrow_p", "wall_density", "e_init", "e_metab", "e_food",
            "e_repro", "attack_num", "attack_den", "policy_form", "n_hidden",
-           "rules", "vision", "view") + PAPER_RULE_FIELDS
+           "rules", "vision", "view", "biomass_density", "photo_q16",
+           "res_cap") + PAPER_RULE_FIELDS + TERRAIN_FIELDS
 
 
 def make_config(envs: Sequence[dict], policy_variant: int = 0, launch_mode: int = 0):
@@ -270,6 +281,9 @@ def make_config(envs: Sequence[dict], policy_variant: int = 0, launch_mode: int 
         policy_form=POLICY_FORMS[w0.get("policy_form", "plain")], n_hidden=w0.get("n_hidden", 1),
         rules=RULES[w0.get("rules", "simple")],
         vision=VISIONS[w0.get("vision", "channels")], view=VIEWS[w0.get("view", "around")],
+        biomass_density=float(w0.get("biomass_density", 0.0)),
+        photo_q16=int(w0.get("photo_q16", 0)), res_cap=int(w0.get("res_cap", 0)),
+        **{k: int(w0.get(k, 0)) for k in TERRAIN_FIELDS},
         **{k: int(w0.get(k, 0)) for k in PAPER_RULE_FIELDS})
     return cfg, (side, slots, alive, seed)
 
@@ -294,6 +308,9 @@ class Env:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.h = eco_create(self.cfg, aligned, nbytes, self.stream.cuda_stream)
         self.workspace_bytes = nbytes
+        for e, w in enumerate(self.envs):   # terrain rules: the rock layers
+            if w.get("rock") is not None:
+                self.set_rock(e, w["rock"])
 
     # -- lifecycle ---------------------------------------------------------
     def close(self) -> None:
@@ -349,7 +366,9 @@ class Env:
                "parent": np.zeros(S, np.int32), "birth_step": np.zeros(S, np.int32),
                "step": np.zeros(1, np.int64), "hp": np.zeros(S, np.int32),
                "age": np.zeros(S, np.int32), "res": np.zeros(N, np.int32),
-               "colour": np.zeros((S, 3), np.float32)}
+               "colour": np.zeros((S, 3), np.float32), "water": np.zeros(N, np.int32),
+               "bio": np.zeros(N, np.int32), "photo": np.zeros(N, np.uint32),
+               "a_water": np.zeros(S, np.int32), "a_bio": np.zeros(S, np.int32)}
         v = eco_state_view(**{k: _p(a) for k, a in out.items()})
         _check(lib().eco_read_state(self.h, int(env), ctypes.byref(v)), self.h)
         return out
@@ -364,12 +383,26 @@ class Env:
                       "x": np.int32, "y": np.int32, "facing": np.uint8, "energy": np.int32,
                       "parent": np.int32, "birth_step": np.int32, "step": np.int64,
                       "hp": np.int32, "age": np.int32, "res": np.int32,
-                      "colour": np.float32}[name]
+                      "colour": np.float32, "water": np.int32, "bio": np.int32,
+                      "photo": np.uint32, "a_water": np.int32, "a_bio": np.int32}[name]
                 a = np.ascontiguousarray(arrays[name], dtype=dt)
                 keep[name] = a
                 kw[name] = _p(a)
         v = eco_state_view(**kw)
         _check(lib().eco_write_state(self.h, int(env), ctypes.byref(v)), self.h)
+
+    def set_rock(self, env: int, rock) -> None:
+        side = self.envs[env]["side"]
+        rock = np.ascontiguousarray(rock, np.int32).ravel()
+        if rock.size != side * side:
+            raise ValueError("rock must hold side * side heights")
+        _check(lib().eco_set_rock(self.h, int(env), _p(rock)), self.h)
+
+    def get_rock(self, env: int = 0) -> np.ndarray:
+        side = self.envs[env]["side"]
+        out = np.zeros(side * side, np.int32)
+        _check(lib().eco_get_rock(self.h, int(env), _p(out)), self.h)
+        return out
 
     def read_params(self, env: int = 0, slot0: int = 0, n: int | None = None) -> np.ndarray:
         if n is None:

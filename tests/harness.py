@@ -25,7 +25,7 @@ import numpy as np
 import oracle
 
 STATE_KEYS = ("food", "wall", "occ", "alive", "x", "y", "facing", "energy", "parent",
-              "birth_step", "hp", "age", "res")
+              "birth_step", "hp", "age", "res", "water", "bio", "photo", "a_water", "a_bio")
 LOGIT_RTOL = 1e-5
 GAP_TOL = 1e-3
 PARAM_RTOL = 2.0 ** -19
@@ -36,7 +36,9 @@ STEP_STATS = (["agent_steps"] + ["act%d" % i for i in range(16)] +
                "energy_transferred", "deaths", "dead_energy", "births", "failed_births",
                "regrown", "alive", "food_total", "energy_total",
                "res_total", "eaten_energy", "metab_paid", "heals", "starved", "damage",
-               "food_emptied", "food_refilled"])
+               "food_emptied", "food_refilled",
+               "water_cells", "water_agents", "bio_cells", "bio_agents", "drunk", "water_spent",
+               "thirsty", "bio_eaten", "photo", "dead_water", "dead_bio"])
 
 
 def runs(slots):

@@ -138,3 +138,11 @@ def test_ecology_workload_lockstep():
     rep = _lockstep(workloads.get("ecology"), 3, sample=256)
     assert rep["steps"] == 3
     print("ecology paper-scale lock-step:", rep)
+
+
+def test_terrain_workload_lockstep():
+    """The terrain rules at paper scale (1024x1024 beach, 65,536 slots,
+    50,000 founders, 500-64-64-64-9 BF16, water flow over 1M cells)."""
+    rep = _lockstep(workloads.get("terrain"), 3, sample=256)
+    assert rep["steps"] == 3
+    print("terrain paper-scale lock-step:", rep)

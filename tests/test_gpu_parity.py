@@ -348,3 +348,72 @@ def test_vision_ranges(k, hidden, view):
     w = _ecology(64, 600, 500, patch_k=k, hidden=hidden, view=view, precision="fp8")
     rep = _run(w, 10)
     assert rep["steps"] == 10
+
+
+def _terrain(side, slots, k, **kw):
+    """The terrain rules (rock, flowing water, biomass, photosynthesis) with
+    the paper form, on a reduced world; weak attacks, little water at birth
+    and a low reproduction threshold so that births, thirst, drinking,
+    eating biomass, photosynthesis and deaths all happen within a short run."""
+    over = dict(e_repro=50, e_child=25, e_init=80, b_child=5, b_bite=10, w_init=12, w_child=5,
+                attack_damage=10)
+    over.update(kw)
+    return workloads.scaled("terrain", side, slots, k, **over)
+
+
+@pytest.mark.parametrize("preset,prec", [("beach", "bf16"), ("island", "fp8"), ("lake", "fp32"),
+                                         ("isthmus", "bf16"), ("channel", "fp8"), ("ocean", "bf16")])
+def test_terrain_lockstep(preset, prec):
+    """Sec. 3.2 "Terrain", "Resources and Agent Health"; App. F.2."""
+    rep, tot = _run_totals(_terrain(64, 1200, 800, terrain=preset, precision=prec), 25)
+    assert rep["births"] > 5
+    for k in ("deaths", "drunk", "bio_eaten", "photo", "thirsty", "heals", "dead_water", "dead_bio"):
+        assert tot[k] > 0, k
+
+
+@pytest.mark.parametrize("over", [
+    dict(policy_form="plain", n_hidden=1, patch_k=5, hidden=32),
+    dict(wall_density=0.08, flags=("rotate_obs", "cancel_all")),
+    dict(view="front", heal_water=2, w_metab=2, photo_q16=6553),
+])
+def test_terrain_variants(over):
+    rep, tot = _run_totals(_terrain(48, 900, 600, **over), 15)
+    assert rep["steps"] == 15 and tot["deaths"] > 0
+
+
+def test_terrain_launch_forms_bit_identical():
+    from paper_2510_18221_gb300 import eco
+    w = _terrain(128, 4096, 3000, terrain="island", precision="fp8", wall_density=0.03)
+    a, b = eco.Env(w, launch_mode=0), eco.Env(w, launch_mode=1)
+    a.reset()
+    b.reset()
+    for t in range(25):
+        a.step(1)
+        b.step(1)
+        sa, sb = a.read_state(0), b.read_state(0)
+        for k in harness.STATE_KEYS:
+            assert np.array_equal(sa[k], sb[k]), (t, k)
+        assert a.stats()[0] == b.stats()[0]
+    assert a.stats()[0]["births"] > 0
+    a.close()
+    b.close()
+
+
+def test_terrain_rock_and_state_roundtrip():
+    from paper_2510_18221_gb300 import eco
+    w = _terrain(32, 64, 40, terrain="lake")
+    env = eco.Env(w)
+    assert np.array_equal(env.get_rock(0), w["rock"])
+    orc = oracle.Oracle(w)
+    orc.reset()
+    for _ in range(4):
+        orc.step_once()
+    env.reset()
+    env.write_state(0, orc.arrays())
+    gs = env.read_state(0)
+    harness.compare_state(gs, orc, "roundtrip")
+    st = env.stats()[0]
+    assert st["water_cells"] == int(orc.water.sum())
+    assert st["water_agents"] == int(orc.a_water[orc.alive == 1].sum())
+    assert st["bio_cells"] == int(orc.bio.sum())
+    env.close()
