@@ -41,6 +41,12 @@ UNIT = "agent-steps/s"
 KERNELS_PER_STEP = {0: 2, 1: 12}
 
 
+def kernels_per_step(launch_mode, rules):
+    """Library kernels per step; the per-phase form of the terrain rules
+    adds the two passes of the water flow."""
+    return KERNELS_PER_STEP[launch_mode] + (2 if launch_mode == 1 and rules == "terrain" else 0)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -53,7 +59,20 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "fp8"],
                     help="override the workload's streamed weight precision")
-    return ap.parse_args()
+    ap.add_argument("--side", type=int, default=None,
+                    help="a smaller world of the same workload (with --slots and --founders), "
+                         "e.g. for a profiler capture")
+    ap.add_argument("--slots", type=int, default=None)
+    ap.add_argument("--founders", type=int, default=None)
+    ap.add_argument("--policy-variant", type=int, default=0,
+                    help="force a policy-kernel variant (0: autotune)")
+    ap.add_argument("--launch-mode", type=int, default=0, choices=[0, 1],
+                    help="environment phases: 0 persistent kernel, 1 one kernel per phase")
+    args = ap.parse_args()
+    scale = (args.side, args.slots, args.founders)
+    if any(v is not None for v in scale) and not all(v is not None for v in scale):
+        ap.error("--side, --slots and --founders go together")
+    return args
 
 
 def reduce_over_ranks(dist, times, counts, device="cpu"):
@@ -77,10 +96,16 @@ def make_workloads(args, rank):
                                  precision=args.precision or "bf16")
     else:
         base = workloads.get(args.workload)
-        envs = [workloads.get(args.workload, seed=base["seed"] + rank)]
+        if args.side is not None:
+            envs = [workloads.scaled(args.workload, args.side, args.slots, args.founders,
+                                     seed=base["seed"] + rank)]
+        else:
+            envs = [workloads.get(args.workload, seed=base["seed"] + rank)]
         if args.precision:
             envs[0]["precision"] = args.precision
-            envs[0]["name"] = envs[0]["name"].rsplit("-", 1)[0] + "-" + args.precision
+            head, _, last = envs[0]["name"].rpartition("-")
+            envs[0]["name"] = (head if last in ("fp32", "bf16", "fp8") else envs[0]["name"]) + \
+                "-" + args.precision
     return envs
 
 
@@ -281,7 +306,7 @@ def main():
 
     envs = make_workloads(args, rank)
     w = envs[0]
-    env = eco.Env(envs)
+    env = eco.Env(envs, policy_variant=args.policy_variant, launch_mode=args.launch_mode)
 
     def agent_steps_of(stats):
         return sum(s["agent_steps"] for s in stats)
@@ -424,7 +449,7 @@ def main():
             },
             "e2e": {"value": e_agent_steps / e_el, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": KERNELS_PER_STEP[launch_mode] * args.steps,
+            "gpu_launches": kernels_per_step(launch_mode, w.get("rules", "simple")) * args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

@@ -37,6 +37,21 @@ __device__ __forceinline__ uint4 ldg_stream(const uint4 *p) {
   return r;
 }
 
+// Two FP32 fused multiply-adds in one instruction (Blackwell's packed FP32
+// pipe): a0 += w0 * x and a1 += w1 * x, each rounded once as by fmaf, so the
+// results are bit-identical to two fmaf calls while the weight stream issues
+// half as many FMA instructions.
+__device__ __forceinline__ void ffma2(float &a0, float &a1, float w0, float w1, float x) {
+  asm("{\n\t.reg .b64 pa, pw, px;\n\t"
+      "mov.b64 pa, {%0, %1};\n\t"
+      "mov.b64 pw, {%2, %3};\n\t"
+      "mov.b64 px, {%4, %4};\n\t"
+      "fma.rn.f32x2 pa, pw, px, pa;\n\t"
+      "mov.b64 {%0, %1}, pa;\n\t}"
+      : "+f"(a0), "+f"(a1)
+      : "f"(w0), "f"(w1), "f"(x));
+}
+
 template <int PREC>
 struct Unit;
 
@@ -44,10 +59,8 @@ template <>
 struct Unit<PREC_FP32> {
   static constexpr int E = 4;
   __device__ __forceinline__ static void fma(float *acc, const uint4 &v, float x) {
-    acc[0] = fmaf(__uint_as_float(v.x), x, acc[0]);
-    acc[1] = fmaf(__uint_as_float(v.y), x, acc[1]);
-    acc[2] = fmaf(__uint_as_float(v.z), x, acc[2]);
-    acc[3] = fmaf(__uint_as_float(v.w), x, acc[3]);
+    ffma2(acc[0], acc[1], __uint_as_float(v.x), __uint_as_float(v.y), x);
+    ffma2(acc[2], acc[3], __uint_as_float(v.z), __uint_as_float(v.w), x);
   }
   __device__ __forceinline__ static float dot(const uint4 &v, const float *h) {
     const float4 a = *reinterpret_cast<const float4 *>(h);
@@ -66,14 +79,10 @@ template <>
 struct Unit<PREC_BF16> {
   static constexpr int E = 8;
   __device__ __forceinline__ static void fma(float *acc, const uint4 &v, float x) {
-    acc[0] = fmaf(bf_lo(v.x), x, acc[0]);
-    acc[1] = fmaf(bf_hi(v.x), x, acc[1]);
-    acc[2] = fmaf(bf_lo(v.y), x, acc[2]);
-    acc[3] = fmaf(bf_hi(v.y), x, acc[3]);
-    acc[4] = fmaf(bf_lo(v.z), x, acc[4]);
-    acc[5] = fmaf(bf_hi(v.z), x, acc[5]);
-    acc[6] = fmaf(bf_lo(v.w), x, acc[6]);
-    acc[7] = fmaf(bf_hi(v.w), x, acc[7]);
+    ffma2(acc[0], acc[1], bf_lo(v.x), bf_hi(v.x), x);
+    ffma2(acc[2], acc[3], bf_lo(v.y), bf_hi(v.y), x);
+    ffma2(acc[4], acc[5], bf_lo(v.z), bf_hi(v.z), x);
+    ffma2(acc[6], acc[7], bf_lo(v.w), bf_hi(v.w), x);
   }
   __device__ __forceinline__ static float dot(const uint4 &v, const float *h) {
     const float4 a = *reinterpret_cast<const float4 *>(h);
@@ -101,10 +110,8 @@ struct Unit<PREC_FP8> {
   static constexpr int E = 16;
   __device__ __forceinline__ static void fma4(float *acc, uint32_t w, float x) {
     const float2 a = e4m3x2(w), b = e4m3x2(w >> 16);
-    acc[0] = fmaf(a.x, x, acc[0]);
-    acc[1] = fmaf(a.y, x, acc[1]);
-    acc[2] = fmaf(b.x, x, acc[2]);
-    acc[3] = fmaf(b.y, x, acc[3]);
+    ffma2(acc[0], acc[1], a.x, a.y, x);
+    ffma2(acc[2], acc[3], b.x, b.y, x);
   }
   __device__ __forceinline__ static void fma(float *acc, const uint4 &v, float x) {
     fma4(acc + 0, v.x, x);
@@ -170,28 +177,46 @@ __device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int 
     const uint4 v = ldg_stream(w + u);
     Unit<PREC>::fma(acc, v, x[u >> LG]);
   }
+  // Reduce-scatter over the 32 / UPJ lanes that hold partial sums of the same
+  // E outputs (xor partners at offsets UPJ, 2 UPJ, ..., 16): at each step a
+  // lane keeps one half of its live sums, sends the other half to its
+  // partner and adds the partner's half of what it keeps.  Afterwards every
+  // lane holds H / 32 finished outputs, so the bias, scale and activation
+  // run on all 32 lanes.
+  int base = 0;
 #pragma unroll
-  for (int off = UPJ; off < 32; off <<= 1) {
+  for (int step = 0; (UPJ << step) < 32; ++step) {
+    const int off = UPJ << step;
+    constexpr int kE = E;
+    const int half = kE >> (step + 1);
+    const bool upper = (lane & off) != 0;
 #pragma unroll
-    for (int e = 0; e < E; ++e) acc[e] += __shfl_xor_sync(0xFFFFFFFFu, acc[e], off);
-  }
-  if (lane < UPJ) {
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int o = lane * E + e;
-      const float s = (PREC == PREC_FP8) ? __ldg(scale + o) : 1.0f;
-      float b = __ldg(bias + o);
-      for (int k = 1; k < nbias; ++k) b += __ldg(bias + k * H + o);
-      const float v = fmaf(acc[e], s, b);
-      out[o] = relu ? fmaxf(v, 0.0f) : tanhf(v);
+    for (int i = 0; i < half; ++i) {
+      const float lo = acc[i], hi = acc[i + half];
+      const float keep = upper ? hi : lo;
+      acc[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, upper ? lo : hi, off);
     }
+    if (upper) base += half;
+  }
+  constexpr int NOUT = H / 32;
+  const int o0 = (lane & (UPJ - 1)) * E + base;
+#pragma unroll
+  for (int i = 0; i < NOUT; ++i) {
+    const int o = o0 + i;
+    const float s = (PREC == PREC_FP8) ? __ldg(scale + o) : 1.0f;
+    float b = __ldg(bias + o);
+    for (int k = 1; k < nbias; ++k) b += __ldg(bias + k * H + o);
+    const float v = fmaf(acc[i], s, b);
+    out[o] = relu ? fmaxf(v, 0.0f) : tanhf(v);
   }
 }
 
 // The weight stream is latency-bound per warp: the register budget is capped
-// so that about 40 warps stay resident per SM.
-template <int PREC, int H, int WARPS, int UNROLL>
-__global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
+// so that MINB CTAs (MINB * WARPS warps) stay resident per SM -- about 40
+// warps at 48 registers, or 32 warps at 64 registers for the FP8 form, whose
+// 16 accumulators per lane need the room.
+template <int PREC, int H, int WARPS, int UNROLL, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
     k_policy(Dev d, Layout L, Rules R, int xs_floats, int apply_moves) {
   constexpr int E = Unit<PREC>::E;
   constexpr int UPJ = H / E;
@@ -206,6 +231,7 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
   const int n_alive = d.counters[CNT_N_ALIVE];
   const uint32_t t = (uint32_t)d.step[0];
   const int k = R.patch_k, RR = k >> 1, kk = k * k;
+  const uint32_t kdiv = 0xFFFFFFFFu / (uint32_t)k + 1u;  // ceil(2^32 / k), k odd
   const bool rotate = (R.flags & F_ROTATE_OBS) != 0;
   const bool greedy = (R.flags & F_GREEDY) != 0;
 
@@ -244,7 +270,8 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
     const bool terrain = R.rules == RULES_TERRAIN;
     const int rock0 = terrain ? d.rock[ed.cell_off + pos] : 0;
     for (int c = lane; c < kk; c += 32) {
-      const int r = c / k, col = c - r * k;
+      // c / k by a multiply-high with ceil(2^32 / k): exact for c < 2^10
+      const int r = (int)__umulhi((uint32_t)c, kdiv), col = c - r * k;
       int dx, dy;
       if (rotate) {
         const int fw = fw0 - r, ri = col - RR;
@@ -254,7 +281,10 @@ __global__ void __launch_bounds__(WARPS * 32, 40 / WARPS)
         dx = col - RR;
         dy = r - RR;
       }
-      const int cx = wrapi(px + dx, side), cy = wrapi(py + dy, side);
+      // |dx|, |dy| <= k / 2 < side: one correction wraps the torus
+      int cx = px + dx, cy = py + dy;
+      cx += cx < 0 ? side : (cx >= side ? -side : 0);
+      cy += cy < 0 ? side : (cy >= side ? -side : 0);
       const int gc = ed.cell_off + cy * side + cx;
       const uint32_t cf = cellf[cy * side + cx];
       if (R.vision == VISION_RGB) {
@@ -456,6 +486,8 @@ static const VariantDesc kVariants[] = {
     {"warp-per-agent, 8 warps/CTA, 8 units in flight per lane", 8, 8},
     {"warp-per-agent, 8 warps/CTA, 4 units in flight per lane", 8, 4},
     {"warp-per-agent, 16 warps/CTA, 4 units in flight per lane", 16, 4},
+    {"warp-per-agent, 8 warps/CTA, 4 units in flight per lane, 64 registers", 8, 4},
+    {"warp-per-agent, 4 warps/CTA, 8 units in flight per lane, 64 registers", 4, 8},
 };
 static const int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -468,10 +500,12 @@ const char *policy_variant_name(int k) {
 template <int PREC, int H>
 static PolicyFn pick_fn(int variant) {
   switch (variant) {
-    case 1: return k_policy<PREC, H, 4, 8>;
-    case 2: return k_policy<PREC, H, 8, 8>;
-    case 3: return k_policy<PREC, H, 8, 4>;
-    default: return k_policy<PREC, H, 16, 4>;
+    case 1: return k_policy<PREC, H, 4, 8, 10>;
+    case 2: return k_policy<PREC, H, 8, 8, 5>;
+    case 3: return k_policy<PREC, H, 8, 4, 5>;
+    case 4: return k_policy<PREC, H, 16, 4, 2>;
+    case 5: return k_policy<PREC, H, 8, 4, 4>;
+    default: return k_policy<PREC, H, 4, 8, 8>;
   }
 }
 

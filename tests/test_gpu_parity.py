@@ -58,9 +58,10 @@ def test_rule_flags(flags):
     _run(w, 10)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
-def test_every_policy_variant(variant):
-    w = workloads.scaled("mid", 64, 512, 450, precision="bf16")
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+def test_every_policy_variant(variant, prec):
+    w = workloads.scaled("mid", 64, 512, 450, precision=prec)
     _run(w, 3, policy_variant=variant)
 
 

@@ -30,6 +30,7 @@ def _rank_main(rank, world, port, out):
     class A:
         workload = "small"
         precision = None
+        side = slots = founders = None
 
     envs = bench.make_workloads(A, rank)
     w = envs[0]
