@@ -390,6 +390,37 @@ def main():
         del singles
         torch.cuda.empty_cache()
 
+    # ---- the input-sparse policy variants (opt-in: they stream only the
+    #      W_in rows of nonzero inputs), same worlds and window; reported
+    #      beside the dense figures, never as the roofline fraction
+    sparse = None
+    if args.workload != "batched" and args.policy_variant == 0:
+        senv = eco.Env(envs, policy_variant=-1, launch_mode=args.launch_mode)
+        senv.reset()
+        senv.step(args.warmup)
+        torch.cuda.synchronize()
+        q0 = agent_steps_of(senv.stats())
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(senv.stream)
+        senv.step_timed(args.steps)
+        b.record(senv.stream)
+        b.synchronize()
+        sms = a.elapsed_time(b)
+        s_agent_steps = agent_steps_of(senv.stats()) - q0
+        s_policy_ms, s_n = senv.policy_timing()
+        sparse = {"value": s_agent_steps / (sms * 1e-3), "unit": UNIT,
+                  "ms_per_step": sms / args.steps,
+                  "policy_ms_per_step": s_policy_ms / max(1, s_n),
+                  "effective_gbs": s_agent_steps * per_agent_bytes / (s_policy_ms * 1e-3) / 1e9
+                  if s_policy_ms > 0 else None,
+                  "variant": eco.eco_policy_variant_name(senv.variants()[1]),
+                  "note": "streams only the W_in rows of nonzero inputs; effective_gbs = dense "
+                          "algorithmic bytes / policy time (not a roofline fraction)"}
+        senv.close()
+        del senv
+        torch.cuda.empty_cache()
+
     if dist is not None:
         ms, e_el, agent_steps, e_agent_steps = reduce_over_ranks(
             dist, [ms, e_el], [agent_steps, e_agent_steps], device="cuda")
@@ -455,6 +486,8 @@ def main():
         }
         if sequential is not None:
             line["sequential_single_world_launches"] = sequential
+        if sparse is not None:
+            line["input_sparse"] = sparse
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -174,8 +174,12 @@ typedef struct {
   int32_t e_repro;               /* reproduction threshold; also the energy
                                     scale of the observation scalar          */
   int32_t attack_num, attack_den;/* transferred fraction of victim energy    */
-  int32_t policy_variant;        /* 0 = autotune at create; k > 0 = force
-                                    variant k (see eco_policy_variants)      */
+  int32_t policy_variant;        /* 0 = autotune over the dense variants;
+                                    -1 = autotune over the input-sparse
+                                    variants, which stream only the W_in
+                                    rows of nonzero inputs (same result up to
+                                    the order of FP32 additions); k > 0 =
+                                    force variant k (eco_policy_variants) */
   int32_t launch_mode;           /* environment phases: 0 = one persistent
                                     cooperative kernel when the device
                                     supports it, 1 = one kernel per phase

@@ -15,8 +15,9 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeco.so")
-SOURCES = ["eco_api.cu", "eco_policy.cu", "eco_env.cu", "eco_init.cu", "eco_noalloc.cu"]
-HEADERS = ["eco_internal.cuh", "eco_kernels.h"]
+SOURCES = ["eco_policy_fp8.cu", "eco_policy_bf16.cu", "eco_policy_fp32.cu", "eco_api.cu",
+           "eco_policy.cu", "eco_env.cu", "eco_init.cu", "eco_noalloc.cu"]
+HEADERS = ["eco_internal.cuh", "eco_kernels.h", "eco_policy_kernel.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

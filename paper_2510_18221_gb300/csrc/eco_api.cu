@@ -41,7 +41,8 @@ struct eco_handle {
   EnvGrid grid;
   // policy
   int variant;       // chosen variant (0 = not chosen yet)
-  int forced;        // variant forced by the configuration (0 = autotune)
+  int forced;        // variant forced by the configuration (0 = autotune the dense
+                     // variants, -1 = autotune the input-sparse ones)
   PolicyLaunch pl;
   // step graph
   cudaGraphExec_t graph;
@@ -132,7 +133,7 @@ static int validate(const eco_config *c, char *msg, size_t n) {
   const int nch = terrain ? 4 : 3;
   if (nch * c->patch_k * c->patch_k + c->n_scalars < c->hidden)
     return snprintf(msg, n, "observation smaller than the hidden width"), ECO_EINVAL;
-  if (c->policy_variant < 0 || c->policy_variant > policy_variant_count())
+  if (c->policy_variant < -1 || c->policy_variant > policy_variant_count())
     return snprintf(msg, n, "policy_variant out of range"), ECO_EINVAL;
   long long cells = 0, slots = 0;
   for (int e = 0; e < c->n_envs; ++e) {
@@ -424,7 +425,7 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
     delete h;
     return r;
   }
-  if (h->forced) {
+  if (h->forced > 0) {
     e = policy_prepare(h->L, h->R, h->forced, &h->pl);
     if (e != cudaSuccess) {
       int r = fail(nullptr, ECO_ECUDA, "policy variant %d: %s", h->forced, cudaGetErrorString(e));
@@ -477,7 +478,9 @@ static int autotune(eco_handle *h) {
   CUDA_TRY(h, cudaEventCreate(&b));
   float best_ms = 1e30f;
   int best = 0;
+  const bool sparse = h->forced < 0;
   for (int v = 1; v <= policy_variant_count(); ++v) {
+    if (policy_variant_sparse(v) != sparse) continue;
     PolicyLaunch pl;
     if (policy_prepare(h->L, h->R, v, &pl) != cudaSuccess) {
       cudaGetLastError();

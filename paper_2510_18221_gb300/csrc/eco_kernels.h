@@ -16,6 +16,23 @@ struct PolicyLaunch {
 };
 int policy_variant_count();
 const char *policy_variant_name(int k);
+// Variants that stream only the W_in rows of nonzero inputs (opt-in: the
+// autotuner chooses among them only when asked to, policy_variant = -1).
+bool policy_variant_sparse(int k);
+typedef void (*PolicyFn)(Dev, Layout, Rules, int, int);
+// Floats of one warp's shared-memory slice: observation (xs_floats, a
+// multiple of 4), hidden activation (H), logits (16) and, for the sparse
+// variants, the list of nonzero inputs (xs_floats shorts, rounded up to whole
+// 16-byte units).  Every part is a multiple of 4 floats, so each warp's
+// slice and the float4 reads of its activations stay 16-byte aligned.
+__host__ __device__ inline int policy_warp_floats(int xs_floats, int H, bool sparse) {
+  return xs_floats + H + 16 + (sparse ? ((xs_floats / 2 + 3) & ~3) : 0);
+}
+// Kernel instance of variant k for a hidden width (one translation unit per
+// precision: eco_policy_fp32.cu, eco_policy_bf16.cu, eco_policy_fp8.cu).
+PolicyFn policy_pick_fp32(int H, int variant);
+PolicyFn policy_pick_bf16(int H, int variant);
+PolicyFn policy_pick_fp8(int H, int variant);
 cudaError_t policy_prepare(const Layout &L, const Rules &R, int variant, PolicyLaunch *pl);
 // apply_moves: also apply facing / turns and file move claims (the step);
 // false leaves the world state untouched (timing, parity of the policy).

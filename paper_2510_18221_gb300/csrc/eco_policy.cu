@@ -1,493 +1,29 @@
-// eco_policy.cu -- the policy phase of the step: observation gather
-// (Sec. 3.2 "Sensors"), per-agent MLP D -> H -> H -> A with tanh hidden
-// layers (Sec. 3.3), and Gumbel-max sampling of the action (Sec. 3.3:
-// actions are sampled from a softmax over the logits).
-//
-// Every agent owns its weights, so the work is a batch of independent
-// matrix-vector products bound by HBM reads of the weights (about 57 KB per
-// agent in BF16 at 371 -> 64 -> 64 -> 9), not a dense contraction: tensor
-// cores do not apply.  The kernel is warp-per-agent:
-//   * the warp gathers the agent's k x k x 3 patch and scalars into its own
-//     shared-memory row (one byte per cell: food / wall / agent bits);
-//   * each lane streams 16-byte units of the agent's weight block with
-//     non-allocating loads, UNROLL units in flight per lane; a warp load is
-//     512 contiguous bytes;
-//   * in the input-major layout a lane's units always hold the same group of
-//     E outputs, so the lane accumulates E partial sums in FP32 and a
-//     butterfly over lanes with the same group finishes each output;
-//   * the head (A rows, output-major) reduces over small lane groups, and a
-//     warp argmax of logit + Gumbel picks the action (ties to the lowest
-//     action index).
-// All floating-point reductions run in a fixed order, so results are
-// bit-reproducible from run to run.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <cuda_fp8.h>
-
+// eco_policy.cu -- the policy phase's host side: the table of kernel
+// variants the autotuner chooses from, shared-memory sizing and the launch.
+// The kernel itself is eco_policy_kernel.cuh, instantiated per precision in
+// eco_policy_fp32.cu, eco_policy_bf16.cu and eco_policy_fp8.cu.
 #include "eco_internal.cuh"
 #include "eco_kernels.h"
 
 namespace eco {
 
-__device__ __forceinline__ uint4 ldg_stream(const uint4 *p) {
-  uint4 r;
-  asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
-      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-      : "l"(p));
-  return r;
-}
-
-// Two FP32 fused multiply-adds in one instruction (Blackwell's packed FP32
-// pipe): a0 += w0 * x and a1 += w1 * x, each rounded once as by fmaf, so the
-// results are bit-identical to two fmaf calls while the weight stream issues
-// half as many FMA instructions.
-__device__ __forceinline__ void ffma2(float &a0, float &a1, float w0, float w1, float x) {
-  asm("{\n\t.reg .b64 pa, pw, px;\n\t"
-      "mov.b64 pa, {%0, %1};\n\t"
-      "mov.b64 pw, {%2, %3};\n\t"
-      "mov.b64 px, {%4, %4};\n\t"
-      "fma.rn.f32x2 pa, pw, px, pa;\n\t"
-      "mov.b64 {%0, %1}, pa;\n\t}"
-      : "+f"(a0), "+f"(a1)
-      : "f"(w0), "f"(w1), "f"(x));
-}
-
-template <int PREC>
-struct Unit;
-
-template <>
-struct Unit<PREC_FP32> {
-  static constexpr int E = 4;
-  __device__ __forceinline__ static void fma(float *acc, const uint4 &v, float x) {
-    ffma2(acc[0], acc[1], __uint_as_float(v.x), __uint_as_float(v.y), x);
-    ffma2(acc[2], acc[3], __uint_as_float(v.z), __uint_as_float(v.w), x);
-  }
-  __device__ __forceinline__ static float dot(const uint4 &v, const float *h) {
-    const float4 a = *reinterpret_cast<const float4 *>(h);
-    float s = __uint_as_float(v.x) * a.x;
-    s = fmaf(__uint_as_float(v.y), a.y, s);
-    s = fmaf(__uint_as_float(v.z), a.z, s);
-    s = fmaf(__uint_as_float(v.w), a.w, s);
-    return s;
-  }
-};
-
-__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
-__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
-
-template <>
-struct Unit<PREC_BF16> {
-  static constexpr int E = 8;
-  __device__ __forceinline__ static void fma(float *acc, const uint4 &v, float x) {
-    ffma2(acc[0], acc[1], bf_lo(v.x), bf_hi(v.x), x);
-    ffma2(acc[2], acc[3], bf_lo(v.y), bf_hi(v.y), x);
-    ffma2(acc[4], acc[5], bf_lo(v.z), bf_hi(v.z), x);
-    ffma2(acc[6], acc[7], bf_lo(v.w), bf_hi(v.w), x);
-  }
-  __device__ __forceinline__ static float dot(const uint4 &v, const float *h) {
-    const float4 a = *reinterpret_cast<const float4 *>(h);
-    const float4 b = *reinterpret_cast<const float4 *>(h + 4);
-    float s = bf_lo(v.x) * a.x;
-    s = fmaf(bf_hi(v.x), a.y, s);
-    s = fmaf(bf_lo(v.y), a.z, s);
-    s = fmaf(bf_hi(v.y), a.w, s);
-    s = fmaf(bf_lo(v.z), b.x, s);
-    s = fmaf(bf_hi(v.z), b.y, s);
-    s = fmaf(bf_lo(v.w), b.z, s);
-    s = fmaf(bf_hi(v.w), b.w, s);
-    return s;
-  }
-};
-
-// Two e4m3 codes (low byte = first element) to two floats, exactly.
-__device__ __forceinline__ float2 e4m3x2(uint32_t two) {
-  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(two & 0xFFFFu), __NV_E4M3);
-  return __half22float2(*reinterpret_cast<const __half2 *>(&h));
-}
-
-template <>
-struct Unit<PREC_FP8> {
-  static constexpr int E = 16;
-  __device__ __forceinline__ static void fma4(float *acc, uint32_t w, float x) {
-    const float2 a = e4m3x2(w), b = e4m3x2(w >> 16);
-    ffma2(acc[0], acc[1], a.x, a.y, x);
-    ffma2(acc[2], acc[3], b.x, b.y, x);
-  }
-  __device__ __forceinline__ static void fma(float *acc, const uint4 &v, float x) {
-    fma4(acc + 0, v.x, x);
-    fma4(acc + 4, v.y, x);
-    fma4(acc + 8, v.z, x);
-    fma4(acc + 12, v.w, x);
-  }
-  __device__ __forceinline__ static float dot4(uint32_t w, const float *h, float s) {
-    const float2 a = e4m3x2(w), b = e4m3x2(w >> 16);
-    const float4 x = *reinterpret_cast<const float4 *>(h);
-    s = fmaf(a.x, x.x, s);
-    s = fmaf(a.y, x.y, s);
-    s = fmaf(b.x, x.z, s);
-    s = fmaf(b.y, x.w, s);
-    return s;
-  }
-  __device__ __forceinline__ static float dot(const uint4 &v, const float *h) {
-    float s = 0.0f;
-    s = dot4(v.x, h, s);
-    s = dot4(v.y, h + 4, s);
-    s = dot4(v.z, h + 8, s);
-    s = dot4(v.w, h + 12, s);
-    return s;
-  }
-};
-
-template <int N>
-struct Log2 {
-  static constexpr int v = 1 + Log2<N / 2>::v;
-};
-template <>
-struct Log2<1> {
-  static constexpr int v = 0;
-};
-
-// One input-major layer: out[o] = act(s_o * sum_j W[j][o] x[j] + b_o) for
-// o in [0, H), written to shared memory by lanes 0 .. H/E - 1.  b_o is the
-// sum of nbias bias vectors (the paper form's per-sensor input biases);
-// act is ReLU or tanh.
-template <int PREC, int H, int UNROLL>
-__device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int n_in,
-                                               const float *__restrict__ x,
-                                               const float *__restrict__ bias, int nbias,
-                                               const float *__restrict__ scale,
-                                               float *__restrict__ out, int lane, int relu) {
-  constexpr int E = Unit<PREC>::E;
-  constexpr int UPJ = H / E;  // units per input
-  constexpr int LG = Log2<UPJ>::v;
-  static_assert((1 << LG) == UPJ && UPJ <= 32, "H / E must be a power of two <= 32");
-  float acc[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) acc[e] = 0.0f;
-  const int U = n_in * UPJ;
-  int u = lane;
-  for (; u + 32 * (UNROLL - 1) < U; u += 32 * UNROLL) {
-    uint4 v[UNROLL];
-#pragma unroll
-    for (int k = 0; k < UNROLL; ++k) v[k] = ldg_stream(w + u + 32 * k);
-#pragma unroll
-    for (int k = 0; k < UNROLL; ++k) Unit<PREC>::fma(acc, v[k], x[(u + 32 * k) >> LG]);
-  }
-  for (; u < U; u += 32) {
-    const uint4 v = ldg_stream(w + u);
-    Unit<PREC>::fma(acc, v, x[u >> LG]);
-  }
-  // Reduce-scatter over the 32 / UPJ lanes that hold partial sums of the same
-  // E outputs (xor partners at offsets UPJ, 2 UPJ, ..., 16): at each step a
-  // lane keeps one half of its live sums, sends the other half to its
-  // partner and adds the partner's half of what it keeps.  Afterwards every
-  // lane holds H / 32 finished outputs, so the bias, scale and activation
-  // run on all 32 lanes.
-  int base = 0;
-#pragma unroll
-  for (int step = 0; (UPJ << step) < 32; ++step) {
-    const int off = UPJ << step;
-    constexpr int kE = E;
-    const int half = kE >> (step + 1);
-    const bool upper = (lane & off) != 0;
-#pragma unroll
-    for (int i = 0; i < half; ++i) {
-      const float lo = acc[i], hi = acc[i + half];
-      const float keep = upper ? hi : lo;
-      acc[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, upper ? lo : hi, off);
-    }
-    if (upper) base += half;
-  }
-  constexpr int NOUT = H / 32;
-  const int o0 = (lane & (UPJ - 1)) * E + base;
-#pragma unroll
-  for (int i = 0; i < NOUT; ++i) {
-    const int o = o0 + i;
-    const float s = (PREC == PREC_FP8) ? __ldg(scale + o) : 1.0f;
-    float b = __ldg(bias + o);
-    for (int k = 1; k < nbias; ++k) b += __ldg(bias + k * H + o);
-    const float v = fmaf(acc[i], s, b);
-    out[o] = relu ? fmaxf(v, 0.0f) : tanhf(v);
-  }
-}
-
-// The weight stream is latency-bound per warp: the register budget is capped
-// so that MINB CTAs (MINB * WARPS warps) stay resident per SM -- about 40
-// warps at 48 registers, or 32 warps at 64 registers for the FP8 form, whose
-// 16 accumulators per lane need the room.
-template <int PREC, int H, int WARPS, int UNROLL, int MINB>
-__global__ void __launch_bounds__(WARPS * 32, MINB)
-    k_policy(Dev d, Layout L, Rules R, int xs_floats, int apply_moves) {
-  constexpr int E = Unit<PREC>::E;
-  constexpr int UPJ = H / E;
-  constexpr int LG = Log2<UPJ>::v;
-  extern __shared__ __align__(16) float smem[];
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  float *xs = smem + warp * (xs_floats + H + 16);
-  float *hs = xs + xs_floats;
-  float *ls = hs + H;
-
-  const int n_alive = d.counters[CNT_N_ALIVE];
-  const uint32_t t = (uint32_t)d.step[0];
-  const int k = R.patch_k, RR = k >> 1, kk = k * k;
-  const uint32_t kdiv = 0xFFFFFFFFu / (uint32_t)k + 1u;  // ceil(2^32 / k), k odd
-  const bool rotate = (R.flags & F_ROTATE_OBS) != 0;
-  const bool greedy = (R.flags & F_GREEDY) != 0;
-
-  // Per-warp counters, flushed when the environment changes: lane a < 16
-  // counts action a, lane 16 counts moves blocked by a wall or an agent.
-  int cnt = 0, e_cur = -1;
-  auto flush = [&]() {
-    if (e_cur >= 0 && cnt && lane <= 16)
-      atomicAdd((unsigned long long *)&d.stats_step[e_cur * N_ST + (lane < 16 ? ST_ACT0 + lane : ST_MOVE_BLOCKED)],
-                (unsigned long long)cnt);
-    cnt = 0;
-  };
-
-  for (int i = blockIdx.x * WARPS + warp; i < n_alive; i += gridDim.x * WARPS) {
-    const int slot = d.alive_list[i];
-    const int env = d.env_of[slot];
-    if (env != e_cur) {
-      flush();
-      e_cur = env;
-    }
-    // -- observation: k x k x nch patch (row, column, channel), then scalars.
-    // Its locals end with this scope so that they do not stay live (in
-    // registers) through the weight stream below.
-    {
-    const EnvDesc ed = d.env[env];
-    const int side = ed.side;
-    const int pos = d.pos[slot];
-    const int px = pos % side, py = pos / side;
-    const int f = d.facing[slot];
-    const int rt = (f + 1) & 3;
-    const uint8_t *cellf = d.cellf + ed.cell_off;
-    // rows run from far ahead (top) to behind (Around) or to the agent's
-    // own row (Front); columns from the agent's left to its right
-    const int fw0 = R.view == VIEW_FRONT ? k - 1 : RR;
-    const int nch = L.nch;
-    const bool terrain = R.rules == RULES_TERRAIN;
-    const int rock0 = terrain ? d.rock[ed.cell_off + pos] : 0;
-    for (int c = lane; c < kk; c += 32) {
-      // c / k by a multiply-high with ceil(2^32 / k): exact for c < 2^10
-      const int r = (int)__umulhi((uint32_t)c, kdiv), col = c - r * k;
-      int dx, dy;
-      if (rotate) {
-        const int fw = fw0 - r, ri = col - RR;
-        dx = fw * dir_dx(f) + ri * dir_dx(rt);
-        dy = fw * dir_dy(f) + ri * dir_dy(rt);
-      } else {
-        dx = col - RR;
-        dy = r - RR;
-      }
-      // |dx|, |dy| <= k / 2 < side: one correction wraps the torus
-      int cx = px + dx, cy = py + dy;
-      cx += cx < 0 ? side : (cx >= side ? -side : 0);
-      cy += cy < 0 ? side : (cy >= side ? -side : 0);
-      const int gc = ed.cell_off + cy * side + cx;
-      const uint32_t cf = cellf[cy * side + cx];
-      if (R.vision == VISION_RGB) {
-        // rendered colours: the occupant's colour trait, else grey wall,
-        // else green food (terrain: the cell's biomass, energy and water)
-        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (cf & CELL_AGENT) {
-          v = d.colour[d.occ[gc]];
-        } else if (cf & CELL_WALL) {
-          v = make_float4(0.5f, 0.5f, 0.5f, 0.0f);
-        } else if (terrain) {
-          const float b = (float)d.bio[gc], r = (float)d.res[gc], w = (float)d.water[gc];
-          v = make_float4(b / (b + (float)R.b_bite), r / (r + (float)R.e_food), w / (w + (float)R.w_bite), 0.0f);
-        } else if (cf & CELL_FOOD) {
-          v.y = 1.0f;
-        }
-        xs[nch * c + 0] = v.x;
-        xs[nch * c + 1] = v.y;
-        xs[nch * c + 2] = v.z;
-        if (terrain) {  // elevation: rock difference d as d / (|d| + 16)
-          const float dz = (float)(d.rock[gc] - rock0);
-          xs[nch * c + 3] = dz / (fabsf(dz) + 16.0f);
-        }
-      } else {
-        xs[3 * c + 0] = (cf & CELL_FOOD) ? 1.0f : 0.0f;
-        xs[3 * c + 1] = (cf & CELL_AGENT) ? 1.0f : 0.0f;
-        xs[3 * c + 2] = (cf & CELL_WALL) ? 1.0f : 0.0f;
-      }
-    }
-    if (lane < R.n_scalars) {
-      // [e / e_repro, one-hot facing (8-scalar form), zeros]; the paper
-      // rules fill the zeros with HP / hp_max, age / (age + age_div) and
-      // r / (r + e_food), r the energy lying on the agent's cell
-      float v = 0.0f;
-      if (lane == 0)
-        v = (float)d.energy[slot] / (float)R.e_repro;
-      else if (R.n_scalars >= 8 && lane == 1 + f)
-        v = 1.0f;
-      if (R.rules != RULES_SIMPLE) {
-        const int extra = lane - (R.n_scalars >= 8 ? 5 : 1);
-        if (extra == 0) {
-          v = (float)d.hp[slot] / (float)R.hp_max;
-        } else if (extra == 1) {
-          const float a = (float)d.age[slot];
-          v = a / (a + (float)R.age_div);
-        } else if (extra == 2) {
-          const float r = (float)d.res[ed.cell_off + pos];
-          v = r / (r + (float)R.e_food);
-        }
-      }
-      if (terrain) {  // carried water and biomass; the cell's water and biomass
-        if (lane == 8) {
-          v = (float)d.a_water[slot] / (float)R.w_cap;
-        } else if (lane == 9) {
-          v = (float)d.a_bio[slot] / (float)R.b_cap;
-        } else if (lane == 10) {
-          const float w = (float)d.water[ed.cell_off + pos];
-          v = w / (w + (float)R.w_bite);
-        } else if (lane == 11) {
-          const float b = (float)d.bio[ed.cell_off + pos];
-          v = b / (b + (float)R.b_bite);
-        }
-      }
-      xs[nch * kk + lane] = v;
-    }
-    }
-    __syncwarp();
-
-    const uint8_t *blk = d.wq + (int64_t)slot * L.stride;
-    const uint4 *wb = reinterpret_cast<const uint4 *>(blk);
-    const float *bias = reinterpret_cast<const float *>(blk + L.off_bias);
-    const float *scale = reinterpret_cast<const float *>(blk + L.off_scale);
-
-    // -- input layer: act(sum over sensors of (W_s x_s + b_s)) -> hs
-    layer_in_major<PREC, H, UNROLL>(wb + L.off_w1 / 16, L.D, xs, bias, L.ns, scale, hs, lane,
-                                    L.relu);
-    __syncwarp();
-    // -- hidden layers: h = act(W_l h + b_l), alternating between hs and xs
-    float *cur = hs, *nxt = xs;
-    for (int l = 0; l < L.L; ++l) {
-      layer_in_major<PREC, H, UNROLL>(wb + (L.off_w2 + l * H * H * L.es) / 16, H, cur,
-                                      bias + L.ns * H + l * H, 1, scale + H + l * H, nxt, lane,
-                                      L.relu);
-      __syncwarp();
-      float *tmp = cur;
-      cur = nxt;
-      nxt = tmp;
-    }
-
-    // -- head: logits = (W_out h [+ b_out]) / exp(tau) (output-major rows of
-    //    H / E units; the temperature only in the paper form)
-    const uint4 *w3 = wb + L.off_w3 / 16;
-    const int U3 = L.A * UPJ;
-    const float *hb = bias + L.ns * H + L.L * H;  // head bias, then tau
-    const float tmul = L.temp ? expf(-__ldg(hb + (L.out_bias ? L.A : 0))) : 1.0f;
-    for (int base = 0; base < U3; base += 32) {
-      const int u = base + lane;
-      float part = 0.0f;
-      if (u < U3) part = Unit<PREC>::dot(ldg_stream(w3 + u), cur + (u & (UPJ - 1)) * E);
-#pragma unroll
-      for (int off = 1; off < UPJ; off <<= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, off);
-      if (u < U3 && (lane & (UPJ - 1)) == 0) {
-        const int a = u >> LG;
-        const float s = (PREC == PREC_FP8) ? __ldg(scale + H + L.L * H + a) : 1.0f;
-        const float v = L.out_bias ? fmaf(part, s, __ldg(hb + a)) : part * s;
-        ls[a] = L.temp ? v * tmul : v;
-      }
-    }
-    __syncwarp();
-
-    // -- sample: argmax_a (logit_a + Gumbel_a), ties to the lowest a
-    float score = -INFINITY;
-    int best = lane;
-    if (lane < L.A) {
-      const float lg = ls[lane];
-      d.logits[(int64_t)slot * L.A + lane] = lg;
-      score = lg;
-      if (!greedy) {
-        const EnvDesc ed = d.env[env];
-        const U4 r = philox(t, (uint32_t)(slot - ed.slot_off), (uint32_t)(lane >> 2), 0u, ed.seed,
-                            S_SAMPLE);
-        const float u = uniform01(word_of(r, lane & 3));
-        score = lg + (-logf(-logf(u)));
-      }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float os = __shfl_xor_sync(0xFFFFFFFFu, score, off);
-      const int oa = __shfl_xor_sync(0xFFFFFFFFu, best, off);
-      if (os > score || (os == score && oa < best)) {
-        score = os;
-        best = oa;
-      }
-    }
-    if (apply_moves) {
-      // A6 (part 1), fused: facing and turns, and the move claim on a cell
-      // that is neither a wall nor occupied now, at the start of the step
-      // (no cell changes while the policy phase runs).
-      int blk = 0;
-      if (lane == 0) {
-        const EnvDesc ed = d.env[env];
-        const int side = ed.side;
-        const int pos = d.pos[slot];
-        const int f = d.facing[slot];
-        const uint8_t *cellf = d.cellf + ed.cell_off;
-        int nf = f, tc = -1;
-        bool move = false;
-        if (R.rules != RULES_SIMPLE) {
-          // rotate clockwise / counter-clockwise, or one cell forward
-          if (best == PA_CW) nf = (f + 1) & 3;
-          else if (best == PA_CCW) nf = (f + 3) & 3;
-          move = best == PA_FORWARD;
-        } else if (best >= ACT_N && best <= ACT_W) {
-          nf = (best == ACT_N) ? 0 : (best == ACT_S) ? 2 : (best == ACT_E) ? 1 : 3;
-          move = true;
-        } else if (best == ACT_LEFT) {
-          nf = (f + 3) & 3;
-        } else if (best == ACT_RIGHT) {
-          nf = (f + 1) & 3;
-        }
-        if (move) {
-          const int c = step_cell(pos, nf, side);
-          if (cellf[c] & (CELL_WALL | CELL_AGENT)) {
-            blk = 1;
-          } else {
-            const int local = slot - ed.slot_off;
-            const U4 r = philox(t, (uint32_t)local, 0u, 0u, ed.seed, S_CLAIM_MOVE);
-            atomicMax(&d.claim_move[ed.cell_off + c], claim_key(r.x, local));
-            if (R.flags & F_CANCEL_ALL) atomicAdd(&d.cnt_move[ed.cell_off + c], 1u);
-            tc = c;
-          }
-        }
-        d.facing[slot] = (uint8_t)nf;
-        d.tgt[slot] = tc;
-      }
-      blk = __shfl_sync(0xFFFFFFFFu, blk, 0);
-      if (lane == best) ++cnt;
-      if (lane == 16 && blk) ++cnt;
-    }
-    if (lane == 0) d.act[slot] = (uint8_t)best;
-    __syncwarp();
-  }
-  flush();
-}
-
-// ---------------------------------------------------------------------------
-// Variants and launch
-// ---------------------------------------------------------------------------
-
-typedef void (*PolicyFn)(Dev, Layout, Rules, int, int);
-
 struct VariantDesc {
   const char *name;
   int warps, unroll;
+  bool sparse;
 };
 
+// The launch bounds of each (warps, units in flight, resident CTAs) are in
+// policy_pick_variant (eco_policy_kernel.cuh).
 static const VariantDesc kVariants[] = {
-    {"warp-per-agent, 4 warps/CTA, 8 units in flight per lane", 4, 8},
-    {"warp-per-agent, 8 warps/CTA, 8 units in flight per lane", 8, 8},
-    {"warp-per-agent, 8 warps/CTA, 4 units in flight per lane", 8, 4},
-    {"warp-per-agent, 16 warps/CTA, 4 units in flight per lane", 16, 4},
-    {"warp-per-agent, 8 warps/CTA, 4 units in flight per lane, 64 registers", 8, 4},
-    {"warp-per-agent, 4 warps/CTA, 8 units in flight per lane, 64 registers", 4, 8},
+    {"warp-per-agent, 4 warps/CTA, 8 units in flight per lane", 4, 8, false},
+    {"warp-per-agent, 8 warps/CTA, 8 units in flight per lane", 8, 8, false},
+    {"warp-per-agent, 8 warps/CTA, 4 units in flight per lane", 8, 4, false},
+    {"warp-per-agent, 16 warps/CTA, 4 units in flight per lane", 16, 4, false},
+    {"warp-per-agent, 8 warps/CTA, 4 units in flight per lane, 64 registers", 8, 4, false},
+    {"warp-per-agent, 4 warps/CTA, 8 units in flight per lane, 64 registers", 4, 8, false},
+    {"input-sparse W_in rows, 8 warps/CTA, 4 units in flight per lane", 8, 4, true},
+    {"input-sparse W_in rows, 4 warps/CTA, 8 units in flight per lane, 64 registers", 4, 8, true},
 };
 static const int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -496,44 +32,24 @@ const char *policy_variant_name(int k) {
   if (k < 1 || k > kNumVariants) return "invalid";
   return kVariants[k - 1].name;
 }
-
-template <int PREC, int H>
-static PolicyFn pick_fn(int variant) {
-  switch (variant) {
-    case 1: return k_policy<PREC, H, 4, 8, 10>;
-    case 2: return k_policy<PREC, H, 8, 8, 5>;
-    case 3: return k_policy<PREC, H, 8, 4, 5>;
-    case 4: return k_policy<PREC, H, 16, 4, 2>;
-    case 5: return k_policy<PREC, H, 8, 4, 4>;
-    default: return k_policy<PREC, H, 4, 8, 8>;
-  }
-}
+bool policy_variant_sparse(int k) { return k >= 1 && k <= kNumVariants && kVariants[k - 1].sparse; }
 
 static PolicyFn pick(int prec, int H, int variant) {
-  if (prec == PREC_FP32) {
-    if (H == 32) return pick_fn<PREC_FP32, 32>(variant);
-    if (H == 64) return pick_fn<PREC_FP32, 64>(variant);
-    if (H == 128) return pick_fn<PREC_FP32, 128>(variant);
-  } else if (prec == PREC_BF16) {
-    if (H == 32) return pick_fn<PREC_BF16, 32>(variant);
-    if (H == 64) return pick_fn<PREC_BF16, 64>(variant);
-    if (H == 128) return pick_fn<PREC_BF16, 128>(variant);
-  } else {
-    if (H == 32) return pick_fn<PREC_FP8, 32>(variant);
-    if (H == 64) return pick_fn<PREC_FP8, 64>(variant);
-    if (H == 128) return pick_fn<PREC_FP8, 128>(variant);
-  }
-  return nullptr;
+  if (prec == PREC_FP32) return policy_pick_fp32(H, variant);
+  if (prec == PREC_BF16) return policy_pick_bf16(H, variant);
+  return policy_pick_fp8(H, variant);
 }
 
 int policy_xs_floats(const Layout &L) { return ((L.D > L.H ? L.D : L.H) + 3) & ~3; }
 
 cudaError_t policy_prepare(const Layout &L, const Rules &R, int variant, PolicyLaunch *pl) {
+  if (variant < 1 || variant > kNumVariants) return cudaErrorInvalidValue;
   PolicyFn fn = pick(R.precision, L.H, variant);
   if (!fn) return cudaErrorInvalidValue;
-  const int warps = kVariants[variant - 1].warps;
+  const VariantDesc &v = kVariants[variant - 1];
   const int xs = policy_xs_floats(L);
-  const size_t smem = (size_t)warps * (xs + L.H + 16) * sizeof(float);
+  // per warp: observation, hidden activation, logits (+ the sparse input list)
+  const size_t smem = (size_t)v.warps * policy_warp_floats(xs, L.H, v.sparse) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -542,11 +58,11 @@ cudaError_t policy_prepare(const Layout &L, const Rules &R, int variant, PolicyL
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, warps * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, v.warps * 32, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   pl->fn = (void *)fn;
-  pl->threads = warps * 32;
+  pl->threads = v.warps * 32;
   pl->blocks = sms * per_sm;  // one full wave of resident CTAs on every SM
   pl->smem = smem;
   pl->xs_floats = xs;

@@ -58,7 +58,7 @@ def test_rule_flags(flags):
     _run(w, 10)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
 def test_every_policy_variant(variant, prec):
     w = workloads.scaled("mid", 64, 512, 450, precision=prec)
@@ -418,3 +418,14 @@ def test_terrain_rock_and_state_roundtrip():
     assert st["water_agents"] == int(orc.a_water[orc.alive == 1].sum())
     assert st["bio_cells"] == int(orc.bio.sum())
     env.close()
+
+
+@pytest.mark.parametrize("base", ["ecology", "terrain", "paperform"])
+def test_input_sparse_variants_on_dense_inputs(base):
+    """The input-sparse variants (7, 8) on worlds whose observations are
+    mostly nonzero (RGB, elevation) and on the paper form's sensors."""
+    w = workloads.scaled(base, 64, 600, 450, e_init=60, e_repro=50, e_child=20, precision="bf16")
+    if base == "paperform":
+        w = workloads.scaled(base, 64, 600, 450, e_init=190, precision="fp8")
+    for v in (7, 8):
+        _run(w, 5, policy_variant=v)
