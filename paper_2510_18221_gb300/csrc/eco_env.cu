@@ -4,9 +4,9 @@
 //
 // Phase order: policy (+ facing, turns and move claims, fused into its
 // epilogue; eco_policy.cu) -> move apply + eat -> attack claims -> attack
-// gains -> metabolism + death -> birth claims -> slot assignment ->
-// mutation of the children + regrowth -> statistics + the alive list of the
-// next step.
+// transfers + metabolism + death -> birth claims (+ regrowth, which commutes
+// with them) -> slot assignment -> mutation of the children -> statistics +
+// the alive list of the next step.
 //
 // Two launch forms run the same phase functions: one persistent kernel
 // (cooperative launch; phases separated by grid barriers whose waits are
@@ -99,18 +99,30 @@ __device__ void ph_compact_scatter(const Dev &d, int b0, int bs, int *sh) {
 }
 
 // ---------------------------------------------------------------------------
-// Per-agent phases (grid-stride over the alive list).
+// Per-agent phases (grid-stride over the alive list).  The alive list does
+// not change until the compaction at the end of the step, so a persistent
+// thread loads the slot of its first entry once and passes it in (`first`;
+// -1 in the one-kernel-per-phase form).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int agent_slot(const Dev &d, int i, int g0, int first) {
+  return (i == g0 && first >= 0) ? first : d.alive_list[i];
+}
+
+// Environment of a slot (no lookup when there is one environment).
+__device__ __forceinline__ int env_index(const Dev &d, int slot) {
+  return d.n_envs == 1 ? 0 : (int)d.env_of[slot];
+}
+
 
 // A6 (part 2) + A7: winners move (only the winner of a cell writes it, and
 // a winner's old cell was occupied when the step began, so nobody moves
 // into it); then every agent eats the food of its post-move cell, when the
 // rules say it eats.  Nobody else can be on that cell.
-__device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, int g0, int gs) {
+__device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, int g0, int gs, int first) {
   const int n = d.counters[CNT_N_ALIVE];
   for (int i = g0; i < n; i += gs) {
-    const int slot = d.alive_list[i];
-    const int e = d.env_of[slot];
+    const int slot = agent_slot(d, i, g0, first);
+    const int e = env_index(d, slot);
     const EnvDesc ed = d.env[e];
     const int tc = d.tgt[slot];
     int pos = d.pos[slot];
@@ -178,6 +190,10 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
         stat_add(d.stats_step, e, ST_EATEN, 1);
       }
     }
+    // simple rules: the post-eat energy, which attack transfers are computed
+    // from, kept where an attacker can read it while the owner updates its
+    // own energy in the metabolism phase
+    if (R.rules == RULES_SIMPLE) d.gain[slot] = d.energy[slot];
   }
 }
 
@@ -185,12 +201,12 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
 // the faced cell (post-move occupancy).  Paper rules: an attacker adds
 // attack_damage to every agent in the 3x3 square in front of it (1..3 cells
 // ahead, one to either side); damage from several attackers adds up.
-__device__ void ph_attack_claim(const Dev &d, const Rules &R, int g0, int gs) {
+__device__ void ph_attack_claim(const Dev &d, const Rules &R, int g0, int gs, int first) {
   const int n = d.counters[CNT_N_ALIVE];
   const uint32_t t = (uint32_t)d.step[0];
   for (int i = g0; i < n; i += gs) {
-    const int slot = d.alive_list[i];
-    const int e = d.env_of[slot];
+    const int slot = agent_slot(d, i, g0, first);
+    const int e = env_index(d, slot);
     const EnvDesc ed = d.env[e];
     const int tc = d.tgt[slot];
     if (tc >= 0) {
@@ -233,27 +249,6 @@ __device__ void ph_attack_claim(const Dev &d, const Rules &R, int g0, int gs) {
   }
 }
 
-// A8 (part 2): the winning attacker of each victim takes floor(e * num /
-// den) of the victim's post-eat energy (read here, written only later).
-__device__ void ph_attack_gain(const Dev &d, const Rules &R, int g0, int gs) {
-  if (R.rules != RULES_SIMPLE) return;  // damage is applied in the health phase
-  const int n = d.counters[CNT_N_ALIVE];
-  for (int i = g0; i < n; i += gs) {
-    const int slot = d.alive_list[i];
-    const int v = d.tgt[slot];
-    int g = 0;
-    if (v >= 0) {
-      const int e = d.env_of[slot];
-      const int local = slot - d.env[e].slot_off;
-      if (claim_local_slot(d.claim_att[v]) == local) {
-        g = (int)(((long long)d.energy[v] * R.attack_num) / R.attack_den);
-        stat_add(d.stats_step, e, ST_ATTACK_HITS, 1);
-        stat_add(d.stats_step, e, ST_ENERGY_TRANSFERRED, g);
-      }
-    }
-    d.gain[slot] = g;
-  }
-}
 
 // Paper rules, one agent: pay the action's cost (starving when it exceeds
 // the energy), take the attack and age damage, heal from energy, and die at
@@ -277,7 +272,7 @@ __device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int s
     starved = 1;
   }
   const bool terrain = R.rules == RULES_TERRAIN;
-  const int e = d.env_of[slot];
+  const int e = env_index(d, slot);
   const int gpos = d.env[e].cell_off + d.pos[slot];
   int aw = terrain ? d.a_water[slot] : 0, spent = 0, thirsty = 0;
   if (terrain) {
@@ -344,23 +339,32 @@ __device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int s
   d.energy[slot] = en;
 }
 
-// A8 (part 3) + A9: apply the transfer, pay metabolism, die at e <= 0
+// A8 (part 2) + A9: the attack transfer, metabolism, death at e <= 0
 // (paper rules: health_paper).
-__device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs) {
+__device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs, int first) {
   const int n = d.counters[CNT_N_ALIVE];
   for (int i = g0; i < n; i += gs) {
-    const int slot = d.alive_list[i];
+    const int slot = agent_slot(d, i, g0, first);
     if (R.rules != RULES_SIMPLE) {
       health_paper(d, R, slot);
       continue;
     }
+    // A8 (part 2): a victim loses floor(e * num / den) of its post-eat
+    // energy to the attacker that won its claim, which gains the same amount
+    // (read from the victim's post-eat snapshot); claims are cleared in the
+    // birth-claim phase, after every attacker has read its victim's claim
     int en = d.energy[slot];
-    const unsigned long long ca = d.claim_att[slot];
-    const int loss = ca ? (int)(((long long)en * R.attack_num) / R.attack_den) : 0;
-    if (ca) d.claim_att[slot] = 0ull;
-    en = en - loss + d.gain[slot] - R.e_metab;
+    const int e = env_index(d, slot);
+    const int loss = d.claim_att[slot] ? (int)(((long long)en * R.attack_num) / R.attack_den) : 0;
+    int g = 0;
+    const int v = d.tgt[slot];
+    if (v >= 0 && claim_local_slot(d.claim_att[v]) == slot - d.env[e].slot_off) {
+      g = (int)(((long long)d.gain[v] * R.attack_num) / R.attack_den);
+      stat_add(d.stats_step, e, ST_ATTACK_HITS, 1);
+      stat_add(d.stats_step, e, ST_ENERGY_TRANSFERRED, g);
+    }
+    en = en - loss + g - R.e_metab;
     if (en <= 0) {
-      const int e = d.env_of[slot];
       const int gpos = d.env[e].cell_off + d.pos[slot];
       d.alive[slot] = 0;
       d.occ[gpos] = -1;
@@ -377,17 +381,18 @@ __device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs) {
 // reproduce; terrain rules: that also carry b_body + b_child biomass and
 // w_child water) claim the free non-wall cell behind them and join their
 // environment's contender list.
-__device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs) {
+__device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs, int first) {
   const int n = d.counters[CNT_N_ALIVE];
   const uint32_t t = (uint32_t)d.step[0];
   for (int i = g0; i < n; i += gs) {
-    const int slot = d.alive_list[i];
+    const int slot = agent_slot(d, i, g0, first);
+    if (R.rules == RULES_SIMPLE && d.claim_att[slot]) d.claim_att[slot] = 0ull;
     int bt = -1;
     if (d.alive[slot] && d.energy[slot] >= R.e_repro &&
         (R.rules == RULES_SIMPLE || d.act[slot] == PA_REPRODUCE) &&
         (R.rules != RULES_TERRAIN ||
          (d.a_bio[slot] >= R.b_body + R.b_child && d.a_water[slot] >= R.w_child))) {
-      const int e = d.env_of[slot];
+      const int e = env_index(d, slot);
       const EnvDesc ed = d.env[e];
       const int c = step_cell(d.pos[slot], (d.facing[slot] + 2) & 3, ed.side);
       const int gc = ed.cell_off + c;
@@ -913,11 +918,10 @@ __global__ void __launch_bounds__(256) k_compact_scatter(Dev d) {
   __shared__ int sh[33];
   ph_compact_scatter(d, blockIdx.x, gridDim.x, sh);
 }
-__global__ void k_move_apply_eat(Dev d, Rules R, int A) { ph_move_apply_eat(d, R, A, GRID_ARGS); }
-__global__ void k_attack_claim(Dev d, Rules R) { ph_attack_claim(d, R, GRID_ARGS); }
-__global__ void k_attack_gain(Dev d, Rules R) { ph_attack_gain(d, R, GRID_ARGS); }
-__global__ void k_metab_death(Dev d, Rules R) { ph_metab_death(d, R, GRID_ARGS); }
-__global__ void k_birth_claim(Dev d, Rules R) { ph_birth_claim(d, R, GRID_ARGS); }
+__global__ void k_move_apply_eat(Dev d, Rules R, int A) { ph_move_apply_eat(d, R, A, GRID_ARGS, -1); }
+__global__ void k_attack_claim(Dev d, Rules R) { ph_attack_claim(d, R, GRID_ARGS, -1); }
+__global__ void k_metab_death(Dev d, Rules R) { ph_metab_death(d, R, GRID_ARGS, -1); }
+__global__ void k_birth_claim(Dev d, Rules R) { ph_birth_claim(d, R, GRID_ARGS, -1); }
 __global__ void __launch_bounds__(1024) k_birth_assign(Dev d, Rules R) {
   __shared__ BirthSmem S;
   ph_birth_assign(d, R, blockIdx.x, gridDim.x, S);
@@ -980,21 +984,24 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   __shared__ int s_flag;
   const unsigned nb = gridDim.x;
   const int g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  ph_move_apply_eat(d, R, L.A, g0, gs);
+  // each thread's first alive-list entry, loaded once for all phases
+  const int first = g0 < d.counters[CNT_N_ALIVE] ? d.alive_list[g0] : -1;
+  ph_move_apply_eat(d, R, L.A, g0, gs, first);
   if (!grid_sync(d, nb, &s_flag)) return;
-  ph_attack_claim(d, R, g0, gs);
+  ph_attack_claim(d, R, g0, gs, first);
   if (!grid_sync(d, nb, &s_flag)) return;
-  ph_attack_gain(d, R, g0, gs);
+  ph_metab_death(d, R, g0, gs, first);
   if (!grid_sync(d, nb, &s_flag)) return;
-  ph_metab_death(d, R, g0, gs);
-  if (!grid_sync(d, nb, &s_flag)) return;
-  ph_birth_claim(d, R, g0, gs);
+  // regrowth (with photosynthesis and the flow's transfers) needs only the
+  // state after the deaths, and birth claims read only wall and agent bits,
+  // which regrowth keeps: the two share an interval
+  ph_birth_claim(d, R, g0, gs, first);
+  ph_regrow(d, R, g0, gs);
+  if (R.rules == RULES_TERRAIN) ph_flow_out(d, g0, gs);
   if (!grid_sync(d, nb, &s_flag)) return;
   ph_birth_assign(d, R, blockIdx.x, gridDim.x, S);
   if (!grid_sync(d, nb, &s_flag)) return;
   ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale);
-  ph_regrow(d, R, g0, gs);
-  if (R.rules == RULES_TERRAIN) ph_flow_out(d, g0, gs);
   ph_compact_count(d, blockIdx.x, gridDim.x, S.sh);
   if (!grid_sync(d, nb, &s_flag)) return;
   if (R.rules == RULES_TERRAIN) ph_flow_in(d, g0, gs);
@@ -1052,7 +1059,6 @@ cudaError_t launch_env_phases(const Dev &d, const Layout &L, const Rules &R, con
   const int T = 256;
   k_move_apply_eat<<<g.slot_blocks, T, 0, s>>>(d, R, L.A);
   k_attack_claim<<<g.slot_blocks, T, 0, s>>>(d, R);
-  k_attack_gain<<<g.slot_blocks, T, 0, s>>>(d, R);
   k_metab_death<<<g.slot_blocks, T, 0, s>>>(d, R);
   k_birth_claim<<<g.slot_blocks, T, 0, s>>>(d, R);
   k_birth_assign<<<d.n_envs, 1024, 0, s>>>(d, R);
