@@ -158,7 +158,9 @@ typedef struct {
   const int32_t *env_slots;      /* [n_envs] agent slots                     */
   const int32_t *env_init_alive; /* [n_envs] founders placed by eco_reset    */
   const uint32_t *env_seed;      /* [n_envs] Philox seed                     */
-  int32_t patch_k;               /* odd patch side k: D = 3k^2 + n_scalars   */
+  int32_t patch_k;               /* odd patch side k: D = 3k^2 + n_scalars
+                                    (4k^2 under the terrain rules); 0 = no
+                                    vision sensor (App. F.6 "Blind")        */
   int32_t n_scalars;             /* 4 or 8; 16 under the terrain rules       */
   int32_t hidden;                /* H in {32, 64, 128}                       */
   int32_t n_actions;             /* A in {6, 9}; 7 under the paper rules     */

@@ -139,7 +139,8 @@ typedef struct {
   int32_t side;        /* L: the grid is L x L and toroidal              */
   int32_t slots;       /* S: agent slots (alive or free)                 */
   int32_t init_alive;  /* K: agents placed at reset                      */
-  int32_t patch_k;     /* k: odd side of the egocentric patch            */
+  int32_t patch_k;     /* k: odd side of the egocentric patch; 0 = no     */
+                       /* vision sensor ("Blind", App. F.6)               */
   int32_t n_scalars;   /* 4 (energy + 3 zeros) or 8 (+ facing one-hot)   */
   int32_t hidden;      /* H                                              */
   int32_t n_actions;   /* A: 6 or 9                                      */
@@ -299,7 +300,8 @@ static void shape_of(const orc_config *c, orc_shape *s) {
   s->A = c->n_actions;
   if (c->policy_form == ORC_PAPER_FORM) {
     s->L = c->n_hidden;
-    s->ns = c->n_scalars >= 8 ? 3 : 2;
+    /* sensors: vision (when there is a patch), compass (8+ scalars), internal */
+    s->ns = (c->patch_k > 0 ? 1 : 0) + (c->n_scalars >= 8 ? 1 : 0) + 1;
     s->relu = 1;
     s->out_bias = 0;
     s->temp = 1;

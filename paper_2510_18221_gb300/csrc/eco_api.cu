@@ -86,7 +86,8 @@ static int validate(const eco_config *c, char *msg, size_t n) {
   if (c->n_envs < 1 || c->n_envs > 4096) return snprintf(msg, n, "n_envs out of range"), ECO_EINVAL;
   if (!c->env_side || !c->env_slots || !c->env_init_alive || !c->env_seed)
     return snprintf(msg, n, "null per-environment array"), ECO_EINVAL;
-  if (c->patch_k < 1 || (c->patch_k & 1) == 0 || c->patch_k > 31) return snprintf(msg, n, "patch_k must be odd in [1, 31]"), ECO_EINVAL;
+  if (c->patch_k < 0 || (c->patch_k > 0 && (c->patch_k & 1) == 0) || c->patch_k > 31)
+    return snprintf(msg, n, "patch_k must be 0 (no vision) or odd in [1, 31]"), ECO_EINVAL;
   const bool terrain = c->rules == ECO_RULES_TERRAIN;
   if (terrain ? c->n_scalars != 16 : (c->n_scalars != 4 && c->n_scalars != 8))
     return snprintf(msg, n, "n_scalars must be 4 or 8 (16 under the terrain rules)"), ECO_EINVAL;
@@ -130,9 +131,6 @@ static int validate(const eco_config *c, char *msg, size_t n) {
     if (c->w_child > c->w_cap || c->b_child > c->b_cap)
       return snprintf(msg, n, "a child's water and biomass must fit its capacities"), ECO_EINVAL;
   }
-  const int nch = terrain ? 4 : 3;
-  if (nch * c->patch_k * c->patch_k + c->n_scalars < c->hidden)
-    return snprintf(msg, n, "observation smaller than the hidden width"), ECO_EINVAL;
   if (c->policy_variant < -1 || c->policy_variant > policy_variant_count())
     return snprintf(msg, n, "policy_variant out of range"), ECO_EINVAL;
   long long cells = 0, slots = 0;
@@ -163,7 +161,8 @@ static Layout make_layout(const eco_config *c) {
   L.n_scalars = c->n_scalars;
   if (c->policy_form == ECO_POLICY_PAPER) {
     L.L = c->n_hidden;
-    L.ns = c->n_scalars >= 8 ? 3 : 2;  // vision, internal (+ compass)
+    // sensors: vision (when there is a patch), compass (8+ scalars), internal
+    L.ns = (c->patch_k > 0 ? 1 : 0) + (c->n_scalars >= 8 ? 1 : 0) + 1;
     L.relu = 1;
     L.out_bias = 0;
     L.temp = 1;

@@ -731,8 +731,11 @@ __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0,
   }
 }
 
+// Shared memory of the mutation: a tile of kMutRows rows of nin + 1 floats,
+// where nin is D for W_in and H for the hidden layers (D may be below H: an
+// agent without a vision sensor), or the head's A x H rows.
 size_t mutate_smem_bytes(const Layout &L) {
-  const size_t tile = (size_t)kMutRows * (L.D + 1);
+  const size_t tile = (size_t)kMutRows * ((L.D > L.H ? L.D : L.H) + 1);
   const size_t head = (size_t)L.A * L.H;
   return 4 * (tile > head ? tile : head);
 }

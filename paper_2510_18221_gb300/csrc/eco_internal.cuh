@@ -232,7 +232,7 @@ __host__ __device__ __forceinline__ int layout_logical(const Layout &L, int q) {
 // paper form; D for W_in in the plain form; H for hidden layers and the head.
 __host__ __device__ __forceinline__ int layout_fan_in(const Layout &L, int q) {
   if (q >= L.D * L.H) return L.H;
-  if (L.ns == 1) return L.D;
+  if (!L.relu) return L.D;  // the plain (tanh) form: one input layer over all of x
   const int j = q / L.H;
   if (j < L.patch) return L.patch;
   if (L.n_scalars >= 8 && j >= L.patch + 1 && j < L.patch + 5) return 4;

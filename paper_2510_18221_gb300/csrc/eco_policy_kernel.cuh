@@ -263,7 +263,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
   const int n_alive = d.counters[CNT_N_ALIVE];
   const uint32_t t = (uint32_t)d.step[0];
   const int k = R.patch_k, RR = k >> 1, kk = k * k;
-  const uint32_t kdiv = 0xFFFFFFFFu / (uint32_t)k + 1u;  // ceil(2^32 / k), k odd
+  // ceil(2^32 / k) for odd k (k = 0: no patch, the gather loop is empty)
+  const uint32_t kdiv = k > 0 ? 0xFFFFFFFFu / (uint32_t)k + 1u : 0u;
   const bool rotate = (R.flags & F_ROTATE_OBS) != 0;
   const bool greedy = (R.flags & F_GREEDY) != 0;
 

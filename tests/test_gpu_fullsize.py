@@ -146,3 +146,17 @@ def test_terrain_workload_lockstep():
     rep = _lockstep(workloads.get("terrain"), 3, sample=256)
     assert rep["steps"] == 3
     print("terrain paper-scale lock-step:", rep)
+
+
+@pytest.mark.skipif(not LONG, reason="long lock-step runs only with ECO_LONG=1")
+@pytest.mark.parametrize("base,over", [
+    ("ecology", dict(e_init=60, e_repro=50, e_child=20)),
+    ("terrain", dict(e_init=80, e_repro=50, e_child=25, b_child=5, b_bite=10, w_init=12,
+                     w_child=5, attack_damage=10)),
+])
+def test_long_rule_sets_300_steps(base, over):
+    """300 lock-step steps of the paper rules (RGB vision, paper form) and of
+    the terrain rules on a 128x128 world, 2,048 slots, 1,500 founders."""
+    rep = _lockstep(workloads.scaled(base, 128, 2048, 1500, **over), 300, sample=128)
+    assert rep["steps"] == 300
+    print("%s 300-step lock-step:" % base, rep)

@@ -429,3 +429,19 @@ def test_input_sparse_variants_on_dense_inputs(base):
         w = workloads.scaled(base, 64, 600, 450, e_init=190, precision="fp8")
     for v in (7, 8):
         _run(w, 5, policy_variant=v)
+
+
+@pytest.mark.parametrize("base,over", [
+    ("mid", dict(e_init=190, precision="bf16")),
+    ("paperform", dict(e_init=190, precision="fp8")),
+    ("paperform", dict(e_init=190, n_scalars=4, precision="bf16")),
+    ("ecology", dict(e_init=60, e_repro=50, e_child=20, precision="bf16")),
+    ("terrain", dict(e_init=80, e_repro=50, e_child=25, b_child=5, b_bite=10, w_init=12,
+                     w_child=5, attack_damage=10, precision="bf16")),
+])
+def test_blind_agents(base, over):
+    """Agents without a vision sensor (App. F.6 "Blind"; the paper's R / RC
+    agents): the observation is the scalars alone, so D is below H."""
+    w = workloads.scaled(base, 64, 600, 450, patch_k=0, **over)
+    rep = _run(w, 12)
+    assert rep["steps"] == 12

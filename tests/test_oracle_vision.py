@@ -13,6 +13,10 @@
   clamp keeps every channel in [0, 1] with about half the mass of a
   parent at 1 landing exactly on 1; a child born in the world carries
   mutate_colour of its parent's colour.
+* Blind agents (App. F.6; the R and RC agents of the main experiments):
+  the observation is the scalars alone, and the paper form has the compass
+  and internal sensors only -- the parameter count of App. F.5's form with
+  their sensor count, Kaiming fan-ins 4 and n_scalars - 4, zero biases.
 """
 import math
 import os
@@ -192,3 +196,42 @@ def test_colours_stay_in_range_over_a_run():
         alive = o.alive == 1
         assert ((o.colour[alive] >= 0) & (o.colour[alive] <= 1)).all()
     assert births > 0
+
+
+# ----------------------------------------------------------------------------- blind agents
+
+@pytest.mark.parametrize("n_scalars", [4, 8])
+def test_blind_observation_is_the_scalars(n_scalars):
+    """App. F.6 "Blind" (the R / RC agents of the main experiments): no
+    vision sensor, so the observation is the scalars alone."""
+    o = scenarios.empty_world(scenarios.tiny_cfg(side=5, patch_k=0, n_scalars=n_scalars))
+    place(o, 0, 2, 2, facing=3, energy=150)
+    o.food[cell(o, 2, 1)] = 1
+    x = o.observe(0)
+    want = [150 / 200] + ([0, 0, 0, 1] if n_scalars == 8 else []) + [0, 0, 0]
+    np.testing.assert_array_equal(x, np.array(want, np.float64))
+
+
+@pytest.mark.parametrize("n_scalars,L,H", [(8, 2, 64), (4, 2, 64), (8, 1, 32), (8, 3, 128)])
+def test_blind_paper_form_sensors_and_count(n_scalars, L, H):
+    """Without a vision sensor the paper form has the compass (8 scalars)
+    and the internal sensor: L(H^2+H) + H(D + n_sensors + A) + 1 parameters
+    (the form of App. F.5's table), and Kaiming fan-ins of 4 and
+    n_scalars - 4 (or n_scalars)."""
+    w = workloads.scaled("paperform", 32, 64, 40, patch_k=0, n_scalars=n_scalars,
+                         n_hidden=L, hidden=H)
+    o = oracle.Oracle(w)
+    ns = 2 if n_scalars == 8 else 1
+    A = w["n_actions"]
+    assert o.D == n_scalars
+    assert o.P == L * (H * H + H) + H * (n_scalars + ns + A) + 1
+    rows = np.array([o.init_params(s) for s in range(40)], np.float64)
+    w_in = rows[:, :H * n_scalars].reshape(40, H, n_scalars)
+    if n_scalars == 8:
+        compass = w_in[:, :, 1:5].ravel()
+        internal = np.concatenate([w_in[:, :, :1].ravel(), w_in[:, :, 5:].ravel()])
+        assert scipy.stats.kstest(compass / np.sqrt(2.0 / 4), "norm").pvalue > 1e-3
+        assert scipy.stats.kstest(internal / np.sqrt(2.0 / 4), "norm").pvalue > 1e-3
+    else:
+        assert scipy.stats.kstest(w_in.ravel() / np.sqrt(2.0 / 4), "norm").pvalue > 1e-3
+    assert not rows[:, H * n_scalars:H * n_scalars + ns * H].any()   # sensor biases zero
