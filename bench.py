@@ -357,6 +357,7 @@ def main():
     e_agent_steps = int(tot[:, 1].sum()) - agent_steps_of(e0)
     d2h = tot.nbytes + last.nbytes
     variant_name = eco.eco_policy_variant_name(env.variants()[1])
+    sparse_forced = variant_name.startswith("input-sparse")
     launch_mode, launch_blocks = env.launch_mode()
     env.close()
     del env
@@ -467,15 +468,19 @@ def main():
                                if launch_mode == 0 else "one kernel per phase"),
             },
             "roofline": {
-                "bound": "hbm", "kernel": "k_policy", "achieved": achieved,
+                "bound": "hbm", "kernel": "k_policy",
+                # a forced input-sparse variant reads only some W_in rows, so
+                # the dense byte count gives no roofline fraction for it
+                "achieved": None if sparse_forced else achieved,
                 "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                "frac": achieved / float(peaks["hbm_gbs"]),
+                "frac": None if sparse_forced else achieved / float(peaks["hbm_gbs"]),
+                "effective_gbs": achieved if sparse_forced else None,
                 "peak_kind": "%s copy bandwidth" % peak_kind,
                 "bytes_per_agent": per_agent_bytes,
                 "policy_ms_per_step": policy_ms / max(1, n_timed),
                 "policy_share_of_step": policy_ms / ms if ms > 0 else None,
                 "traffic": (traffic["dram_bytes_per_agent"] * agent_steps / max(1, args.steps * world))
-                           if traffic else None,
+                           if traffic and not sparse_forced else None,
                 "traffic_source": traffic["source"] if traffic else None,
             },
             "e2e": {"value": e_agent_steps / e_el, "unit": UNIT, "h2d_bytes_per_step": 0,
