@@ -20,6 +20,7 @@ using namespace eco;
 static_assert((int)ECO_STAT_ACT0 == (int)eco::ST_ACT0, "stat enum");
 static_assert((int)ECO_STAT_ENERGY_TOTAL == (int)eco::ST_ENERGY_TOTAL, "stat enum");
 static_assert((int)ECO_N_STATS == (int)eco::N_ST, "stat enum");
+static_assert(sizeof(eco_stats) == sizeof(long long) * eco::N_ST, "stat record");
 
 static char g_err[512] = "";
 
@@ -51,6 +52,10 @@ struct eco_handle {
   cudaEvent_t ev_dummy[2];
   std::vector<cudaEvent_t> ev_pool;  // pairs
   int ev_used;
+  // pinned host mirror of [stats_total, stats_last, counters], contiguous
+  // in the workspace: eco_read_stats reads it with one copy
+  uint8_t *rd_host;
+  size_t rd_bytes;
   char err[512];
 };
 
@@ -249,7 +254,6 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.alive_list = k.take<int32_t>(slots);
   D.tile_counts = k.take<int32_t>(compact_tiles((int)slots));
   D.barrier = k.take<unsigned>(2);
-  D.counters = k.take<int32_t>(CNT_N);
   D.births = k.take<int2>(slots);
   D.free_list = k.take<int32_t>(slots);
   D.bflag = k.take<uint8_t>(slots);
@@ -258,6 +262,9 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.stats_step = k.take<long long>((size_t)E * N_ST);
   D.stats_total = k.take<long long>((size_t)E * N_ST);
   D.stats_last = k.take<long long>((size_t)E * N_ST);
+  // the counters (with the status word) follow the statistics, so that one
+  // copy brings both to the host
+  D.counters = k.take<int32_t>(CNT_N);
   D.step = k.take<long long>(1);
   D.hist = k.take<uint32_t>((size_t)E * 65536);
   D.place_prefix = k.take<unsigned long long>(E);
@@ -408,6 +415,9 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
   h->graph_src = nullptr;
   h->ev_used = 0;
   h->err[0] = 0;
+  h->rd_bytes = (size_t)(reinterpret_cast<uint8_t *>(h->d.counters + CNT_N) -
+                         reinterpret_cast<uint8_t *>(h->d.stats_total));
+  h->rd_host = nullptr;
   // zero the whole workspace first, then install the environment table
   cudaError_t e = cudaMemsetAsync(h->ws, 0, need, h->stream);
   if (e == cudaSuccess)
@@ -415,11 +425,13 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
                         cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = launch_init_static(h->d, h->grid, h->stream);
   if (e == cudaSuccess) e = env_prepare(h->L, &h->grid);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->rd_host, h->rd_bytes);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[1]);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     int r = fail(nullptr, ECO_ECUDA, "create: %s", cudaGetErrorString(e));
+    if (h->rd_host) cudaFreeHost(h->rd_host);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
     return r;
@@ -444,6 +456,7 @@ extern "C" void eco_destroy(eco_handle *h) {
   for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
   if (h->ev_dummy[0]) cudaEventDestroy(h->ev_dummy[0]);
   if (h->ev_dummy[1]) cudaEventDestroy(h->ev_dummy[1]);
+  if (h->rd_host) cudaFreeHost(h->rd_host);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -658,11 +671,21 @@ extern "C" int eco_policy_bytes(eco_handle *h, int64_t *bytes, int64_t *n_alive)
 extern "C" int eco_read_stats(eco_handle *h, eco_stats *total, eco_stats *last, int32_t n_envs) {
   if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
   if (n_envs < 0 || n_envs > h->n_envs) return fail(h, ECO_EINVAL, "n_envs out of range");
-  if (total)
-    CUDA_TRY(h, cudaMemcpyAsync(total, h->d.stats_total, sizeof(eco_stats) * n_envs, cudaMemcpyDeviceToHost, h->stream));
-  if (last)
-    CUDA_TRY(h, cudaMemcpyAsync(last, h->d.stats_last, sizeof(eco_stats) * n_envs, cudaMemcpyDeviceToHost, h->stream));
-  return check_status(h);
+  // one asynchronous copy of the statistics and the status word into pinned
+  // memory, one synchronisation, then host-side copies
+  CUDA_TRY(h, cudaMemcpyAsync(h->rd_host, h->d.stats_total, h->rd_bytes, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  const uint8_t *base = reinterpret_cast<const uint8_t *>(h->d.stats_total);
+  auto mirror = [&](const void *dev) {
+    return h->rd_host + (reinterpret_cast<const uint8_t *>(dev) - base);
+  };
+  if (total) memcpy(total, mirror(h->d.stats_total), sizeof(eco_stats) * n_envs);
+  if (last) memcpy(last, mirror(h->d.stats_last), sizeof(eco_stats) * n_envs);
+  int32_t st = 0;
+  memcpy(&st, mirror(h->d.counters + CNT_STATUS), sizeof st);
+  if (st & 3) return fail(h, ECO_EINVAL, "reset: fewer non-wall cells than founders (status %d)", st);
+  if (st & 4) return fail(h, ECO_ETIMEOUT, "a device-side wait ran out of its budget");
+  return ECO_OK;
 }
 
 // ---------------------------------------------------------------------------
