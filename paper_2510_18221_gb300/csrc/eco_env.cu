@@ -29,48 +29,6 @@
 
 namespace eco {
 
-// ---------------------------------------------------------------------------
-// Statistics.  Phases add their counts to a per-CTA table in shared memory
-// (warp-aggregated first: lanes with the same key combine, one shared
-// atomic per key and warp); a kernel flushes the table to the step record
-// once, with one global atomic per nonzero entry.  A step then costs a few
-// hundred global atomics per counter in place of one per warp and event,
-// which would serialise on the few L2 lines that hold the record.  Worlds
-// past the first kStatSmemEnvs add straight to the global record.
-// Integer adds commute, so totals do not depend on the order.
-// ---------------------------------------------------------------------------
-constexpr int kStatSmemEnvs = 8;
-__shared__ unsigned long long s_stat[kStatSmemEnvs * N_ST];
-
-__device__ __forceinline__ void stat_begin() {
-  for (int i = threadIdx.x; i < kStatSmemEnvs * N_ST; i += blockDim.x) s_stat[i] = 0ull;
-  __syncthreads();
-}
-
-// The per-warp partial sum must fit in 32 bits (every counter here does).
-__device__ __forceinline__ void stat_add(const Dev &d, int env, int idx, int v) {
-  const unsigned active = __activemask();
-  const int key = env * N_ST + idx;
-  const unsigned peers = __match_any_sync(active, key);
-  const int tot = __reduce_add_sync(peers, v);
-  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1 && tot != 0) {
-    const unsigned long long u = (unsigned long long)(long long)tot;
-    if (env < kStatSmemEnvs)
-      atomicAdd(&s_stat[key], u);
-    else
-      atomicAdd((unsigned long long *)&d.stats_step[key], u);
-  }
-}
-
-__device__ __forceinline__ void stat_flush(const Dev &d) {
-  __syncthreads();
-  const int n = min(d.n_envs, kStatSmemEnvs) * N_ST;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const unsigned long long v = s_stat[i];
-    if (v) atomicAdd((unsigned long long *)&d.stats_step[i], v);
-  }
-}
-
 int grid_for(long long n, int threads, int max_blocks) {
   long long b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -168,12 +126,6 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
     const EnvDesc ed = d.env[e];
     const int tc = d.tgt[slot];
     int pos = d.pos[slot];
-    const int a = d.act[slot];
-    // the action histogram, and the moves the policy phase found blocked by
-    // a wall or an agent (a move action left without a target)
-    stat_add(d, e, ST_ACT0 + a, 1);
-    const bool move_act = R.rules != RULES_SIMPLE ? a == PA_FORWARD : (a >= ACT_N && a <= ACT_W);
-    if (move_act && tc < 0) stat_add(d, e, ST_MOVE_BLOCKED, 1);
     if (tc >= 0) {
       const int gc = ed.cell_off + tc;
       bool won = claim_local_slot(d.claim_move[gc]) == slot - ed.slot_off;
@@ -186,11 +138,12 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
         d.cellf[gc] |= (uint8_t)CELL_AGENT;
         d.pos[slot] = tc;
         pos = tc;
-        stat_add(d, e, ST_MOVES, 1);
+        stat_add(d.stats_step, e, ST_MOVES, 1);
       } else {
-        stat_add(d, e, ST_MOVE_LOST, 1);
+        stat_add(d.stats_step, e, ST_MOVE_LOST, 1);
       }
     }
+    const int a = d.act[slot];
     if (R.rules == RULES_TERRAIN && (a == TA_DRINK || a == TA_EAT_BIO)) {
       // terrain rules: drink or eat biomass, min(bite, on the cell, room)
       const int gpos = ed.cell_off + pos;
@@ -200,7 +153,7 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
         if (sip > 0) {
           d.water[gpos] = w - sip;
           d.a_water[slot] += sip;
-          stat_add(d, e, ST_DRUNK, sip);
+          stat_add(d.stats_step, e, ST_DRUNK, sip);
         }
       } else {
         const int b = d.bio[gpos];
@@ -208,7 +161,7 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
         if (bite > 0) {
           d.bio[gpos] = b - bite;
           d.a_bio[slot] += bite;
-          stat_add(d, e, ST_BIO_EATEN, bite);
+          stat_add(d.stats_step, e, ST_BIO_EATEN, bite);
         }
       }
     } else if (R.rules != RULES_SIMPLE) {
@@ -220,11 +173,11 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
         if (bite > 0) {
           d.res[gpos] = r - bite;
           d.energy[slot] += bite;
-          stat_add(d, e, ST_EATEN, 1);
-          stat_add(d, e, ST_EATEN_ENERGY, bite);
+          stat_add(d.stats_step, e, ST_EATEN, 1);
+          stat_add(d.stats_step, e, ST_EATEN_ENERGY, bite);
           if (r == bite) {
             d.cellf[gpos] &= (uint8_t)~CELL_FOOD;
-            stat_add(d, e, ST_FOOD_EMPTIED, 1);
+            stat_add(d.stats_step, e, ST_FOOD_EMPTIED, 1);
           }
         }
       }
@@ -234,7 +187,7 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
       if (cf & CELL_FOOD) {
         d.cellf[gpos] = (uint8_t)(cf & ~CELL_FOOD);
         d.energy[slot] += R.e_food;
-        stat_add(d, e, ST_EATEN, 1);
+        stat_add(d.stats_step, e, ST_EATEN, 1);
       }
     }
     // simple rules: the post-eat energy, which attack transfers are computed
@@ -279,8 +232,8 @@ __device__ void ph_attack_claim(const Dev &d, const Rules &R, int g0, int gs, in
             }
           }
         }
-        stat_add(d, e, ST_ATTACK_HITS, hits);
-        stat_add(d, e, ST_DAMAGE, hits * R.attack_damage);
+        stat_add(d.stats_step, e, ST_ATTACK_HITS, hits);
+        stat_add(d.stats_step, e, ST_DAMAGE, hits * R.attack_damage);
       }
     } else if (d.act[slot] == ACT_ATTACK) {
       const int c = step_cell(d.pos[slot], d.facing[slot], ed.side);
@@ -350,18 +303,18 @@ __device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int s
       const int ab = d.a_bio[slot];
       d.bio[gpos] += ab;
       d.a_bio[slot] = 0;
-      stat_add(d, e, ST_DEAD_WATER, aw);
-      stat_add(d, e, ST_DEAD_BIO, ab);
+      stat_add(d.stats_step, e, ST_DEAD_WATER, aw);
+      stat_add(d.stats_step, e, ST_DEAD_BIO, ab);
       aw = 0;
     }
     d.water[gpos] += back;
     d.a_water[slot] = aw;
-    stat_add(d, e, ST_WATER_SPENT, spent);
-    stat_add(d, e, ST_THIRSTY, thirsty);
+    stat_add(d.stats_step, e, ST_WATER_SPENT, spent);
+    stat_add(d.stats_step, e, ST_THIRSTY, thirsty);
   }
-  stat_add(d, e, ST_METAB_PAID, paid);
-  stat_add(d, e, ST_STARVED, starved);
-  stat_add(d, e, ST_HEALS, healed);
+  stat_add(d.stats_step, e, ST_METAB_PAID, paid);
+  stat_add(d.stats_step, e, ST_STARVED, starved);
+  stat_add(d.stats_step, e, ST_HEALS, healed);
   if (hp <= 0) {
     uint8_t cf = (uint8_t)(d.cellf[gpos] & ~CELL_AGENT);
     if (en > 0) {
@@ -369,14 +322,14 @@ __device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int s
       d.res[gpos] = r + en;
       if (r == 0) {
         cf |= (uint8_t)CELL_FOOD;
-        stat_add(d, e, ST_FOOD_REFILLED, 1);
+        stat_add(d.stats_step, e, ST_FOOD_REFILLED, 1);
       }
     }
     d.cellf[gpos] = cf;
     d.occ[gpos] = -1;
     d.alive[slot] = 0;
-    stat_add(d, e, ST_DEATHS, 1);
-    stat_add(d, e, ST_DEAD_ENERGY, en);
+    stat_add(d.stats_step, e, ST_DEATHS, 1);
+    stat_add(d.stats_step, e, ST_DEAD_ENERGY, en);
     en = 0;
     hp = 0;
   } else {
@@ -407,8 +360,8 @@ __device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs, int
     const int v = d.tgt[slot];
     if (v >= 0 && claim_local_slot(d.claim_att[v]) == slot - d.env[e].slot_off) {
       g = (int)(((long long)d.gain[v] * R.attack_num) / R.attack_den);
-      stat_add(d, e, ST_ATTACK_HITS, 1);
-      stat_add(d, e, ST_ENERGY_TRANSFERRED, g);
+      stat_add(d.stats_step, e, ST_ATTACK_HITS, 1);
+      stat_add(d.stats_step, e, ST_ENERGY_TRANSFERRED, g);
     }
     en = en - loss + g - R.e_metab;
     if (en <= 0) {
@@ -416,8 +369,8 @@ __device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs, int
       d.alive[slot] = 0;
       d.occ[gpos] = -1;
       d.cellf[gpos] &= (uint8_t)~CELL_AGENT;
-      stat_add(d, e, ST_DEATHS, 1);
-      stat_add(d, e, ST_DEAD_ENERGY, en);
+      stat_add(d.stats_step, e, ST_DEATHS, 1);
+      stat_add(d.stats_step, e, ST_DEAD_ENERGY, en);
       en = 0;
     }
     d.energy[slot] = en;
@@ -836,11 +789,11 @@ __device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs) {
         d.res[c] = r + (int)gain;
         grew += gain;
       }
-      stat_add(d, e, ST_FOOD_REFILLED, refilled);
-      stat_add(d, e, ST_PHOTO, (int)grew);
+      stat_add(d.stats_step, e, ST_FOOD_REFILLED, refilled);
+      stat_add(d.stats_step, e, ST_PHOTO, (int)grew);
     }
     if (changed) reinterpret_cast<uchar4 *>(d.cellf)[g] = cf;
-    stat_add(d, e, ST_REGROWN, grown);
+    stat_add(d.stats_step, e, ST_REGROWN, grown);
   }
 }
 
@@ -897,7 +850,7 @@ __device__ void ph_flow_in(const Dev &d, int g0, int gs) {
 
 // A13: fold this step's counters into the per-environment records and
 // advance the step counter (one CTA).  Agent-steps and attacks come from the
-// action histogram counted in the move phase.
+// action histogram the policy kernel counted.
 __device__ void ph_finish(const Dev &d, const Rules &R) {
   const long long t = d.step[0];
   for (int i = threadIdx.x; i < d.n_envs; i += blockDim.x) {
@@ -968,21 +921,9 @@ __global__ void __launch_bounds__(256) k_compact_scatter(Dev d) {
   __shared__ int sh[33];
   ph_compact_scatter(d, blockIdx.x, gridDim.x, sh);
 }
-__global__ void k_move_apply_eat(Dev d, Rules R, int A) {
-  stat_begin();
-  ph_move_apply_eat(d, R, A, GRID_ARGS, -1);
-  stat_flush(d);
-}
-__global__ void k_attack_claim(Dev d, Rules R) {
-  stat_begin();
-  ph_attack_claim(d, R, GRID_ARGS, -1);
-  stat_flush(d);
-}
-__global__ void k_metab_death(Dev d, Rules R) {
-  stat_begin();
-  ph_metab_death(d, R, GRID_ARGS, -1);
-  stat_flush(d);
-}
+__global__ void k_move_apply_eat(Dev d, Rules R, int A) { ph_move_apply_eat(d, R, A, GRID_ARGS, -1); }
+__global__ void k_attack_claim(Dev d, Rules R) { ph_attack_claim(d, R, GRID_ARGS, -1); }
+__global__ void k_metab_death(Dev d, Rules R) { ph_metab_death(d, R, GRID_ARGS, -1); }
 __global__ void k_birth_claim(Dev d, Rules R) { ph_birth_claim(d, R, GRID_ARGS, -1); }
 __global__ void __launch_bounds__(1024) k_birth_assign(Dev d, Rules R) {
   __shared__ BirthSmem S;
@@ -993,11 +934,7 @@ __global__ void __launch_bounds__(256) k_mutate(Dev d, Layout L, Rules R) {
   __shared__ float s_scale[kMutRows];
   ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale);
 }
-__global__ void k_regrow(Dev d, Rules R) {
-  stat_begin();
-  ph_regrow(d, R, GRID_ARGS);
-  stat_flush(d);
-}
+__global__ void k_regrow(Dev d, Rules R) { ph_regrow(d, R, GRID_ARGS); }
 __global__ void k_flow_out(Dev d) { ph_flow_out(d, GRID_ARGS); }
 __global__ void k_flow_in(Dev d) { ph_flow_in(d, GRID_ARGS); }
 __global__ void k_finish(Dev d, Rules R) { ph_finish(d, R); }
@@ -1052,7 +989,6 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   const int g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   // each thread's first alive-list entry, loaded once for all phases
   const int first = g0 < d.counters[CNT_N_ALIVE] ? d.alive_list[g0] : -1;
-  stat_begin();
   ph_move_apply_eat(d, R, L.A, g0, gs, first);
   if (!grid_sync(d, nb, &s_flag)) return;
   ph_attack_claim(d, R, g0, gs, first);
@@ -1070,8 +1006,6 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   if (!grid_sync(d, nb, &s_flag)) return;
   ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale);
   ph_compact_count(d, blockIdx.x, gridDim.x, S.sh);
-  // every count of the step is in; the last CTA's finish reads them
-  stat_flush(d);
   if (!grid_sync(d, nb, &s_flag)) return;
   if (R.rules == RULES_TERRAIN) ph_flow_in(d, g0, gs);
   ph_compact_scatter(d, blockIdx.x, gridDim.x, S.sh);

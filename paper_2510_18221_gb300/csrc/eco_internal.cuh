@@ -408,6 +408,19 @@ __device__ __forceinline__ int claim_local_slot(unsigned long long key) {
   return (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
 }
 
+// Warp-aggregated add of v to stats[env][idx]: lanes with the same
+// (env, idx) combine before one 64-bit atomic.  Integer adds commute, so
+// totals do not depend on thread order.  The per-warp partial sum must fit
+// in 32 bits (every counter here does).
+__device__ __forceinline__ void stat_add(long long *stats, int env, int idx, int v) {
+  const unsigned active = __activemask();
+  const int key = env * N_ST + idx;
+  const unsigned peers = __match_any_sync(active, key);
+  const int tot = __reduce_add_sync(peers, v);
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1 && tot != 0)
+    atomicAdd((unsigned long long *)&stats[key], (unsigned long long)(long long)tot);
+}
+
 // Find the environment of a global cell (environments are sorted by cell
 // offset; a short binary search).
 __device__ __forceinline__ int env_of_cell(const EnvDesc *env, int n_envs, int cell) {

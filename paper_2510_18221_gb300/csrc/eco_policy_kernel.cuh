@@ -38,29 +38,12 @@
 
 namespace eco {
 
-constexpr bool kPrefetchL2 = true;
-constexpr bool kStreamEvictFirst = true;
-
 __device__ __forceinline__ uint4 ldg_stream(const uint4 *p) {
   uint4 r;
-  if constexpr (kStreamEvictFirst) {
-    uint64_t pol;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "l"(p), "l"(pol));
-  } else {
-    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
-        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "l"(p));
-  }
+  asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p));
   return r;
-}
-
-// Asynchronous prefetch of [p, p + bytes) into L2 (p and bytes multiples of
-// 16); issued by one lane, it returns at once.
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // Two FP32 fused multiply-adds in one instruction (Blackwell's packed FP32
@@ -125,36 +108,19 @@ struct Unit<PREC_BF16> {
   }
 };
 
-// Four e4m3 codes (byte i = element i) to four floats, exactly: the word is
-// split into its two 16-bit halves once, each half widened to two halves
-// (f16, which holds every e4m3 value) and each half to FP32.
-__device__ __forceinline__ void e4m3x4(uint32_t w, float &f0, float &f1, float &f2, float &f3) {
-  uint32_t h01, h23;
-  asm("{\n\t.reg .b16 lo, hi;\n\t"
-      "mov.b32 {lo, hi}, %2;\n\t"
-      "cvt.rn.f16x2.e4m3x2 %0, lo;\n\t"
-      "cvt.rn.f16x2.e4m3x2 %1, hi;\n\t}"
-      : "=r"(h01), "=r"(h23)
-      : "r"(w));
-  asm("{\n\t.reg .b16 a, b, c, d;\n\t"
-      "mov.b32 {a, b}, %4;\n\t"
-      "mov.b32 {c, d}, %5;\n\t"
-      "cvt.f32.f16 %0, a;\n\t"
-      "cvt.f32.f16 %1, b;\n\t"
-      "cvt.f32.f16 %2, c;\n\t"
-      "cvt.f32.f16 %3, d;\n\t}"
-      : "=f"(f0), "=f"(f1), "=f"(f2), "=f"(f3)
-      : "r"(h01), "r"(h23));
+// Two e4m3 codes (low byte = first element) to two floats, exactly.
+__device__ __forceinline__ float2 e4m3x2(uint32_t two) {
+  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(two & 0xFFFFu), __NV_E4M3);
+  return __half22float2(*reinterpret_cast<const __half2 *>(&h));
 }
 
 template <>
 struct Unit<PREC_FP8> {
   static constexpr int E = 16;
   __device__ __forceinline__ static void fma4(float *acc, uint32_t w, float x) {
-    float w0, w1, w2, w3;
-    e4m3x4(w, w0, w1, w2, w3);
-    ffma2(acc[0], acc[1], w0, w1, x);
-    ffma2(acc[2], acc[3], w2, w3, x);
+    const float2 a = e4m3x2(w), b = e4m3x2(w >> 16);
+    ffma2(acc[0], acc[1], a.x, a.y, x);
+    ffma2(acc[2], acc[3], b.x, b.y, x);
   }
   __device__ __forceinline__ static void fma(float *acc, const uint4 &v, float x) {
     fma4(acc + 0, v.x, x);
@@ -163,13 +129,12 @@ struct Unit<PREC_FP8> {
     fma4(acc + 12, v.w, x);
   }
   __device__ __forceinline__ static float dot4(uint32_t w, const float *h, float s) {
-    float w0, w1, w2, w3;
-    e4m3x4(w, w0, w1, w2, w3);
+    const float2 a = e4m3x2(w), b = e4m3x2(w >> 16);
     const float4 x = *reinterpret_cast<const float4 *>(h);
-    s = fmaf(w0, x.x, s);
-    s = fmaf(w1, x.y, s);
-    s = fmaf(w2, x.z, s);
-    s = fmaf(w3, x.w, s);
+    s = fmaf(a.x, x.x, s);
+    s = fmaf(a.y, x.y, s);
+    s = fmaf(b.x, x.z, s);
+    s = fmaf(b.y, x.w, s);
     return s;
   }
   __device__ __forceinline__ static float dot(const uint4 &v, const float *h) {
@@ -205,8 +170,7 @@ __device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int 
                                                const float *__restrict__ bias, int nbias,
                                                const float *__restrict__ scale,
                                                float *__restrict__ out, int lane, int relu,
-                                               const short *__restrict__ idx,
-                                               const void *pf = nullptr, uint32_t pf_bytes = 0) {
+                                               const short *__restrict__ idx) {
   constexpr int E = Unit<PREC>::E;
   constexpr int UPJ = H / E;  // units per input
   constexpr int LG = Log2<UPJ>::v;
@@ -215,15 +179,8 @@ __device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int 
 #pragma unroll
   for (int e = 0; e < E; ++e) acc[e] = 0.0f;
   const int U = n_in * UPJ;
-  // lane 0 prefetches what the warp streams next (pf) into L2 two batches
-  // before this layer's stream ends, so that its first loads hit L2
-  const int pf_at = (pf != nullptr && lane == 0) ? U - 2 * 32 * UNROLL : 0x7FFFFFFF;
   int u = lane;
   for (; u + 32 * (UNROLL - 1) < U; u += 32 * UNROLL) {
-    if (kPrefetchL2 && u >= pf_at) {
-      prefetch_l2(pf, pf_bytes);
-      pf = nullptr;
-    }
     uint4 v[UNROLL];
     int j[UNROLL];
 #pragma unroll
@@ -240,7 +197,6 @@ __device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int 
 #pragma unroll
     for (int k = 0; k < UNROLL; ++k) Unit<PREC>::fma(acc, v[k], x[j[k]]);
   }
-  if (kPrefetchL2 && pf != nullptr && lane == 0) prefetch_l2(pf, pf_bytes);
   for (; u < U; u += 32) {
     if constexpr (SPARSE) {
       const int jj = idx[u >> LG];
@@ -312,18 +268,23 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
   const bool rotate = (R.flags & F_ROTATE_OBS) != 0;
   const bool greedy = (R.flags & F_GREEDY) != 0;
 
-  const int first = blockIdx.x * WARPS + warp, G = gridDim.x * WARPS;
-  // the first kPrefetchFirst bytes of an agent's weight block are
-  // prefetched into L2 before its observation is gathered (the first agent)
-  // or while the previous agent's head runs (the others)
-  constexpr uint32_t kPrefetchFirst = 4096;
-  const uint32_t pf_first = (uint32_t)min((int64_t)kPrefetchFirst, (int64_t)L.off_w2);
-  if (kPrefetchL2 && lane == 0 && first < n_alive)
-    prefetch_l2(d.wq + (int64_t)d.alive_list[first] * L.stride, pf_first);
-  for (int i = first; i < n_alive; i += G) {
+  // Per-warp counters, flushed when the environment changes: lane a < 16
+  // counts action a, lane 16 counts moves blocked by a wall or an agent.
+  int cnt = 0, e_cur = -1;
+  auto flush = [&]() {
+    if (e_cur >= 0 && cnt && lane <= 16)
+      atomicAdd((unsigned long long *)&d.stats_step[e_cur * N_ST + (lane < 16 ? ST_ACT0 + lane : ST_MOVE_BLOCKED)],
+                (unsigned long long)cnt);
+    cnt = 0;
+  };
+
+  for (int i = blockIdx.x * WARPS + warp; i < n_alive; i += gridDim.x * WARPS) {
     const int slot = d.alive_list[i];
-    const int next_slot = (kPrefetchL2 && lane == 0 && i + G < n_alive) ? d.alive_list[i + G] : -1;
     const int env = d.env_of[slot];
+    if (env != e_cur) {
+      flush();
+      e_cur = env;
+    }
     // -- observation: k x k x nch patch (row, column, channel), then scalars.
     // Its locals end with this scope so that they do not stay live (in
     // registers) through the weight stream below.
@@ -444,12 +405,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
       }
       __syncwarp();
       layer_in_major<PREC, H, UNROLL, true>(wb + L.off_w1 / 16, n_nz, xs, bias, L.ns, scale, hs,
-                                            lane, L.relu, idx, blk + L.off_w2,
-                                            (uint32_t)(L.stride - L.off_w2));
+                                            lane, L.relu, idx);
     } else {
       layer_in_major<PREC, H, UNROLL, false>(wb + L.off_w1 / 16, L.D, xs, bias, L.ns, scale, hs,
-                                             lane, L.relu, nullptr, blk + L.off_w2,
-                                             (uint32_t)(L.stride - L.off_w2));
+                                             lane, L.relu, nullptr);
     }
     __syncwarp();
     // -- hidden layers: h = act(W_l h + b_l), alternating between hs and xs
@@ -466,7 +425,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
 
     // -- head: logits = (W_out h [+ b_out]) / exp(tau) (output-major rows of
     //    H / E units; the temperature only in the paper form)
-    if (kPrefetchL2 && next_slot >= 0) prefetch_l2(d.wq + (int64_t)next_slot * L.stride, pf_first);
     const uint4 *w3 = wb + L.off_w3 / 16;
     const int U3 = L.A * UPJ;
     const float *hb = bias + L.ns * H + L.L * H;  // head bias, then tau
@@ -513,8 +471,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     if (apply_moves) {
       // A6 (part 1), fused: facing and turns, and the move claim on a cell
       // that is neither a wall nor occupied now, at the start of the step
-      // (no cell changes while the policy phase runs).  The environment
-      // phase counts the actions, and the moves left without a target.
+      // (no cell changes while the policy phase runs).
+      int blk = 0;
       if (lane == 0) {
         const EnvDesc ed = d.env[env];
         const int side = ed.side;
@@ -538,7 +496,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
         }
         if (move) {
           const int c = step_cell(pos, nf, side);
-          if (!(cellf[c] & (CELL_WALL | CELL_AGENT))) {
+          if (cellf[c] & (CELL_WALL | CELL_AGENT)) {
+            blk = 1;
+          } else {
             const int local = slot - ed.slot_off;
             const U4 r = philox(t, (uint32_t)local, 0u, 0u, ed.seed, S_CLAIM_MOVE);
             atomicMax(&d.claim_move[ed.cell_off + c], claim_key(r.x, local));
@@ -549,10 +509,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
         d.facing[slot] = (uint8_t)nf;
         d.tgt[slot] = tc;
       }
+      blk = __shfl_sync(0xFFFFFFFFu, blk, 0);
+      if (lane == best) ++cnt;
+      if (lane == 16 && blk) ++cnt;
     }
     if (lane == 0) d.act[slot] = (uint8_t)best;
     __syncwarp();
   }
+  flush();
 }
 
 // ---------------------------------------------------------------------------
