@@ -311,9 +311,35 @@ def main():
     def agent_steps_of(stats):
         return sum(s["agent_steps"] for s in stats)
 
+    def replay_policy_timing(e, expect_agent_steps):
+        """Policy-kernel time over the timed window, replayed: reset, the same
+        warm-up, then eco_step_timed, whose one-step graph records a CUDA-event
+        pair around every policy launch on the library stream.  The simulation
+        is deterministic (integer state, counter-based draws), so the replay
+        launches the same kernels on the same data; the agent-step count is
+        checked to prove it.  The event-record nodes add a few us per step,
+        which is why the timed region itself runs eco_step's graphs."""
+        e.reset()
+        e.step(args.warmup)
+        torch.cuda.synchronize()
+        r0 = agent_steps_of(e.stats())
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(e.stream)
+        e.step_timed(args.steps)
+        b.record(e.stream)
+        b.synchronize()
+        r_agent_steps = agent_steps_of(e.stats()) - r0
+        if r_agent_steps != expect_agent_steps:
+            raise RuntimeError("policy-timing replay diverged: %d vs %d agent-steps"
+                               % (r_agent_steps, expect_agent_steps))
+        p_ms, n_t = e.policy_timing()
+        return p_ms, n_t, a.elapsed_time(b)
+
     # ---- device-timed region -------------------------------------------------
     env.reset()
-    env.step(args.warmup)            # builds the graph, autotunes the policy kernel
+    env.prepare()                    # autotunes the policy kernel, builds the step graphs
+    env.step(args.warmup)
     torch.cuda.synchronize()
     s0 = env.stats()
     props = torch.cuda.get_device_properties(local)
@@ -327,7 +353,7 @@ def main():
     t_end = torch.cuda.Event(enable_timing=True)
     wall0 = time.time()
     t_start.record(env.stream)
-    env.step_timed(args.steps)
+    env.step(args.steps)
     t_end.record(env.stream)
     t_end.synchronize()
     wall1 = time.time()
@@ -335,12 +361,12 @@ def main():
     clk = clocks.stop(wall0, wall1) if clocks else None
     ms = t_start.elapsed_time(t_end)
     s1 = env.stats()
-    policy_ms, n_timed = env.policy_timing()
     agent_steps = agent_steps_of(s1) - agent_steps_of(s0)
     births = sum(s["births"] for s in s1) - sum(s["births"] for s in s0)
     per_agent_bytes, n_alive_now = env.policy_bytes()
     per_agent_bytes = per_agent_bytes // max(1, n_alive_now)
     policy_bytes = agent_steps * per_agent_bytes
+    policy_ms, n_timed, replay_ms = replay_policy_timing(env, agent_steps)
 
     # ---- end-to-end through the C-ABI: step + host read of the step's stats --
     env.reset()
@@ -398,18 +424,19 @@ def main():
     if args.workload != "batched" and args.policy_variant == 0:
         senv = eco.Env(envs, policy_variant=-1, launch_mode=args.launch_mode)
         senv.reset()
+        senv.prepare()
         senv.step(args.warmup)
         torch.cuda.synchronize()
         q0 = agent_steps_of(senv.stats())
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(senv.stream)
-        senv.step_timed(args.steps)
+        senv.step(args.steps)
         b.record(senv.stream)
         b.synchronize()
         sms = a.elapsed_time(b)
         s_agent_steps = agent_steps_of(senv.stats()) - q0
-        s_policy_ms, s_n = senv.policy_timing()
+        s_policy_ms, s_n, _ = replay_policy_timing(senv, s_agent_steps)
         sparse = {"value": s_agent_steps / (sms * 1e-3), "unit": UNIT,
                   "ms_per_step": sms / args.steps,
                   "policy_ms_per_step": s_policy_ms / max(1, s_n),
@@ -478,6 +505,10 @@ def main():
                 "peak_kind": "%s copy bandwidth" % peak_kind,
                 "bytes_per_agent": per_agent_bytes,
                 "policy_ms_per_step": policy_ms / max(1, n_timed),
+                "policy_timing": "CUDA events around each policy launch, in a replay of the timed "
+                                 "window through eco_step_timed (deterministic: same launches, "
+                                 "agent-steps checked equal)",
+                "replay_ms_per_step": replay_ms / max(1, args.steps),
                 "policy_share_of_step": policy_ms / ms if ms > 0 else None,
                 "traffic": (traffic["dram_bytes_per_agent"] * agent_steps / max(1, args.steps * world))
                            if traffic and not sparse_forced else None,

@@ -328,9 +328,17 @@ int eco_create(const eco_config *cfg, void *dev_workspace, size_t bytes,
 int eco_reset(eco_handle *h);
 
 /* Advance every environment by n_steps >= 0 steps.  Asynchronous; replays
- * a CUDA graph of the step.  Returns ECO_ETIMEOUT if a previous step
- * recorded a device-side timeout. */
+ * CUDA graphs of 8 steps and of one step (built at the first call that
+ * needs them; the first call should not come inside a stream capture).
+ * A device-side wait that ran out of its budget in a step is reported as
+ * ECO_ETIMEOUT by the next eco_read_stats(). */
 int eco_step(eco_handle *h, int32_t n_steps);
+
+/* Optional: choose the policy-kernel variant (autotuned on the current
+ * state, so call it after eco_reset) and build every step graph now rather
+ * than in the first eco_step / eco_step_timed that needs them.  Steps
+ * nothing.  Synchronises the stream. */
+int eco_prepare(eco_handle *h);
 
 /* Copy statistics of environments [0, n_envs) to host records (either
  * pointer may be NULL).  Synchronises the stream. */
@@ -386,7 +394,9 @@ const char *eco_policy_variant_name(int32_t k);
 int eco_launch_mode(const eco_handle *h, int32_t *mode, int32_t *blocks);
 
 /* Like eco_step, and also records a CUDA-event pair around the policy
- * kernel of every step, on the library stream, inside the step's graph.
+ * kernel of every step, on the library stream, inside a one-step graph.
+ * The results are identical; each event-record node adds a few us to the
+ * step, so eco_step's graphs have none.
  * eco_policy_timing() synchronises, then returns the summed policy-kernel
  * time in milliseconds and the number of timed steps since its last call
  * (at most 4096 steps are buffered; more returns ECO_EINVAL). */

@@ -45,10 +45,14 @@ struct eco_handle {
   int forced;        // variant forced by the configuration (0 = autotune the dense
                      // variants, -1 = autotune the input-sparse ones)
   PolicyLaunch pl;
-  // step graph
-  cudaGraphExec_t graph;
-  cudaGraph_t graph_src;  // kept alive: its node handles address the exec's nodes
-  cudaGraphNode_t ev_node[2];
+  // step graphs: [GRAPH_TIMED] one step with event-record nodes around the
+  // policy kernel (eco_step_timed), [GRAPH_ONE] one step, [GRAPH_MANY]
+  // kStepsPerGraph steps (eco_step).  An event-record node costs a few us
+  // on the critical path between two kernels, so the untimed graphs have
+  // none, and a graph of several steps saves the launch gap between graphs.
+  cudaGraphExec_t graph[3];
+  cudaGraph_t graph_src[3];  // kept alive: their node handles address the execs' nodes
+  cudaGraphNode_t ev_node[2];  // in graph[GRAPH_TIMED]
   cudaEvent_t ev_dummy[2];
   std::vector<cudaEvent_t> ev_pool;  // pairs
   int ev_used;
@@ -306,11 +310,16 @@ extern "C" int eco_workspace_bytes(const eco_config *cfg, size_t *bytes) {
   return ECO_OK;
 }
 
+enum { GRAPH_TIMED = 0, GRAPH_ONE = 1, GRAPH_MANY = 2 };
+constexpr int kStepsPerGraph = 8;
+
 static void destroy_graph(eco_handle *h) {
-  if (h->graph) cudaGraphExecDestroy(h->graph);
-  if (h->graph_src) cudaGraphDestroy(h->graph_src);
-  h->graph = nullptr;
-  h->graph_src = nullptr;
+  for (int k = 0; k < 3; ++k) {
+    if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    if (h->graph_src[k]) cudaGraphDestroy(h->graph_src[k]);
+    h->graph[k] = nullptr;
+    h->graph_src[k] = nullptr;
+  }
 }
 
 extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t bytes, void *stream,
@@ -411,8 +420,10 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
   h->grid.use_persistent = cfg->launch_mode == 0;
   h->forced = cfg->policy_variant;
   h->variant = 0;
-  h->graph = nullptr;
-  h->graph_src = nullptr;
+  for (int k = 0; k < 3; ++k) {
+    h->graph[k] = nullptr;
+    h->graph_src[k] = nullptr;
+  }
   h->ev_used = 0;
   h->err[0] = 0;
   h->rd_bytes = (size_t)(reinterpret_cast<uint8_t *>(h->d.counters + CNT_N) -
@@ -520,24 +531,30 @@ static int autotune(eco_handle *h) {
 
 // One step: the alive list was built by the previous step (or by reset /
 // write_state), so the step is the policy kernel and the environment
-// phases, which end by building the next step's alive list.
-static cudaError_t enqueue_step(eco_handle *h) {
+// phases, which end by building the next step's alive list.  timed: an
+// event-record node on each side of the policy kernel.
+static cudaError_t enqueue_step(eco_handle *h, bool timed) {
+  cudaError_t e = cudaSuccess;
   // "external" records become event-record nodes of the captured graph
-  cudaError_t e = cudaEventRecordWithFlags(h->ev_dummy[0], h->stream, cudaEventRecordExternal);
+  if (timed) e = cudaEventRecordWithFlags(h->ev_dummy[0], h->stream, cudaEventRecordExternal);
   if (e == cudaSuccess) e = policy_launch(h->pl, h->d, h->L, h->R, h->stream, true);
-  if (e == cudaSuccess) e = cudaEventRecordWithFlags(h->ev_dummy[1], h->stream, cudaEventRecordExternal);
+  if (e == cudaSuccess && timed)
+    e = cudaEventRecordWithFlags(h->ev_dummy[1], h->stream, cudaEventRecordExternal);
   if (e == cudaSuccess) e = launch_env_phases(h->d, h->L, h->R, h->grid, h->stream);
   return e;
 }
 
-static int build_graph(eco_handle *h) {
-  if (h->graph) return ECO_OK;
+static int build_graph(eco_handle *h, int kind) {
+  if (h->graph[kind]) return ECO_OK;
   int rc = autotune(h);
   if (rc) return rc;
+  const bool timed = kind == GRAPH_TIMED;
+  const int steps = kind == GRAPH_MANY ? kStepsPerGraph : 1;
   cudaGraph_t g = nullptr;
   for (;;) {
     CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_step(h);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = enqueue_step(h, timed);
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (e == cudaSuccess && e2 == cudaSuccess) break;
     if (e2 == cudaSuccess && g) cudaGraphDestroy(g);
@@ -545,40 +562,44 @@ static int build_graph(eco_handle *h) {
     cudaGetLastError();
     if (h->grid.use_persistent && h->grid.persistent_blocks > 0) {
       // the persistent form could not be captured: fall back to one
-      // kernel per phase (identical results)
+      // kernel per phase (identical results) in every graph
       h->grid.use_persistent = 0;
+      CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+      destroy_graph(h);
       continue;
     }
     if (e != cudaSuccess) return fail(h, ECO_ECUDA, "capture: %s", cudaGetErrorString(e));
     return fail(h, ECO_ECUDA, "end capture: %s", cudaGetErrorString(e2));
   }
-  // locate the two event-record nodes (in capture order)
-  size_t n = 0;
-  CUDA_TRY(h, cudaGraphGetNodes(g, nullptr, &n));
-  std::vector<cudaGraphNode_t> nodes(n);
-  CUDA_TRY(h, cudaGraphGetNodes(g, nodes.data(), &n));
-  int found = 0;
-  for (size_t i = 0; i < n; ++i) {
-    cudaGraphNodeType t;
-    CUDA_TRY(h, cudaGraphNodeGetType(nodes[i], &t));
-    if (t == cudaGraphNodeTypeEventRecord) {
-      cudaEvent_t ev;
-      CUDA_TRY(h, cudaGraphEventRecordNodeGetEvent(nodes[i], &ev));
-      if (ev == h->ev_dummy[0]) h->ev_node[0] = nodes[i], ++found;
-      if (ev == h->ev_dummy[1]) h->ev_node[1] = nodes[i], ++found;
+  if (timed) {
+    // locate the two event-record nodes
+    size_t n = 0;
+    CUDA_TRY(h, cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    CUDA_TRY(h, cudaGraphGetNodes(g, nodes.data(), &n));
+    int found = 0;
+    for (size_t i = 0; i < n; ++i) {
+      cudaGraphNodeType t;
+      CUDA_TRY(h, cudaGraphNodeGetType(nodes[i], &t));
+      if (t == cudaGraphNodeTypeEventRecord) {
+        cudaEvent_t ev;
+        CUDA_TRY(h, cudaGraphEventRecordNodeGetEvent(nodes[i], &ev));
+        if (ev == h->ev_dummy[0]) h->ev_node[0] = nodes[i], ++found;
+        if (ev == h->ev_dummy[1]) h->ev_node[1] = nodes[i], ++found;
+      }
+    }
+    if (found != 2) {
+      cudaGraphDestroy(g);
+      return fail(h, ECO_ECUDA, "step graph: event nodes not found");
     }
   }
-  if (found != 2) {
-    cudaGraphDestroy(g);
-    return fail(h, ECO_ECUDA, "step graph: event nodes not found");
-  }
-  cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaError_t ie = cudaGraphInstantiate(&h->graph[kind], g, 0);
   if (ie != cudaSuccess) {
     cudaGraphDestroy(g);
-    h->graph = nullptr;
+    h->graph[kind] = nullptr;
     return fail(h, ECO_ECUDA, "instantiate: %s", cudaGetErrorString(ie));
   }
-  h->graph_src = g;
+  h->graph_src[kind] = g;
   return ECO_OK;
 }
 
@@ -586,32 +607,45 @@ static int step_impl(eco_handle *h, int32_t n_steps, bool timed) {
   if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
   if (n_steps < 0) return fail(h, ECO_EINVAL, "n_steps < 0");
   if (n_steps == 0) return ECO_OK;
-  int rc = build_graph(h);
+  if (!timed) {
+    const int many = n_steps / kStepsPerGraph, rest = n_steps % kStepsPerGraph;
+    int rc = many ? build_graph(h, GRAPH_MANY) : ECO_OK;
+    if (rc == ECO_OK && rest) rc = build_graph(h, GRAPH_ONE);
+    if (rc) return rc;
+    for (int i = 0; i < many; ++i) CUDA_TRY(h, cudaGraphLaunch(h->graph[GRAPH_MANY], h->stream));
+    for (int i = 0; i < rest; ++i) CUDA_TRY(h, cudaGraphLaunch(h->graph[GRAPH_ONE], h->stream));
+    return ECO_OK;
+  }
+  int rc = build_graph(h, GRAPH_TIMED);
   if (rc) return rc;
-  if (timed) {
-    if (h->ev_used + n_steps > 4096) return fail(h, ECO_EINVAL, "more than 4096 timed steps buffered");
-    while ((int)h->ev_pool.size() < 2 * (h->ev_used + n_steps)) {
-      cudaEvent_t ev;
-      CUDA_TRY(h, cudaEventCreate(&ev));
-      h->ev_pool.push_back(ev);
-    }
+  cudaGraphExec_t gx = h->graph[GRAPH_TIMED];
+  if (h->ev_used + n_steps > 4096) return fail(h, ECO_EINVAL, "more than 4096 timed steps buffered");
+  while ((int)h->ev_pool.size() < 2 * (h->ev_used + n_steps)) {
+    cudaEvent_t ev;
+    CUDA_TRY(h, cudaEventCreate(&ev));
+    h->ev_pool.push_back(ev);
   }
   for (int i = 0; i < n_steps; ++i) {
-    if (timed) {
-      CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(h->graph, h->ev_node[0], h->ev_pool[2 * h->ev_used]));
-      CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(h->graph, h->ev_node[1], h->ev_pool[2 * h->ev_used + 1]));
-      ++h->ev_used;
-    }
-    CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
+    CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(gx, h->ev_node[0], h->ev_pool[2 * h->ev_used]));
+    CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(gx, h->ev_node[1], h->ev_pool[2 * h->ev_used + 1]));
+    ++h->ev_used;
+    CUDA_TRY(h, cudaGraphLaunch(gx, h->stream));
   }
-  if (timed) {
-    CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(h->graph, h->ev_node[0], h->ev_dummy[0]));
-    CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(h->graph, h->ev_node[1], h->ev_dummy[1]));
-  }
+  CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(gx, h->ev_node[0], h->ev_dummy[0]));
+  CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(gx, h->ev_node[1], h->ev_dummy[1]));
   return ECO_OK;
 }
 
 extern "C" int eco_step(eco_handle *h, int32_t n_steps) { return step_impl(h, n_steps, false); }
+
+extern "C" int eco_prepare(eco_handle *h) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  int rc = build_graph(h, GRAPH_ONE);
+  if (rc == ECO_OK) rc = build_graph(h, GRAPH_MANY);
+  if (rc == ECO_OK) rc = build_graph(h, GRAPH_TIMED);
+  if (rc == ECO_OK) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return rc;
+}
 extern "C" int eco_step_timed(eco_handle *h, int32_t n_steps) { return step_impl(h, n_steps, true); }
 
 extern "C" int eco_policy_timing(eco_handle *h, double *total_ms, int32_t *n_timed) {

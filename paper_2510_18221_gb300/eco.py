@@ -113,6 +113,7 @@ def lib() -> ctypes.CDLL:
         L.eco_reset.argtypes = [H]
         L.eco_step.argtypes = [H, ctypes.c_int32]
         L.eco_step_timed.argtypes = [H, ctypes.c_int32]
+        L.eco_prepare.argtypes = [H]
         L.eco_policy_timing.argtypes = [H, ctypes.POINTER(ctypes.c_double), _i32p]
         L.eco_read_stats.argtypes = [H, _vp, _vp, ctypes.c_int32]
         L.eco_read_state.argtypes = [H, ctypes.c_int32, ctypes.POINTER(eco_state_view)]
@@ -180,6 +181,10 @@ def eco_reset(h) -> None:
 
 def eco_step(h, n_steps: int) -> None:
     _check(lib().eco_step(h, int(n_steps)), h)
+
+
+def eco_prepare(h) -> None:
+    _check(lib().eco_prepare(h), h)
 
 
 def eco_step_timed(h, n_steps: int) -> None:
@@ -330,6 +335,9 @@ class Env:
 
     def step(self, n: int = 1) -> None:
         eco_step(self.h, n)
+
+    def prepare(self) -> None:
+        eco_prepare(self.h)
 
     def step_timed(self, n: int = 1) -> None:
         eco_step_timed(self.h, n)

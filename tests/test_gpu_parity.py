@@ -187,6 +187,37 @@ def test_launch_forms_bit_identical():
     b.close()
 
 
+@pytest.mark.parametrize("launch_mode", [0, 1])
+def test_step_graph_forms_bit_identical(launch_mode):
+    """eco_step(n) replays graphs of 8 steps and of one step, eco_step_timed
+    a one-step graph with event-record nodes around the policy kernel, and
+    eco_prepare builds them ahead: every array and statistic must match
+    after 8k + r steps taken in each of these ways."""
+    from paper_2510_18221_gb300 import eco
+    envs = [workloads.scaled("mid", s, n, k, seed=50 + i, precision="bf16", e_init=185)
+            for i, (s, n, k) in enumerate([(64, 600, 500), (128, 2048, 1500)])]
+    many, ones, timed = (eco.Env(envs, launch_mode=launch_mode) for _ in range(3))
+    for x in (many, ones, timed):
+        x.reset()
+    many.prepare()
+    many.step(19)                 # 2 x 8 steps + 3 x 1
+    for _ in range(19):
+        ones.step(1)
+    timed.step_timed(19)
+    _, n_timed = timed.policy_timing()
+    assert n_timed == 19
+    for e in range(len(envs)):
+        sm, so, st = many.read_state(e), ones.read_state(e), timed.read_state(e)
+        for k in harness.STATE_KEYS:
+            assert np.array_equal(sm[k], so[k]) and np.array_equal(sm[k], st[k]), (e, k)
+        assert many.stats()[e] == ones.stats()[e] == timed.stats()[e]
+        assert np.array_equal(many.read_params(e), ones.read_params(e))
+        assert np.array_equal(many.read_params(e), timed.read_params(e))
+    assert many.stats()[0]["step"] == 19 and sum(s["births"] for s in many.stats()) > 0
+    for x in (many, ones, timed):
+        x.close()
+
+
 def test_per_phase_launch_form_lockstep():
     w = workloads.scaled("mid", 128, 2048, 1500, precision="fp8", e_init=190)
     rep = _run(w, 15, launch_mode=1)
