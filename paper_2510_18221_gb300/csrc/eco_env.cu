@@ -750,6 +750,18 @@ __device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs) {
     const int e = env_of_cell(d.env, d.n_envs, c0);
     const EnvDesc ed = d.env[e];
     uchar4 cf = reinterpret_cast<uchar4 *>(d.cellf)[g];
+    // terrain: the group's biomass, remainders and energy, loaded together
+    // (the loads are independent; the chain per cell was the phase's cost)
+    int bio[4] = {0, 0, 0, 0}, res[4] = {0, 0, 0, 0};
+    uint32_t pho[4] = {0u, 0u, 0u, 0u};
+    if (R.rules == RULES_TERRAIN) {
+      const int4 b4 = reinterpret_cast<const int4 *>(d.bio)[g];
+      const int4 r4 = reinterpret_cast<const int4 *>(d.res)[g];
+      const uint4 p4 = reinterpret_cast<const uint4 *>(d.photo)[g];
+      bio[0] = b4.x, bio[1] = b4.y, bio[2] = b4.z, bio[3] = b4.w;
+      res[0] = r4.x, res[1] = r4.y, res[2] = r4.z, res[3] = r4.w;
+      pho[0] = p4.x, pho[1] = p4.y, pho[2] = p4.z, pho[3] = p4.w;
+    }
     int grown = 0;
     const bool any = !((cf.x & (CELL_WALL | CELL_FOOD)) && (cf.y & (CELL_WALL | CELL_FOOD)) &&
                        (cf.z & (CELL_WALL | CELL_FOOD)) && (cf.w & (CELL_WALL | CELL_FOOD)));
@@ -761,9 +773,12 @@ __device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs) {
       if (!(cf.z & (CELL_WALL | CELL_FOOD)) && r.z < R.thr_regrow) { cf.z |= CELL_FOOD; mask |= 4; }
       if (!(cf.w & (CELL_WALL | CELL_FOOD)) && r.w < R.thr_regrow) { cf.w |= CELL_FOOD; mask |= 8; }
       grown = __popc(mask);
-      if (grown && R.rules != RULES_SIMPLE)  // one bite of energy on each regrown cell
+      if (grown && R.rules == RULES_PAPER)  // one bite of energy on each regrown cell
         for (int k = 0; k < 4; ++k)
           if (mask & (1 << k)) d.res[c0 + k] = R.e_food;
+      if (R.rules == RULES_TERRAIN)  // the same, in the group's registers
+        for (int k = 0; k < 4; ++k)
+          if (mask & (1 << k)) res[k] = R.e_food;
     }
     bool changed = grown != 0;
     if (R.rules == RULES_TERRAIN) {
@@ -772,13 +787,14 @@ __device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs) {
       uint8_t *cfb = reinterpret_cast<uint8_t *>(&cf);
       int refilled = 0;
       long long grew = 0;
+      bool touched = grown != 0;
       for (int k = 0; k < 4; ++k) {
-        const int c = c0 + k;
-        const int b = d.bio[c];
+        const int b = bio[k];
         if ((cfb[k] & CELL_WALL) || b <= 0) continue;
-        const unsigned long long acc = (unsigned long long)d.photo[c] + (unsigned long long)b * (unsigned)R.photo_q16;
-        d.photo[c] = (uint32_t)(acc & 0xFFFFull);
-        const int r = d.res[c];
+        const unsigned long long acc = (unsigned long long)pho[k] + (unsigned long long)b * (unsigned)R.photo_q16;
+        pho[k] = (uint32_t)(acc & 0xFFFFull);
+        touched = true;
+        const int r = res[k];
         const long long gain = min((long long)(acc >> 16), (long long)R.res_cap - r);
         if (gain <= 0) continue;
         if (r == 0) {
@@ -786,8 +802,12 @@ __device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs) {
           ++refilled;
           changed = true;
         }
-        d.res[c] = r + (int)gain;
+        res[k] = r + (int)gain;
         grew += gain;
+      }
+      if (touched) {
+        reinterpret_cast<int4 *>(d.res)[g] = make_int4(res[0], res[1], res[2], res[3]);
+        reinterpret_cast<uint4 *>(d.photo)[g] = make_uint4(pho[0], pho[1], pho[2], pho[3]);
       }
       stat_add(d.stats_step, e, ST_FOOD_REFILLED, refilled);
       stat_add(d.stats_step, e, ST_PHOTO, (int)grew);
@@ -803,48 +823,160 @@ __device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs) {
 // neighbour (the first of N, E, S, W on ties) when that one lies `drop`
 // below it.  Stored as amount << 2 | direction (amount 0: none); the total
 // water of an environment is below 2^30, so the amount fits.
+//
+// Both parts take cells in groups of four along a row (cell offsets and
+// sides are even; a group stays in one row when the side is a multiple of
+// four): the group, the four cells above and below it (16-byte loads) and
+// the two at its ends are loaded together, so a group costs one round
+// trip of independent loads.  Other sides take the neighbours one by one.
+__device__ __forceinline__ uint32_t flow_pick(int w, long long here, const long long hn[4], const bool wn[4]) {
+  long long lowest = 0;
+  int best = -1;
+#pragma unroll
+  for (int dir = 0; dir < 4; ++dir) {
+    if (wn[dir]) continue;
+    if (best < 0 || hn[dir] < lowest) {
+      best = dir;
+      lowest = hn[dir];
+    }
+  }
+  if (best >= 0 && lowest < here) {
+    const long long amount = min((here - lowest) / 5, (long long)w);
+    return ((uint32_t)amount << 2) | (uint32_t)best;
+  }
+  return 0u;
+}
+
+// The four cells of a group and their neighbours: global indices of the
+// group start, the rows above and below (same columns) and the cells west
+// of the first and east of the last.
+struct FlowGroup {
+  int c0, up0, dn0, west, east;
+};
+
+__device__ __forceinline__ FlowGroup flow_group(const EnvDesc &ed, int c0) {
+  const int lc = c0 - ed.cell_off, L = ed.side;
+  const int x0 = lc % L, y = lc / L;
+  const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
+  FlowGroup fg;
+  fg.c0 = c0;
+  fg.up0 = ed.cell_off + yu * L + x0;
+  fg.dn0 = ed.cell_off + yd * L + x0;
+  fg.west = ed.cell_off + y * L + (x0 == 0 ? L - 1 : x0 - 1);
+  fg.east = ed.cell_off + y * L + (x0 + 4 == L ? 0 : x0 + 4);
+  return fg;
+}
+
+__device__ __forceinline__ void unpack4(const int4 v, int o[4]) { o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w; }
+
 __device__ void ph_flow_out(const Dev &d, int g0, int gs) {
-  for (int c = g0; c < d.total_cells; c += gs) {
-    const int w = d.water[c];
-    uint32_t f = 0u;
-    if (w > 0 && !(d.cellf[c] & CELL_WALL)) {
-      const EnvDesc ed = d.env[env_of_cell(d.env, d.n_envs, c)];
-      const int lc = c - ed.cell_off;
-      const long long here = (long long)d.rock[c] + w;
-      long long lowest = 0;
-      int best = -1;
-      for (int dir = 0; dir < 4; ++dir) {
-        const int n = ed.cell_off + step_cell(lc, dir, ed.side);
-        if (d.cellf[n] & CELL_WALL) continue;
-        const long long h = (long long)d.rock[n] + d.water[n];
-        if (best < 0 || h < lowest) {
-          best = dir;
-          lowest = h;
+  const int groups = d.total_cells >> 2;
+  for (int g = g0; g < groups; g += gs) {
+    const int c0 = g << 2;
+    int w[4];
+    unpack4(reinterpret_cast<const int4 *>(d.water)[g], w);
+    const uchar4 cf4 = reinterpret_cast<const uchar4 *>(d.cellf)[g];
+    const uint8_t cf[4] = {cf4.x, cf4.y, cf4.z, cf4.w};
+    bool wet[4], any = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      wet[k] = w[k] > 0 && !(cf[k] & CELL_WALL);
+      any |= wet[k];
+    }
+    uint32_t f[4] = {0u, 0u, 0u, 0u};
+    if (any) {
+      const EnvDesc ed = d.env[env_of_cell(d.env, d.n_envs, c0)];
+      int rk[4];
+      unpack4(reinterpret_cast<const int4 *>(d.rock)[g], rk);
+      if ((ed.side & 3) == 0) {
+        const FlowGroup fg = flow_group(ed, c0);
+        int wu[4], ru[4], wd[4], rd[4];
+        unpack4(*reinterpret_cast<const int4 *>(d.water + fg.up0), wu);
+        unpack4(*reinterpret_cast<const int4 *>(d.rock + fg.up0), ru);
+        unpack4(*reinterpret_cast<const int4 *>(d.water + fg.dn0), wd);
+        unpack4(*reinterpret_cast<const int4 *>(d.rock + fg.dn0), rd);
+        const uchar4 cu = *reinterpret_cast<const uchar4 *>(d.cellf + fg.up0);
+        const uchar4 cd = *reinterpret_cast<const uchar4 *>(d.cellf + fg.dn0);
+        const uint8_t cuv[4] = {cu.x, cu.y, cu.z, cu.w}, cdv[4] = {cd.x, cd.y, cd.z, cd.w};
+        const long long hw = (long long)d.rock[fg.west] + d.water[fg.west];
+        const long long he = (long long)d.rock[fg.east] + d.water[fg.east];
+        const bool ww = (d.cellf[fg.west] & CELL_WALL) != 0, we = (d.cellf[fg.east] & CELL_WALL) != 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (!wet[k]) continue;
+          // N, E, S, W
+          const long long hn[4] = {(long long)ru[k] + wu[k],
+                                   k < 3 ? (long long)rk[k + 1] + w[k + 1] : he,
+                                   (long long)rd[k] + wd[k],
+                                   k > 0 ? (long long)rk[k - 1] + w[k - 1] : hw};
+          const bool wn[4] = {(cuv[k] & CELL_WALL) != 0, k < 3 ? (cf[k + 1] & CELL_WALL) != 0 : we,
+                              (cdv[k] & CELL_WALL) != 0, k > 0 ? (cf[k - 1] & CELL_WALL) != 0 : ww};
+          f[k] = flow_pick(w[k], (long long)rk[k] + w[k], hn, wn);
+        }
+      } else {
+        for (int k = 0; k < 4; ++k) {
+          if (!wet[k]) continue;
+          const int lc = c0 + k - ed.cell_off;
+          long long hn[4];
+          bool wn[4];
+          for (int dir = 0; dir < 4; ++dir) {
+            const int n = ed.cell_off + step_cell(lc, dir, ed.side);
+            wn[dir] = (d.cellf[n] & CELL_WALL) != 0;
+            hn[dir] = (long long)d.rock[n] + d.water[n];
+          }
+          f[k] = flow_pick(w[k], (long long)rk[k] + w[k], hn, wn);
         }
       }
-      if (best >= 0 && lowest < here) {
-        const long long amount = min((here - lowest) / 5, (long long)w);
-        f = ((uint32_t)amount << 2) | (uint32_t)best;
-      }
     }
-    d.flow[c] = f;
+    reinterpret_cast<uint4 *>(d.flow)[g] = make_uint4(f[0], f[1], f[2], f[3]);
   }
 }
 
 // Part 2: every cell gives its transfer and takes those of the neighbours
 // that point at it (a neighbour in direction dir points back with dir + 2).
 // Only this cell's water is written, from the transfers alone.
+__device__ __forceinline__ int flow_in_of(uint32_t fn, int dir) {
+  return ((fn >> 2) && (int)(fn & 3u) == ((dir + 2) & 3)) ? (int)(fn >> 2) : 0;
+}
+
 __device__ void ph_flow_in(const Dev &d, int g0, int gs) {
-  for (int c = g0; c < d.total_cells; c += gs) {
-    if (d.cellf[c] & CELL_WALL) continue;
-    const EnvDesc ed = d.env[env_of_cell(d.env, d.n_envs, c)];
-    const int lc = c - ed.cell_off;
-    int w = d.water[c] - (int)(d.flow[c] >> 2);
-    for (int dir = 0; dir < 4; ++dir) {
-      const uint32_t fn = d.flow[ed.cell_off + step_cell(lc, dir, ed.side)];
-      if ((fn >> 2) && (int)(fn & 3u) == ((dir + 2) & 3)) w += (int)(fn >> 2);
+  const int groups = d.total_cells >> 2;
+  for (int g = g0; g < groups; g += gs) {
+    const int c0 = g << 2;
+    const uchar4 cf4 = reinterpret_cast<const uchar4 *>(d.cellf)[g];
+    const uint8_t cf[4] = {cf4.x, cf4.y, cf4.z, cf4.w};
+    if ((cf[0] & cf[1] & cf[2] & cf[3]) & CELL_WALL) continue;
+    int w[4];
+    unpack4(reinterpret_cast<const int4 *>(d.water)[g], w);
+    const uint4 f4 = reinterpret_cast<const uint4 *>(d.flow)[g];
+    const uint32_t f[4] = {f4.x, f4.y, f4.z, f4.w};
+    const EnvDesc ed = d.env[env_of_cell(d.env, d.n_envs, c0)];
+    if ((ed.side & 3) == 0) {
+      const FlowGroup fg = flow_group(ed, c0);
+      const uint4 fu4 = *reinterpret_cast<const uint4 *>(d.flow + fg.up0);
+      const uint4 fd4 = *reinterpret_cast<const uint4 *>(d.flow + fg.dn0);
+      const uint32_t fu[4] = {fu4.x, fu4.y, fu4.z, fu4.w}, fd[4] = {fd4.x, fd4.y, fd4.z, fd4.w};
+      const uint32_t fw = d.flow[fg.west], fe = d.flow[fg.east];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (cf[k] & CELL_WALL) continue;
+        int v = w[k] - (int)(f[k] >> 2);
+        v += flow_in_of(fu[k], 0);
+        v += flow_in_of(k < 3 ? f[k + 1] : fe, 1);
+        v += flow_in_of(fd[k], 2);
+        v += flow_in_of(k > 0 ? f[k - 1] : fw, 3);
+        w[k] = v;
+      }
+    } else {
+      for (int k = 0; k < 4; ++k) {
+        if (cf[k] & CELL_WALL) continue;
+        const int lc = c0 + k - ed.cell_off;
+        int v = w[k] - (int)(f[k] >> 2);
+        for (int dir = 0; dir < 4; ++dir) v += flow_in_of(d.flow[ed.cell_off + step_cell(lc, dir, ed.side)], dir);
+        w[k] = v;
+      }
     }
-    d.water[c] = w;
+    reinterpret_cast<int4 *>(d.water)[g] = make_int4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -1068,7 +1200,7 @@ cudaError_t launch_env_phases(const Dev &d, const Layout &L, const Rules &R, con
   k_mutate<<<g.birth_blocks, 256, msmem, s>>>(d, L, R);
   k_regrow<<<g.cell_blocks, T, 0, s>>>(d, R);
   if (R.rules == RULES_TERRAIN) {
-    const int fb = grid_for(d.total_cells, T, g.sms * 8);
+    const int fb = grid_for(d.total_cells / 4, T, g.sms * 8);
     k_flow_out<<<fb, T, 0, s>>>(d);
     k_flow_in<<<fb, T, 0, s>>>(d);
   }

@@ -413,6 +413,16 @@ def test_terrain_variants(over):
     assert rep["steps"] == 15 and tot["deaths"] > 0
 
 
+@pytest.mark.parametrize("side,preset,launch_mode", [(50, "beach", 0), (50, "beach", 1), (30, "lake", 0)])
+def test_terrain_sides_two_mod_four(side, preset, launch_mode):
+    """The flow and photosynthesis phases take cells in groups of four; on a
+    side that is 2 mod 4 a group straddles two rows and the neighbours are
+    found cell by cell.  Both launch forms, against the oracle."""
+    slots, k = (700, 450) if side == 50 else (300, 200)
+    rep, tot = _run_totals(_terrain(side, slots, k, terrain=preset), 15, launch_mode=launch_mode)
+    assert rep["steps"] == 15 and tot["photo"] > 0 and tot["deaths"] > 0
+
+
 def test_terrain_launch_forms_bit_identical():
     from paper_2510_18221_gb300 import eco
     w = _terrain(128, 4096, 3000, terrain="island", precision="fp8", wall_density=0.03)
