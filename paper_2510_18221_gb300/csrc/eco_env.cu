@@ -401,6 +401,7 @@ __device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs, int
         const U4 r = philox(t, (uint32_t)local, 0u, 0u, ed.seed, S_CLAIM_BIRTH);
         atomicMax(&d.claim_birth[gc], claim_key(r.x, local));
         const int k = atomicAdd(&d.birth_contenders[e], 1);
+        atomicAdd(&d.counters[CNT_CONTENDERS], 1);
         d.contenders[ed.slot_off + k] = slot;
         bt = c;
       }
@@ -1037,6 +1038,7 @@ __device__ void ph_finish(const Dev &d, const Rules &R) {
   if (threadIdx.x == 0) {
     d.step[0] = t + 1;
     d.counters[CNT_N_BIRTHS] = 0;
+    d.counters[CNT_CONTENDERS] = 0;
   }
 }
 
@@ -1134,9 +1136,16 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   ph_regrow(d, R, g0, gs);
   if (R.rules == RULES_TERRAIN) ph_flow_out(d, g0, gs);
   if (!grid_sync(d, nb, &s_flag)) return;
-  ph_birth_assign(d, R, blockIdx.x, gridDim.x, S);
-  if (!grid_sync(d, nb, &s_flag)) return;
-  ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale);
+  // Every claim is in, and the count of claimants does not change again
+  // before the last barrier, so every CTA takes the same branch.  On a step
+  // without a birth claim, slot assignment and mutation have nothing to do
+  // and their barrier is skipped.
+  if (cuda::atomic_ref<int, cuda::thread_scope_device>(d.counters[CNT_CONTENDERS]).load(
+          cuda::memory_order_relaxed) != 0) {
+    ph_birth_assign(d, R, blockIdx.x, gridDim.x, S);
+    if (!grid_sync(d, nb, &s_flag)) return;
+    ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale);
+  }
   ph_compact_count(d, blockIdx.x, gridDim.x, S.sh);
   if (!grid_sync(d, nb, &s_flag)) return;
   if (R.rules == RULES_TERRAIN) ph_flow_in(d, g0, gs);

@@ -316,6 +316,7 @@ __global__ void __launch_bounds__(1024) k_init_stats(Dev d, Rules R) {
   }
   if (threadIdx.x == 0) {
     d.birth_contenders[e] = 0;
+    if (e == 0) d.counters[CNT_CONTENDERS] = 0;
     d.place_prefix[e] = 0ull;
     d.place_remaining[e] = ed.init_alive;
   }

@@ -315,6 +315,7 @@ enum : int {
   CNT_N_ALIVE = 0,
   CNT_N_BIRTHS = 1,
   CNT_STATUS = 2,
+  CNT_CONTENDERS = 3,  // this step's birth claimants over all environments
   CNT_N = 8,
 };
 
