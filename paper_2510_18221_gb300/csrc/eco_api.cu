@@ -436,6 +436,14 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
                         cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = launch_init_static(h->d, h->grid, h->stream);
   if (e == cudaSuccess) e = env_prepare(h->L, &h->grid);
+  if (e == cudaSuccess && h->grid.persistent_blocks > 0) {
+    // a batch of at most 4,096 slots and 16,384 cells runs the persistent
+    // form on one CTA (at most four slots or cell groups per thread), whose
+    // phases need no grid barrier; anything larger keeps one CTA per SM
+    // (fewer CTAs only made the barriers' waits longer)
+    const long long work = std::max((long long)h->d.total_slots, (long long)h->d.total_cells / 4);
+    if (work <= 4096) h->grid.persistent_blocks = 1;
+  }
   if (e == cudaSuccess) e = cudaMallocHost(&h->rd_host, h->rd_bytes);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[1]);

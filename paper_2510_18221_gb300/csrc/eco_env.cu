@@ -1085,6 +1085,7 @@ constexpr int kStatusTimeout = 4;
 // barrier.  Returns false when the kernel must stop.
 __device__ bool grid_sync(const Dev &d, unsigned nblocks, int *s_flag) {
   __syncthreads();
+  if (nblocks == 1) return true;  // one CTA: the block barrier is the grid barrier
   if (threadIdx.x == 0) {
     cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(d.barrier[1]);
     cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(d.barrier[0]);
