@@ -374,10 +374,14 @@ def main():
     torch.cuda.synchronize()
     e0 = env.stats()
     barrier()
+    # eco_step_read: each call enqueues a step and returns the records of the
+    # step before it (their device -> host copy ends that step's graph), so
+    # the host reads step s while step s + 1 runs; the last step's records
+    # come from eco_read_stats, which synchronises
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        eco.eco_step(env.h, 1)
-        tot, last = eco.eco_read_stats(env.h, env.n_envs)   # device -> host, synchronises
+        tot, last = eco.eco_step_read(env.h, env.n_envs)
+    tot, last = eco.eco_read_stats(env.h, env.n_envs)
     e_el = time.perf_counter() - t0
     barrier()
     e_agent_steps = int(tot[:, 1].sum()) - agent_steps_of(e0)

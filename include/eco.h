@@ -334,6 +334,18 @@ int eco_reset(eco_handle *h);
  * ECO_ETIMEOUT by the next eco_read_stats(). */
 int eco_step(eco_handle *h, int32_t n_steps);
 
+/* Pipelined step and read: enqueue one step whose graph ends by copying
+ * the statistics and status word into one of two pinned buffers the handle
+ * owns, then wait for the copy made by the PREVIOUS eco_step_read call and
+ * return those records.  So a call returns the records as of the end of
+ * the step enqueued by the previous call (on the first call after
+ * eco_create or eco_reset: the records as they stood when the call was
+ * made), while the step it enqueued runs; eco_read_stats afterwards gives
+ * the last step's.  The host never waits for the step it has just
+ * enqueued, so the GPU stays busy across the read.  Buffers as for
+ * eco_read_stats; the status word is checked as there (ECO_ETIMEOUT). */
+int eco_step_read(eco_handle *h, eco_stats *total, eco_stats *last, int32_t n_envs);
+
 /* Optional: choose the policy-kernel variant (autotuned on the current
  * state, so call it after eco_reset) and build every step graph now rather
  * than in the first eco_step / eco_step_timed that needs them.  Steps

@@ -50,16 +50,22 @@ struct eco_handle {
   // kStepsPerGraph steps (eco_step).  An event-record node costs a few us
   // on the critical path between two kernels, so the untimed graphs have
   // none, and a graph of several steps saves the launch gap between graphs.
-  cudaGraphExec_t graph[3];
-  cudaGraph_t graph_src[3];  // kept alive: their node handles address the execs' nodes
+  // [GRAPH_READ1], [GRAPH_READ2]: one step, then a copy of the statistics
+  // into pinned slot 1 or 2 (eco_step_read)
+  cudaGraphExec_t graph[5];
+  cudaGraph_t graph_src[5];  // kept alive: their node handles address the execs' nodes
   cudaGraphNode_t ev_node[2];  // in graph[GRAPH_TIMED]
   cudaEvent_t ev_dummy[2];
   std::vector<cudaEvent_t> ev_pool;  // pairs
   int ev_used;
-  // pinned host mirror of [stats_total, stats_last, counters], contiguous
-  // in the workspace: eco_read_stats reads it with one copy
+  // pinned host mirrors of [stats_total, stats_last, counters], contiguous
+  // in the workspace, rd_bytes each: slot 0 for eco_read_stats, slots 1 and
+  // 2 for eco_step_read, whose copy of slot rd_pending (0: none) may still
+  // be in flight, completion marked by rd_ev[slot - 1]
   uint8_t *rd_host;
   size_t rd_bytes;
+  int rd_pending;
+  cudaEvent_t rd_ev[2];
   char err[512];
 };
 
@@ -310,11 +316,11 @@ extern "C" int eco_workspace_bytes(const eco_config *cfg, size_t *bytes) {
   return ECO_OK;
 }
 
-enum { GRAPH_TIMED = 0, GRAPH_ONE = 1, GRAPH_MANY = 2 };
+enum { GRAPH_TIMED = 0, GRAPH_ONE = 1, GRAPH_MANY = 2, GRAPH_READ1 = 3, GRAPH_READ2 = 4 };
 constexpr int kStepsPerGraph = 8;
 
 static void destroy_graph(eco_handle *h) {
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 5; ++k) {
     if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
     if (h->graph_src[k]) cudaGraphDestroy(h->graph_src[k]);
     h->graph[k] = nullptr;
@@ -420,11 +426,13 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
   h->grid.use_persistent = cfg->launch_mode == 0;
   h->forced = cfg->policy_variant;
   h->variant = 0;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 5; ++k) {
     h->graph[k] = nullptr;
     h->graph_src[k] = nullptr;
   }
   h->ev_used = 0;
+  h->rd_pending = 0;
+  h->rd_ev[0] = h->rd_ev[1] = nullptr;
   h->err[0] = 0;
   h->rd_bytes = (size_t)(reinterpret_cast<uint8_t *>(h->d.counters + CNT_N) -
                          reinterpret_cast<uint8_t *>(h->d.stats_total));
@@ -444,13 +452,17 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
     const long long work = std::max((long long)h->d.total_slots, (long long)h->d.total_cells / 4);
     if (work <= 4096) h->grid.persistent_blocks = 1;
   }
-  if (e == cudaSuccess) e = cudaMallocHost(&h->rd_host, h->rd_bytes);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->rd_host, 3 * h->rd_bytes);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rd_ev[0], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rd_ev[1], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev_dummy[1]);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     int r = fail(nullptr, ECO_ECUDA, "create: %s", cudaGetErrorString(e));
     if (h->rd_host) cudaFreeHost(h->rd_host);
+    for (cudaEvent_t ev : h->rd_ev)
+      if (ev) cudaEventDestroy(ev);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
     return r;
@@ -476,6 +488,8 @@ extern "C" void eco_destroy(eco_handle *h) {
   if (h->ev_dummy[0]) cudaEventDestroy(h->ev_dummy[0]);
   if (h->ev_dummy[1]) cudaEventDestroy(h->ev_dummy[1]);
   if (h->rd_host) cudaFreeHost(h->rd_host);
+  for (cudaEvent_t ev : h->rd_ev)
+    if (ev) cudaEventDestroy(ev);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -497,6 +511,7 @@ extern "C" int eco_reset(eco_handle *h) {
   CUDA_TRY(h, cudaMemsetAsync(h->d.barrier, 0, 2 * sizeof(unsigned), h->stream));
   CUDA_TRY(h, launch_reset(h->d, h->L, h->R, h->grid, h->stream));
   CUDA_TRY(h, launch_compact(h->d, h->stream));
+  h->rd_pending = 0;  // eco_step_read starts over from the reset records
   return check_status(h);
 }
 
@@ -558,11 +573,15 @@ static int build_graph(eco_handle *h, int kind) {
   if (rc) return rc;
   const bool timed = kind == GRAPH_TIMED;
   const int steps = kind == GRAPH_MANY ? kStepsPerGraph : 1;
+  const int copy_slot = kind == GRAPH_READ1 ? 1 : (kind == GRAPH_READ2 ? 2 : 0);
   cudaGraph_t g = nullptr;
   for (;;) {
     CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < steps && e == cudaSuccess; ++k) e = enqueue_step(h, timed);
+    if (e == cudaSuccess && copy_slot)
+      e = cudaMemcpyAsync(h->rd_host + copy_slot * h->rd_bytes, h->d.stats_total, h->rd_bytes,
+                          cudaMemcpyDeviceToHost, h->stream);
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (e == cudaSuccess && e2 == cudaSuccess) break;
     if (e2 == cudaSuccess && g) cudaGraphDestroy(g);
@@ -651,6 +670,8 @@ extern "C" int eco_prepare(eco_handle *h) {
   int rc = build_graph(h, GRAPH_ONE);
   if (rc == ECO_OK) rc = build_graph(h, GRAPH_MANY);
   if (rc == ECO_OK) rc = build_graph(h, GRAPH_TIMED);
+  if (rc == ECO_OK) rc = build_graph(h, GRAPH_READ1);
+  if (rc == ECO_OK) rc = build_graph(h, GRAPH_READ2);
   if (rc == ECO_OK) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return rc;
 }
@@ -710,17 +731,12 @@ extern "C" int eco_policy_bytes(eco_handle *h, int64_t *bytes, int64_t *n_alive)
   return ECO_OK;
 }
 
-extern "C" int eco_read_stats(eco_handle *h, eco_stats *total, eco_stats *last, int32_t n_envs) {
-  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
-  if (n_envs < 0 || n_envs > h->n_envs) return fail(h, ECO_EINVAL, "n_envs out of range");
-  // one asynchronous copy of the statistics and the status word into pinned
-  // memory, one synchronisation, then host-side copies
-  CUDA_TRY(h, cudaMemcpyAsync(h->rd_host, h->d.stats_total, h->rd_bytes, cudaMemcpyDeviceToHost, h->stream));
-  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+// Records of the pinned mirror slot `slot` to the caller's buffers, and the
+// status word's verdict.
+static int stats_from_mirror(eco_handle *h, int slot, eco_stats *total, eco_stats *last, int32_t n_envs) {
   const uint8_t *base = reinterpret_cast<const uint8_t *>(h->d.stats_total);
-  auto mirror = [&](const void *dev) {
-    return h->rd_host + (reinterpret_cast<const uint8_t *>(dev) - base);
-  };
+  const uint8_t *m = h->rd_host + (size_t)slot * h->rd_bytes;
+  auto mirror = [&](const void *dev) { return m + (reinterpret_cast<const uint8_t *>(dev) - base); };
   if (total) memcpy(total, mirror(h->d.stats_total), sizeof(eco_stats) * n_envs);
   if (last) memcpy(last, mirror(h->d.stats_last), sizeof(eco_stats) * n_envs);
   int32_t st = 0;
@@ -728,6 +744,38 @@ extern "C" int eco_read_stats(eco_handle *h, eco_stats *total, eco_stats *last, 
   if (st & 3) return fail(h, ECO_EINVAL, "reset: fewer non-wall cells than founders (status %d)", st);
   if (st & 4) return fail(h, ECO_ETIMEOUT, "a device-side wait ran out of its budget");
   return ECO_OK;
+}
+
+extern "C" int eco_read_stats(eco_handle *h, eco_stats *total, eco_stats *last, int32_t n_envs) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  if (n_envs < 0 || n_envs > h->n_envs) return fail(h, ECO_EINVAL, "n_envs out of range");
+  // one asynchronous copy of the statistics and the status word into pinned
+  // memory, one synchronisation, then host-side copies
+  CUDA_TRY(h, cudaMemcpyAsync(h->rd_host, h->d.stats_total, h->rd_bytes, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return stats_from_mirror(h, 0, total, last, n_envs);
+}
+
+extern "C" int eco_step_read(eco_handle *h, eco_stats *total, eco_stats *last, int32_t n_envs) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  if (n_envs < 0 || n_envs > h->n_envs) return fail(h, ECO_EINVAL, "n_envs out of range");
+  int prev = h->rd_pending;
+  if (prev == 0) {
+    // nothing in flight: the records as they stand now go to slot 2
+    CUDA_TRY(h, cudaMemcpyAsync(h->rd_host + 2 * h->rd_bytes, h->d.stats_total, h->rd_bytes,
+                                cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaEventRecord(h->rd_ev[1], h->stream));
+    prev = 2;
+  }
+  const int slot = prev == 1 ? 2 : 1;
+  int rc = build_graph(h, slot == 1 ? GRAPH_READ1 : GRAPH_READ2);
+  if (rc) return rc;
+  CUDA_TRY(h, cudaGraphLaunch(h->graph[slot == 1 ? GRAPH_READ1 : GRAPH_READ2], h->stream));
+  CUDA_TRY(h, cudaEventRecord(h->rd_ev[slot - 1], h->stream));
+  h->rd_pending = slot;
+  // the step just enqueued runs while the host waits for the previous copy
+  CUDA_TRY(h, cudaEventSynchronize(h->rd_ev[prev - 1]));
+  return stats_from_mirror(h, prev, total, last, n_envs);
 }
 
 // ---------------------------------------------------------------------------

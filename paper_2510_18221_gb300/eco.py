@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
         L.eco_step.argtypes = [H, ctypes.c_int32]
         L.eco_step_timed.argtypes = [H, ctypes.c_int32]
         L.eco_prepare.argtypes = [H]
+        L.eco_step_read.argtypes = [H, _vp, _vp, ctypes.c_int32]
         L.eco_policy_timing.argtypes = [H, ctypes.POINTER(ctypes.c_double), _i32p]
         L.eco_read_stats.argtypes = [H, _vp, _vp, ctypes.c_int32]
         L.eco_read_state.argtypes = [H, ctypes.c_int32, ctypes.POINTER(eco_state_view)]
@@ -185,6 +186,15 @@ def eco_step(h, n_steps: int) -> None:
 
 def eco_prepare(h) -> None:
     _check(lib().eco_prepare(h), h)
+
+
+def eco_step_read(h, n_envs: int):
+    """One pipelined step: returns the (total, last) records of the step the
+    previous call enqueued, while this call's step runs."""
+    tot = np.zeros((n_envs, ECO_N_STATS), np.int64)
+    last = np.zeros((n_envs, ECO_N_STATS), np.int64)
+    _check(lib().eco_step_read(h, _p(tot), _p(last), int(n_envs)), h)
+    return tot, last
 
 
 def eco_step_timed(h, n_steps: int) -> None:
