@@ -38,6 +38,12 @@
 
 namespace eco {
 
+// Asynchronous prefetch of [p, p + bytes) into L2 (p and bytes multiples of
+// 16), issued by one lane; it returns at once.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ uint4 ldg_stream(const uint4 *p) {
   uint4 r;
   asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
@@ -278,6 +284,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     cnt = 0;
   };
 
+  // At the start of the launch every warp gathers an observation with no
+  // weights in flight: the first 4 KB of each warp's first agent's weights
+  // are requested into L2 before that gather.
+  if (lane == 0 && blockIdx.x * WARPS + warp < n_alive)
+    prefetch_l2(d.wq + (int64_t)d.alive_list[blockIdx.x * WARPS + warp] * L.stride,
+                (uint32_t)min((int64_t)4096, (int64_t)L.off_w2));
   for (int i = blockIdx.x * WARPS + warp; i < n_alive; i += gridDim.x * WARPS) {
     const int slot = d.alive_list[i];
     const int env = d.env_of[slot];
