@@ -519,12 +519,10 @@ extern "C" int eco_reset(eco_handle *h) {
 static int autotune(eco_handle *h) {
   if (h->variant) return ECO_OK;
   CUDA_TRY(h, launch_compact(h->d, h->stream));
-  cudaEvent_t a, b;
-  CUDA_TRY(h, cudaEventCreate(&a));
-  CUDA_TRY(h, cudaEventCreate(&b));
-  float best_ms = 1e30f;
-  int best = 0;
+  // candidates of the requested family
   const bool sparse = h->forced < 0;
+  std::vector<int> ids;
+  std::vector<PolicyLaunch> pls;
   for (int v = 1; v <= policy_variant_count(); ++v) {
     if (policy_variant_sparse(v) != sparse) continue;
     PolicyLaunch pl;
@@ -532,23 +530,38 @@ static int autotune(eco_handle *h) {
       cudaGetLastError();
       continue;
     }
-    for (int w = 0; w < 2; ++w) CUDA_TRY(h, policy_launch(pl, h->d, h->L, h->R, h->stream, false));
-    CUDA_TRY(h, cudaEventRecord(a, h->stream));
-    for (int r = 0; r < 5; ++r) CUDA_TRY(h, policy_launch(pl, h->d, h->L, h->R, h->stream, false));
-    CUDA_TRY(h, cudaEventRecord(b, h->stream));
-    CUDA_TRY(h, cudaEventSynchronize(b));
-    float ms = 0;
-    CUDA_TRY(h, cudaEventElapsedTime(&ms, a, b));
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = v;
-      h->pl = pl;
+    ids.push_back(v);
+    pls.push_back(pl);
+  }
+  if (ids.empty()) return fail(h, ECO_ECUDA, "no policy variant could be prepared");
+  // policy-only launches (no state changes) on the current state: one
+  // warm-up each, then kRounds rounds that time kPerRound launches of every
+  // candidate in turn, so that a drift in clocks or memory state over the
+  // tuning affects every candidate alike; the lowest total wins
+  constexpr int kRounds = 3, kPerRound = 3;
+  cudaEvent_t a, b;
+  CUDA_TRY(h, cudaEventCreate(&a));
+  CUDA_TRY(h, cudaEventCreate(&b));
+  for (const PolicyLaunch &pl : pls) CUDA_TRY(h, policy_launch(pl, h->d, h->L, h->R, h->stream, false));
+  std::vector<double> total(ids.size(), 0.0);
+  for (int r = 0; r < kRounds; ++r) {
+    for (size_t c = 0; c < ids.size(); ++c) {
+      CUDA_TRY(h, cudaEventRecord(a, h->stream));
+      for (int k = 0; k < kPerRound; ++k) CUDA_TRY(h, policy_launch(pls[c], h->d, h->L, h->R, h->stream, false));
+      CUDA_TRY(h, cudaEventRecord(b, h->stream));
+      CUDA_TRY(h, cudaEventSynchronize(b));
+      float ms = 0;
+      CUDA_TRY(h, cudaEventElapsedTime(&ms, a, b));
+      total[c] += ms;
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  if (!best) return fail(h, ECO_ECUDA, "no policy variant could be prepared");
-  h->variant = best;
+  size_t best = 0;
+  for (size_t c = 1; c < ids.size(); ++c)
+    if (total[c] < total[best]) best = c;
+  h->variant = ids[best];
+  h->pl = pls[best];
   return ECO_OK;
 }
 
