@@ -316,8 +316,9 @@ int eco_workspace_bytes(const eco_config *cfg, size_t *bytes);
 
 /* Create a handle.  dev_workspace: caller-allocated device memory of at
  * least the reported size (256-byte aligned); stream: cudaStream_t or
- * NULL.  Selects the policy-kernel variant (autotuning on the workspace
- * when cfg->policy_variant == 0).  On failure *out is NULL. */
+ * NULL.  A variant forced by cfg->policy_variant > 0 is set up here; with
+ * 0 or -1 the variant is autotuned on the state at eco_prepare or at the
+ * first step.  On failure *out is NULL. */
 int eco_create(const eco_config *cfg, void *dev_workspace, size_t bytes,
                void *stream, eco_handle **out);
 

@@ -539,9 +539,16 @@ static int autotune(eco_handle *h) {
   // candidate in turn, so that a drift in clocks or memory state over the
   // tuning affects every candidate alike; the lowest total wins
   constexpr int kRounds = 3, kPerRound = 3;
-  cudaEvent_t a, b;
-  CUDA_TRY(h, cudaEventCreate(&a));
-  CUDA_TRY(h, cudaEventCreate(&b));
+  struct EventPair {  // destroyed on every return path
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  CUDA_TRY(h, cudaEventCreate(&ev.a));
+  CUDA_TRY(h, cudaEventCreate(&ev.b));
+  cudaEvent_t a = ev.a, b = ev.b;
   for (const PolicyLaunch &pl : pls) CUDA_TRY(h, policy_launch(pl, h->d, h->L, h->R, h->stream, false));
   std::vector<double> total(ids.size(), 0.0);
   for (int r = 0; r < kRounds; ++r) {
@@ -555,8 +562,6 @@ static int autotune(eco_handle *h) {
       total[c] += ms;
     }
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
   size_t best = 0;
   for (size_t c = 1; c < ids.size(); ++c)
     if (total[c] < total[best]) best = c;

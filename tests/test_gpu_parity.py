@@ -1,5 +1,7 @@
 """Parity of the CUDA step (through the C-ABI) with the CPU oracle, on the
 GPU.  Lock-step rules are in tests/harness.py."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -244,6 +246,26 @@ def test_step_read_pipelined_records():
     assert np.array_equal(tot, want[0][0])
     a.close()
     b.close()
+
+
+def test_api_argument_errors():
+    """Bad arguments come back as ECO_EINVAL with a message, and the handle
+    stays usable."""
+    from paper_2510_18221_gb300 import eco
+    w = workloads.get("small")
+    env = eco.Env(w)
+    env.reset()
+    for call in (lambda: eco.eco_step(env.h, -1),
+                 lambda: eco.eco_read_stats(env.h, 2),
+                 lambda: eco.eco_step_read(env.h, 2)):
+        with pytest.raises(eco.EcoError) as ex:
+            call()
+        assert ex.value.code == eco.ECO_EINVAL and str(ex.value)
+    view = eco.eco_state_view()
+    assert eco.lib().eco_read_state(env.h, 1, ctypes.byref(view)) == eco.ECO_EINVAL   # no env 1
+    env.step(2)
+    assert env.stats()[0]["step"] == 2
+    env.close()
 
 
 def test_per_phase_launch_form_lockstep():
