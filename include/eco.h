@@ -22,9 +22,10 @@
  *     eco_workspace_bytes() reports, 256-byte aligned, and keeps it alive
  *     until eco_destroy().  The library carves every device array out of
  *     it, allocates no other device memory, and never frees caller memory.
- *     Each handle holds one small pinned host buffer (the statistics and
- *     status word, about 2 x n_envs x 8 x ECO_N_STATS bytes), freed by
- *     eco_destroy(), through which eco_read_stats() copies in one transfer.
+ *     Each handle holds three small pinned host buffers for the statistics
+ *     and status word (about 2 x n_envs x 8 x ECO_N_STATS bytes each; one
+ *     for eco_read_stats(), two for eco_step_read()), freed by
+ *     eco_destroy(); a read copies into one of them in one transfer.
  *   - Streams: all device work is enqueued on the stream given to
  *     eco_create() (a cudaStream_t passed as void*; NULL = legacy default
  *     stream).  eco_reset() and eco_step() are asynchronous.  eco_read_*()
