@@ -225,24 +225,26 @@ def test_step_read_pipelined_records():
     previous call enqueued (at the first call after reset, the records as
     they stand), with the state equal to eco_step's throughout."""
     from paper_2510_18221_gb300 import eco
-    w = workloads.scaled("mid", 64, 600, 500, precision="bf16", e_init=185)
+    w = [workloads.scaled("mid", 64, 600, 500, precision="bf16", e_init=185),
+         workloads.scaled("mid", 32, 300, 250, seed=7, precision="bf16", e_init=185)]
     a, b = eco.Env(w), eco.Env(w)
     for x in (a, b):
         x.reset()
-    want = [eco.eco_read_stats(b.h, 1)]
+    want = [eco.eco_read_stats(b.h, 2)]
     for _ in range(12):
         b.step(1)
-        want.append(eco.eco_read_stats(b.h, 1))
+        want.append(eco.eco_read_stats(b.h, 2))
     for k in range(12):
-        tot, last = eco.eco_step_read(a.h, 1)
+        tot, last = eco.eco_step_read(a.h, 2)
         assert np.array_equal(tot, want[k][0]) and np.array_equal(last, want[k][1]), k
-    tot, last = eco.eco_read_stats(a.h, 1)
+    tot, last = eco.eco_read_stats(a.h, 2)
     assert np.array_equal(tot, want[12][0]) and np.array_equal(last, want[12][1])
-    sa, sb = a.read_state(0), b.read_state(0)
-    for k in harness.STATE_KEYS:
-        assert np.array_equal(sa[k], sb[k]), k
+    for e in range(2):
+        sa, sb = a.read_state(e), b.read_state(e)
+        for k in harness.STATE_KEYS:
+            assert np.array_equal(sa[k], sb[k]), (e, k)
     a.reset()   # the pipeline starts over
-    tot, _ = eco.eco_step_read(a.h, 1)
+    tot, _ = eco.eco_step_read(a.h, 2)
     assert np.array_equal(tot, want[0][0])
     a.close()
     b.close()
