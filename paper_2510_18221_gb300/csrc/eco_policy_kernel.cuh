@@ -284,13 +284,24 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     cnt = 0;
   };
 
+  // Balanced rounds (BF16, FP32): the launch needs R = ceil(n_alive / G)
+  // rounds of its G resident warps; only the first ceil(n_alive / R) warps
+  // take agents, so every round keeps the same number of warps streaming
+  // instead of the last one running on a fraction of them.  (CTAs are
+  // spread over the SMs in turn, so the idle warps are spread too.)  Each
+  // agent is still one warp's, computed the same way.  The FP8 form, whose
+  // warps spend more of their time issuing, loses more from the fewer warps
+  // in every round than it gains in the last one, and keeps all G.
+  const int G = gridDim.x * WARPS;
+  const int rounds = (n_alive + G - 1) / G;
+  const int G_eff = (PREC != PREC_FP8 && rounds > 0) ? (n_alive + rounds - 1) / rounds : G;
+  const int w0 = blockIdx.x * WARPS + warp;
   // At the start of the launch every warp gathers an observation with no
   // weights in flight: the first 4 KB of each warp's first agent's weights
   // are requested into L2 before that gather.
-  if (lane == 0 && blockIdx.x * WARPS + warp < n_alive)
-    prefetch_l2(d.wq + (int64_t)d.alive_list[blockIdx.x * WARPS + warp] * L.stride,
-                (uint32_t)min((int64_t)4096, (int64_t)L.off_w2));
-  for (int i = blockIdx.x * WARPS + warp; i < n_alive; i += gridDim.x * WARPS) {
+  if (lane == 0 && w0 < G_eff && w0 < n_alive)
+    prefetch_l2(d.wq + (int64_t)d.alive_list[w0] * L.stride, (uint32_t)min((int64_t)4096, (int64_t)L.off_w2));
+  for (int i = w0 < G_eff ? w0 : n_alive; i < n_alive; i += G_eff) {
     const int slot = d.alive_list[i];
     const int env = d.env_of[slot];
     if (env != e_cur) {
