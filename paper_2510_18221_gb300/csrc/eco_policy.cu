@@ -24,6 +24,8 @@ static const VariantDesc kVariants[] = {
     {"warp-per-agent, 4 warps/CTA, 8 units in flight per lane, 64 registers", 4, 8, false},
     {"input-sparse W_in rows, 8 warps/CTA, 4 units in flight per lane", 8, 4, true},
     {"input-sparse W_in rows, 4 warps/CTA, 8 units in flight per lane, 64 registers", 4, 8, true},
+    {"warp-per-agent, 4 warps/CTA, 8 units in flight per lane, 56 registers", 4, 8, false},
+    {"warp-per-agent, 4 warps/CTA, 4 units in flight per lane, 56 registers", 4, 4, false},
 };
 static const int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 

@@ -545,7 +545,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
 // ---------------------------------------------------------------------------
 // Variant k (1-based) of one precision and hidden width.  Variants 7 and 8
 // are the input-sparse forms of 3 and 6 (they stream only the W_in rows of
-// nonzero inputs); the autotuner keeps the two families apart.
+// nonzero inputs); the autotuner keeps the two families apart.  Variants 9
+// and 10 sit between the 48- and 64-register ones: 56 registers, 36 warps
+// per SM.
 // ---------------------------------------------------------------------------
 template <int PREC, int H>
 PolicyFn policy_pick_variant(int variant) {
@@ -558,6 +560,8 @@ PolicyFn policy_pick_variant(int variant) {
     case 6: return k_policy<PREC, H, 4, 8, 8, false>;
     case 7: return k_policy<PREC, H, 8, 4, 5, true>;
     case 8: return k_policy<PREC, H, 4, 8, 8, true>;
+    case 9: return k_policy<PREC, H, 4, 8, 9, false>;
+    case 10: return k_policy<PREC, H, 4, 4, 9, false>;
     default: return nullptr;
   }
 }

@@ -60,7 +60,7 @@ def test_rule_flags(flags):
     _run(w, 10)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
 def test_every_policy_variant(variant, prec):
     w = workloads.scaled("mid", 64, 512, 450, precision=prec)
