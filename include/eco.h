@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define ECO_ABI_VERSION 4
+#define ECO_ABI_VERSION 5
 
 /* Status codes. */
 #define ECO_OK 0
@@ -407,15 +407,19 @@ const char *eco_policy_variant_name(int32_t k);
  * does not support the cooperative form). */
 int eco_launch_mode(const eco_handle *h, int32_t *mode, int32_t *blocks);
 
-/* Like eco_step, and also records a CUDA-event pair around the policy
- * kernel of every step, on the library stream, inside a one-step graph.
- * The results are identical; each event-record node adds a few us to the
- * step, so eco_step's graphs have none.
- * eco_policy_timing() synchronises, then returns the summed policy-kernel
- * time in milliseconds and the number of timed steps since its last call
- * (at most 4096 steps are buffered; more returns ECO_EINVAL). */
+/* Like eco_step, and also times policy-kernel launches with a CUDA-event
+ * pair on the library stream, inside the step graphs: the first step of
+ * every graph of 8 steps (the rest of n_steps untimed), or, for n_steps
+ * below 8, every step in one-step graphs.  The results are identical; an
+ * event-record node adds a few us to its step, so only one step in 8
+ * carries them and eco_step's graphs have none.
+ * eco_policy_timing() synchronises, then returns, over the launches timed
+ * since its last call: the summed policy-kernel time in milliseconds, their
+ * number, and (agents may be NULL) the summed count of agents they
+ * processed (at most 4096 launches are buffered, and eco_policy_timing must
+ * come within 4096 steps of them; more launches return ECO_EINVAL). */
 int eco_step_timed(eco_handle *h, int32_t n_steps);
-int eco_policy_timing(eco_handle *h, double *total_ms, int32_t *n_timed);
+int eco_policy_timing(eco_handle *h, double *total_ms, int32_t *n_timed, int64_t *agents);
 
 /* Run only the policy phase (observe + MLP + sample) of the current state
  * n_iters times, for timing and for the policy-parity tests; the world

@@ -51,10 +51,16 @@ struct eco_handle {
   // on the critical path between two kernels, so the untimed graphs have
   // none, and a graph of several steps saves the launch gap between graphs.
   // [GRAPH_READ1], [GRAPH_READ2]: one step, then a copy of the statistics
-  // into pinned slot 1 or 2 (eco_step_read)
-  cudaGraphExec_t graph[5];
-  cudaGraph_t graph_src[5];  // kept alive: their node handles address the execs' nodes
-  cudaGraphNode_t ev_node[2];  // in graph[GRAPH_TIMED]
+  // into pinned slot 1 or 2 (eco_step_read); [GRAPH_TIMED_MANY]:
+  // kStepsPerGraph steps with event-record nodes around the first step's
+  // policy kernel only (eco_step_timed: one timed launch per graph)
+  cudaGraphExec_t graph[6];
+  cudaGraph_t graph_src[6];  // kept alive: their node handles address the execs' nodes
+  cudaGraphNode_t ev_node[6][2];  // in the timed graphs
+  // steps run since reset (a host shadow of the device's step counter) and
+  // the first step of every timed launch not yet reported
+  long long steps_done;
+  std::vector<long long> timed_steps;
   cudaEvent_t ev_dummy[2];
   std::vector<cudaEvent_t> ev_pool;  // pairs
   int ev_used;
@@ -276,6 +282,7 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   // copy brings both to the host
   D.counters = k.take<int32_t>(CNT_N);
   D.step = k.take<long long>(1);
+  D.alive_at_step = k.take<int32_t>(kAliveRing);
   D.hist = k.take<uint32_t>((size_t)E * 65536);
   D.place_prefix = k.take<unsigned long long>(E);
   D.place_remaining = k.take<int32_t>(E);
@@ -316,11 +323,12 @@ extern "C" int eco_workspace_bytes(const eco_config *cfg, size_t *bytes) {
   return ECO_OK;
 }
 
-enum { GRAPH_TIMED = 0, GRAPH_ONE = 1, GRAPH_MANY = 2, GRAPH_READ1 = 3, GRAPH_READ2 = 4 };
+enum { GRAPH_TIMED = 0, GRAPH_ONE = 1, GRAPH_MANY = 2, GRAPH_READ1 = 3, GRAPH_READ2 = 4, GRAPH_TIMED_MANY = 5 };
+constexpr int kNumGraphs = 6;
 constexpr int kStepsPerGraph = 8;
 
 static void destroy_graph(eco_handle *h) {
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < kNumGraphs; ++k) {
     if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
     if (h->graph_src[k]) cudaGraphDestroy(h->graph_src[k]);
     h->graph[k] = nullptr;
@@ -426,11 +434,12 @@ extern "C" int eco_create(const eco_config *cfg, void *dev_workspace, size_t byt
   h->grid.use_persistent = cfg->launch_mode == 0;
   h->forced = cfg->policy_variant;
   h->variant = 0;
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < kNumGraphs; ++k) {
     h->graph[k] = nullptr;
     h->graph_src[k] = nullptr;
   }
   h->ev_used = 0;
+  h->steps_done = 0;
   h->rd_pending = 0;
   h->rd_ev[0] = h->rd_ev[1] = nullptr;
   h->err[0] = 0;
@@ -512,6 +521,7 @@ extern "C" int eco_reset(eco_handle *h) {
   CUDA_TRY(h, launch_reset(h->d, h->L, h->R, h->grid, h->stream));
   CUDA_TRY(h, launch_compact(h->d, h->stream));
   h->rd_pending = 0;  // eco_step_read starts over from the reset records
+  h->steps_done = 0;
   return check_status(h);
 }
 
@@ -599,14 +609,14 @@ static int build_graph(eco_handle *h, int kind) {
   if (h->graph[kind]) return ECO_OK;
   int rc = autotune(h);
   if (rc) return rc;
-  const bool timed = kind == GRAPH_TIMED;
-  const int steps = kind == GRAPH_MANY ? kStepsPerGraph : 1;
+  const bool timed = kind == GRAPH_TIMED || kind == GRAPH_TIMED_MANY;
+  const int steps = (kind == GRAPH_MANY || kind == GRAPH_TIMED_MANY) ? kStepsPerGraph : 1;
   const int copy_slot = kind == GRAPH_READ1 ? 1 : (kind == GRAPH_READ2 ? 2 : 0);
   cudaGraph_t g = nullptr;
   for (;;) {
     CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = enqueue_step(h, timed);
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = enqueue_step(h, timed && k == 0);
     if (e == cudaSuccess && copy_slot)
       e = cudaMemcpyAsync(h->rd_host + copy_slot * h->rd_bytes, h->d.stats_total, h->rd_bytes,
                           cudaMemcpyDeviceToHost, h->stream);
@@ -639,8 +649,8 @@ static int build_graph(eco_handle *h, int kind) {
       if (t == cudaGraphNodeTypeEventRecord) {
         cudaEvent_t ev;
         CUDA_TRY(h, cudaGraphEventRecordNodeGetEvent(nodes[i], &ev));
-        if (ev == h->ev_dummy[0]) h->ev_node[0] = nodes[i], ++found;
-        if (ev == h->ev_dummy[1]) h->ev_node[1] = nodes[i], ++found;
+        if (ev == h->ev_dummy[0]) h->ev_node[kind][0] = nodes[i], ++found;
+        if (ev == h->ev_dummy[1]) h->ev_node[kind][1] = nodes[i], ++found;
       }
     }
     if (found != 2) {
@@ -662,32 +672,46 @@ static int step_impl(eco_handle *h, int32_t n_steps, bool timed) {
   if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
   if (n_steps < 0) return fail(h, ECO_EINVAL, "n_steps < 0");
   if (n_steps == 0) return ECO_OK;
+  const int many = n_steps / kStepsPerGraph, rest = n_steps % kStepsPerGraph;
   if (!timed) {
-    const int many = n_steps / kStepsPerGraph, rest = n_steps % kStepsPerGraph;
     int rc = many ? build_graph(h, GRAPH_MANY) : ECO_OK;
     if (rc == ECO_OK && rest) rc = build_graph(h, GRAPH_ONE);
     if (rc) return rc;
     for (int i = 0; i < many; ++i) CUDA_TRY(h, cudaGraphLaunch(h->graph[GRAPH_MANY], h->stream));
     for (int i = 0; i < rest; ++i) CUDA_TRY(h, cudaGraphLaunch(h->graph[GRAPH_ONE], h->stream));
+    h->steps_done += n_steps;
     return ECO_OK;
   }
-  int rc = build_graph(h, GRAPH_TIMED);
+  // one timed launch per graph of kStepsPerGraph steps (the first step's
+  // policy kernel), the remaining steps untimed; fewer steps than a graph:
+  // every step timed, in one-step graphs
+  const int kind = many ? GRAPH_TIMED_MANY : GRAPH_TIMED;
+  const int launches = many ? many : rest;
+  const int per = many ? kStepsPerGraph : 1;
+  int rc = build_graph(h, kind);
+  if (rc == ECO_OK && many && rest) rc = build_graph(h, GRAPH_ONE);
   if (rc) return rc;
-  cudaGraphExec_t gx = h->graph[GRAPH_TIMED];
-  if (h->ev_used + n_steps > 4096) return fail(h, ECO_EINVAL, "more than 4096 timed steps buffered");
-  while ((int)h->ev_pool.size() < 2 * (h->ev_used + n_steps)) {
+  cudaGraphExec_t gx = h->graph[kind];
+  if (h->ev_used + launches > 4096) return fail(h, ECO_EINVAL, "more than 4096 timed launches buffered");
+  while ((int)h->ev_pool.size() < 2 * (h->ev_used + launches)) {
     cudaEvent_t ev;
     CUDA_TRY(h, cudaEventCreate(&ev));
     h->ev_pool.push_back(ev);
   }
-  for (int i = 0; i < n_steps; ++i) {
-    CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(gx, h->ev_node[0], h->ev_pool[2 * h->ev_used]));
-    CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(gx, h->ev_node[1], h->ev_pool[2 * h->ev_used + 1]));
+  for (int i = 0; i < launches; ++i) {
+    CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(gx, h->ev_node[kind][0], h->ev_pool[2 * h->ev_used]));
+    CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(gx, h->ev_node[kind][1], h->ev_pool[2 * h->ev_used + 1]));
     ++h->ev_used;
+    h->timed_steps.push_back(h->steps_done);
     CUDA_TRY(h, cudaGraphLaunch(gx, h->stream));
+    h->steps_done += per;
   }
-  CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(gx, h->ev_node[0], h->ev_dummy[0]));
-  CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(gx, h->ev_node[1], h->ev_dummy[1]));
+  CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(gx, h->ev_node[kind][0], h->ev_dummy[0]));
+  CUDA_TRY(h, cudaGraphExecEventRecordNodeSetEvent(gx, h->ev_node[kind][1], h->ev_dummy[1]));
+  if (many && rest) {
+    for (int i = 0; i < rest; ++i) CUDA_TRY(h, cudaGraphLaunch(h->graph[GRAPH_ONE], h->stream));
+    h->steps_done += rest;
+  }
   return ECO_OK;
 }
 
@@ -698,6 +722,7 @@ extern "C" int eco_prepare(eco_handle *h) {
   int rc = build_graph(h, GRAPH_ONE);
   if (rc == ECO_OK) rc = build_graph(h, GRAPH_MANY);
   if (rc == ECO_OK) rc = build_graph(h, GRAPH_TIMED);
+  if (rc == ECO_OK) rc = build_graph(h, GRAPH_TIMED_MANY);
   if (rc == ECO_OK) rc = build_graph(h, GRAPH_READ1);
   if (rc == ECO_OK) rc = build_graph(h, GRAPH_READ2);
   if (rc == ECO_OK) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -705,7 +730,7 @@ extern "C" int eco_prepare(eco_handle *h) {
 }
 extern "C" int eco_step_timed(eco_handle *h, int32_t n_steps) { return step_impl(h, n_steps, true); }
 
-extern "C" int eco_policy_timing(eco_handle *h, double *total_ms, int32_t *n_timed) {
+extern "C" int eco_policy_timing(eco_handle *h, double *total_ms, int32_t *n_timed, int64_t *agents) {
   if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   double tot = 0;
@@ -714,9 +739,18 @@ extern "C" int eco_policy_timing(eco_handle *h, double *total_ms, int32_t *n_tim
     CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]));
     tot += ms;
   }
+  if (agents) {
+    // the agent counts the policy kernel wrote at the timed steps
+    std::vector<int32_t> ring(kAliveRing);
+    CUDA_TRY(h, cudaMemcpy(ring.data(), h->d.alive_at_step, sizeof(int32_t) * kAliveRing, cudaMemcpyDeviceToHost));
+    long long a = 0;
+    for (long long t : h->timed_steps) a += ring[(size_t)(t & (kAliveRing - 1))];
+    *agents = a;
+  }
   if (total_ms) *total_ms = tot;
   if (n_timed) *n_timed = h->ev_used;
   h->ev_used = 0;
+  h->timed_steps.clear();
   return ECO_OK;
 }
 
@@ -799,6 +833,7 @@ extern "C" int eco_step_read(eco_handle *h, eco_stats *total, eco_stats *last, i
   int rc = build_graph(h, slot == 1 ? GRAPH_READ1 : GRAPH_READ2);
   if (rc) return rc;
   CUDA_TRY(h, cudaGraphLaunch(h->graph[slot == 1 ? GRAPH_READ1 : GRAPH_READ2], h->stream));
+  h->steps_done += 1;
   CUDA_TRY(h, cudaEventRecord(h->rd_ev[slot - 1], h->stream));
   h->rd_pending = slot;
   // the step just enqueued runs while the host waits for the previous copy
@@ -953,6 +988,7 @@ extern "C" int eco_write_state(eco_handle *h, int32_t env, const eco_state_view 
     // all environments share one step counter
     long long st = *in->step;
     CUDA_TRY(h, cudaMemcpyAsync(h->d.step, &st, sizeof st, cudaMemcpyHostToDevice, s));
+    h->steps_done = st;
     CUDA_TRY(h, cudaStreamSynchronize(s));
   }
   CUDA_TRY(h, launch_recount(h->d, h->R, s));

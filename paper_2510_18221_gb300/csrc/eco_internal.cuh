@@ -290,6 +290,7 @@ struct Dev {
   long long *stats_total;  // [n_envs][N_ST]
   long long *stats_last;   // [n_envs][N_ST]
   long long *step;         // [1] current step t (all environments)
+  int32_t *alive_at_step;  // [kAliveRing] agents alive at the start of step t, at t % kAliveRing
   float *master;           // [total_slots][mstride / 4]
   uint8_t *wq;             // [total_slots][stride] streamed copy (or == master)
   uint32_t *hist;          // [n_envs][65536] placement radix select
@@ -310,6 +311,8 @@ struct Dev {
   int32_t *a_water;        // [total_slots] water carried
   int32_t *a_bio;          // [total_slots] biomass carried
 };
+
+constexpr int kAliveRing = 4096;
 
 enum : int {
   CNT_N_ALIVE = 0,

@@ -268,6 +268,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
 
   const int n_alive = d.counters[CNT_N_ALIVE];
   const uint32_t t = (uint32_t)d.step[0];
+  // the step's agent count, for the byte count of timed launches
+  if (apply_moves && blockIdx.x == 0 && threadIdx.x == 0) d.alive_at_step[t & (kAliveRing - 1)] = n_alive;
   const int k = R.patch_k, RR = k >> 1, kk = k * k;
   // ceil(2^32 / k) for odd k (k = 0: no patch, the gather loop is empty)
   const uint32_t kdiv = k > 0 ? 0xFFFFFFFFu / (uint32_t)k + 1u : 0u;

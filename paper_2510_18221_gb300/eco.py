@@ -21,7 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libeco.so")
 
-ECO_ABI_VERSION = 4
+ECO_ABI_VERSION = 5
 ECO_OK, ECO_EINVAL, ECO_ENOMEM, ECO_ECUDA, ECO_ETIMEOUT, ECO_EABI = 0, -1, -2, -3, -4, -5
 ECO_FP32, ECO_BF16, ECO_FP8_E4M3 = 0, 1, 2
 ECO_AUTO_EAT, ECO_ROTATE_OBS, ECO_CANCEL_ALL, ECO_GREEDY = 1, 2, 4, 8
@@ -115,7 +115,8 @@ def lib() -> ctypes.CDLL:
         L.eco_step_timed.argtypes = [H, ctypes.c_int32]
         L.eco_prepare.argtypes = [H]
         L.eco_step_read.argtypes = [H, _vp, _vp, ctypes.c_int32]
-        L.eco_policy_timing.argtypes = [H, ctypes.POINTER(ctypes.c_double), _i32p]
+        L.eco_policy_timing.argtypes = [H, ctypes.POINTER(ctypes.c_double), _i32p,
+                                        ctypes.POINTER(ctypes.c_int64)]
         L.eco_read_stats.argtypes = [H, _vp, _vp, ctypes.c_int32]
         L.eco_read_state.argtypes = [H, ctypes.c_int32, ctypes.POINTER(eco_state_view)]
         L.eco_write_state.argtypes = [H, ctypes.c_int32, ctypes.POINTER(eco_state_view)]
@@ -202,9 +203,10 @@ def eco_step_timed(h, n_steps: int) -> None:
 
 
 def eco_policy_timing(h):
-    ms, n = ctypes.c_double(), ctypes.c_int32()
-    _check(lib().eco_policy_timing(h, ctypes.byref(ms), ctypes.byref(n)), h)
-    return ms.value, n.value
+    """(summed policy-kernel ms, timed launches, agents in those launches)."""
+    ms, n, ag = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().eco_policy_timing(h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(ag)), h)
+    return ms.value, n.value, ag.value
 
 
 def eco_read_stats(h, n_envs: int):

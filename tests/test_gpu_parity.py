@@ -194,7 +194,8 @@ def test_step_graph_forms_bit_identical(launch_mode):
     """eco_step(n) replays graphs of 8 steps and of one step, eco_step_timed
     a one-step graph with event-record nodes around the policy kernel, and
     eco_prepare builds them ahead: every array and statistic must match
-    after 8k + r steps taken in each of these ways."""
+    after 8k + r steps taken in each of these ways, and eco_policy_timing
+    reports the timed launches' agents."""
     from paper_2510_18221_gb300 import eco
     envs = [workloads.scaled("mid", s, n, k, seed=50 + i, precision="bf16", e_init=185)
             for i, (s, n, k) in enumerate([(64, 600, 500), (128, 2048, 1500)])]
@@ -203,11 +204,14 @@ def test_step_graph_forms_bit_identical(launch_mode):
         x.reset()
     many.prepare()
     many.step(19)                 # 2 x 8 steps + 3 x 1
+    per_step = []                 # agents processed by each step
     for _ in range(19):
         ones.step(1)
-    timed.step_timed(19)
-    _, n_timed = timed.policy_timing()
-    assert n_timed == 19
+        per_step.append(sum(st["agent_steps"] for st in ones.stats("last")))
+    timed.step_timed(19)          # 2 x 8 steps, the first of each timed, + 3 x 1
+    ms, n_timed, agents = timed.policy_timing()
+    # the timed launches are the policy kernels of steps 0 and 8
+    assert n_timed == 2 and ms > 0 and agents == per_step[0] + per_step[8]
     for e in range(len(envs)):
         sm, so, st = many.read_state(e), ones.read_state(e), timed.read_state(e)
         for k in harness.STATE_KEYS:
