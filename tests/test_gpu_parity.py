@@ -220,6 +220,11 @@ def test_step_graph_forms_bit_identical(launch_mode):
         assert np.array_equal(many.read_params(e), ones.read_params(e))
         assert np.array_equal(many.read_params(e), timed.read_params(e))
     assert many.stats()[0]["step"] == 19 and sum(s["births"] for s in many.stats()) > 0
+    # fewer steps than a graph: every step timed, in one-step graphs
+    timed.reset()
+    timed.step_timed(3)
+    ms, n_timed, agents = timed.policy_timing()
+    assert n_timed == 3 and ms > 0 and agents == sum(per_step[:3])
     for x in (many, ones, timed):
         x.close()
 
