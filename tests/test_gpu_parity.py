@@ -67,6 +67,32 @@ def test_every_policy_variant(variant, prec):
     _run(w, 3, policy_variant=variant)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_policy_variants_bit_identical(prec):
+    """Every dense variant computes each agent in the same order (units in
+    ascending order per lane, a fixed reduce-scatter), whatever its warps,
+    units in flight or registers, and whichever warp takes the agent: the
+    autotuner's choice does not change a single bit of logits or state."""
+    from paper_2510_18221_gb300 import eco
+    w = workloads.scaled("mid", 128, 2048, 1500, precision=prec, e_init=185)
+    envs = [eco.Env(w, policy_variant=v) for v in (1, 2, 6, 9, 10)]
+    for x in envs:
+        x.reset()
+    for t in range(6):
+        for x in envs:
+            x.step(1)
+        ref_l, ref_a = envs[0].read_policy_io(0)
+        ref_s = envs[0].read_state(0)
+        for x in envs[1:]:
+            lg, ac = x.read_policy_io(0)
+            assert np.array_equal(lg, ref_l) and np.array_equal(ac, ref_a), t
+            st = x.read_state(0)
+            for k in harness.STATE_KEYS:
+                assert np.array_equal(st[k], ref_s[k]), (t, k)
+    for x in envs:
+        x.close()
+
+
 def test_edge_no_founders_and_full_slots():
     _run(workloads.get("small", init_alive=0), 3)
     _run(workloads.get("small", init_alive=256, e_init=250), 5)   # births with no free slot
