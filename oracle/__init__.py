@@ -156,6 +156,8 @@ def lib():
             L.orc_init_params.argtypes = [cfgp, ctypes.c_int32, _P]
             L.orc_observe.argtypes = [cfgp, stp, ctypes.c_int32, _P]
             L.orc_effective_params.argtypes = [cfgp, _P, ctypes.c_int, _P]
+            L.orc_weight_mask.argtypes = [cfgp, _P]
+            L.orc_quantise.argtypes = [cfgp, _P, _P, _P]
             L.orc_mlp.argtypes = [cfgp, _P, _P, _P]
             L.orc_policy.argtypes = [cfgp, stp, ctypes.c_int, ctypes.c_double, _P, _P, _P, _P]
             L.orc_mutate.argtypes = [cfgp, ctypes.c_int64, ctypes.c_int32, _P, _P]
@@ -339,6 +341,37 @@ class Oracle:
         row = np.ascontiguousarray(self.master[slot])
         lib().orc_effective_params(ctypes.byref(self.c), _ptr(row), int(use_master), _ptr(w))
         return w
+
+    def weight_mask(self) -> np.ndarray:
+        """bool[P]: True where logical parameter p is a weight (False: a
+        bias or the temperature)."""
+        m = np.zeros(self.P, np.uint8)
+        lib().orc_weight_mask(ctypes.byref(self.c), _ptr(m))
+        return m.astype(bool)
+
+    def fp8_rows(self) -> int:
+        """Weight rows that carry an FP8 scale: W_in, every hidden layer, the head."""
+        L = self.cfg.get("n_hidden", 1) if self.c.policy_form == PAPER_FORM else 1
+        H = self.cfg["hidden"]
+        return H + L * H + self.A
+
+    def quantise(self, rows: np.ndarray):
+        """The streamed copy of master rows [n][P] (float32) in logical
+        order: (codes, scales).  BF16: codes uint16 [n][P], scales None.
+        FP8: codes uint8 [n][P] and row scales float32 [n][fp8_rows()].
+        Bias positions hold the code of 0."""
+        rows = np.ascontiguousarray(rows, np.float32).reshape(-1, self.P)
+        n = rows.shape[0]
+        if self.c.precision == BF16:
+            codes, scales = np.zeros((n, self.P), np.uint16), None
+        elif self.c.precision == FP8:
+            codes, scales = np.zeros((n, self.P), np.uint8), np.zeros((n, self.fp8_rows()), np.float32)
+        else:
+            raise ValueError("the FP32 form has no streamed copy")
+        for i in range(n):
+            lib().orc_quantise(ctypes.byref(self.c), _ptr(rows[i]), _ptr(codes[i]),
+                               _ptr(scales[i]) if scales is not None else None)
+        return codes, scales
 
     def mlp(self, w: np.ndarray, x: np.ndarray) -> np.ndarray:
         w = np.ascontiguousarray(w, np.float64)

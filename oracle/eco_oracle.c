@@ -809,6 +809,59 @@ void orc_effective_params(const orc_config *c, const float *m, int use_master, d
   }
 }
 
+/* Is logical parameter p a weight (1) or a bias / the temperature (0)?
+ * mask[p] for every p < P. */
+void orc_weight_mask(const orc_config *c, uint8_t *mask) {
+  orc_shape s;
+  int p;
+  shape_of(c, &s);
+  for (p = 0; p < s.P; p++) mask[p] = (uint8_t)is_weight(&s, p);
+}
+
+/* The streamed copy of one master row, as codes in logical order (the
+ * weights the reduced-precision policy multiplies with, Sec. 3.3):
+ *   BF16 form: codes is uint16_t[P], the bfloat16 RNE code of every weight;
+ *   FP8 form:  codes is uint8_t[P]; weight row r of each layer (W_in rows of
+ *              D entries, then every hidden layer's rows of H, then the
+ *              head's rows of H) has scale s_r = max|w| / 448 (1 for an
+ *              all-zero row), written to scales[r], and the e4m3 code of
+ *              w / s_r (IEEE binary32 division, satfinite RNE).
+ * Bias and temperature positions hold the code of 0 (they stay FP32 in the
+ * streamed copy).  Nothing is written for the FP32 form. */
+void orc_quantise(const orc_config *c, const float *m, void *codes, float *scales) {
+  orc_shape s;
+  int p, row;
+  shape_of(c, &s);
+  if (c->precision == ORC_BF16) {
+    uint16_t *q = (uint16_t *)codes;
+    for (p = 0; p < s.P; p++) q[p] = is_weight(&s, p) ? orc_bf16_rne(m[p]) : 0;
+    return;
+  }
+  if (c->precision != ORC_FP8) return;
+  {
+    uint8_t *q = (uint8_t *)codes;
+    for (p = 0; p < s.P; p++) q[p] = 0;
+    for (row = 0; row < s.H + s.L * s.H + s.A; row++) {
+      int start, n, j;
+      float sc;
+      if (row < s.H) {
+        start = s.oWin + row * s.D;
+        n = s.D;
+      } else if (row < s.H + s.L * s.H) {
+        int l = (row - s.H) / s.H, o = (row - s.H) % s.H;
+        start = s.oWh + l * (s.H * s.H + s.H) + o * s.H;
+        n = s.H;
+      } else {
+        start = s.oWout + (row - s.H - s.L * s.H) * s.H;
+        n = s.H;
+      }
+      sc = orc_fp8_row_scale(m + start, n);
+      scales[row] = sc;
+      for (j = 0; j < n; j++) q[start + j] = orc_e4m3_encode(m[start + j] / sc);
+    }
+  }
+}
+
 static double activate(const orc_shape *s, double v) {
   if (s->relu) return v > 0.0 ? v : 0.0;
   return tanh(v);

@@ -86,3 +86,65 @@ def test_fp8_row_scale_definition():
         want = np.float32(np.max(np.abs(row))) / np.float32(448.0)  # IEEE binary32 division
         assert oracle.fp8_row_scale(row) == float(want)
     assert oracle.fp8_row_scale(np.zeros(64, np.float32)) == 1.0
+
+
+def _logical_rows(D, H, A, L, ns):
+    """Weight rows of the logical parameter order (W_in [H][D], ns input
+    biases [H], L x (W_l [H][H], b_l [H]), W_out [A][H], then the head bias
+    or the temperature): (start, length) of every weight row, in the order
+    W_in, hidden layers, head."""
+    rows = [(o * D, D) for o in range(H)]
+    hid0 = H * D + ns * H
+    for l in range(L):
+        rows += [(hid0 + l * (H * H + H) + o * H, H) for o in range(H)]
+    out0 = hid0 + L * (H * H + H)
+    rows += [(out0 + a * H, H) for a in range(A)]
+    return rows
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("form,over", [
+    ("plain", dict()),
+    ("plain", dict(patch_k=5, n_scalars=4, hidden=32, n_actions=6)),
+    ("paper", dict(n_hidden=1, hidden=32)),
+    ("paper", dict(n_hidden=3, hidden=128)),
+    ("paper", dict(n_hidden=2, patch_k=0)),           # blind: D below H
+])
+def test_quantise_matches_torch_row_by_row(prec, form, over):
+    """The oracle's streamed copy of whole master rows (codes in logical
+    order, FP8 row scales) against torch's bfloat16 / float8_e4m3fn
+    conversions applied row by row to the weights, with numpy's binary32
+    max / 448 as the row scale; biases and the temperature keep the code 0."""
+    from paper_2510_18221_gb300 import workloads
+    w = workloads.get("mid", precision=prec, policy_form=form, side=16, slots=4, init_alive=0,
+                      **over)
+    orc = oracle.Oracle(w)
+    D, H, A = orc.D, w["hidden"], w["n_actions"]
+    L = w.get("n_hidden", 1) if form == "paper" else 1
+    ns = 1 if form == "plain" else (1 if w["patch_k"] > 0 else 0) + (1 if w["n_scalars"] >= 8 else 0) + 1
+    rows = _logical_rows(D, H, A, L, ns)
+    n_w = sum(n for _, n in rows)
+    wmask = np.zeros(orc.P, bool)
+    for s, n in rows:
+        wmask[s:s + n] = True
+    assert n_w == H * D + L * H * H + A * H
+    assert np.array_equal(orc.weight_mask(), wmask)
+    m = inputs.random_params(orc.P, n_rows=5, seed=11)
+    m[1] = 0.0                                   # all-zero rows: scale 1
+    m[2, :n_w // 3] *= np.float32(1e-4)          # e4m3 subnormal codes
+    m[3] *= np.float32(50.0)                     # large magnitudes
+    codes, scales = orc.quantise(m)
+    assert not codes[:, ~wmask].any()
+    for i in range(m.shape[0]):
+        if prec == "bf16":
+            assert np.array_equal(codes[i, wmask], _bf16_torch(m[i, wmask]))
+            continue
+        assert scales.shape[1] == len(rows)
+        for r, (s, n) in enumerate(rows):
+            row = m[i, s:s + n]
+            mx = np.float32(np.max(np.abs(row)))
+            want_s = np.float32(1.0) if mx == 0 else mx / np.float32(448.0)
+            assert scales[i, r] == want_s, (i, r)
+            q = (row / want_s).astype(np.float32)     # binary32 division
+            want = torch.from_numpy(q).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+            assert np.array_equal(codes[i, s:s + n], want), (i, r)
