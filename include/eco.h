@@ -323,11 +323,20 @@ int eco_workspace_bytes(const eco_config *cfg, size_t *bytes);
 int eco_create(const eco_config *cfg, void *dev_workspace, size_t bytes,
                void *stream, eco_handle **out);
 
-/* Reset every environment (Sec. 3.2, 3.3): walls and food by Bernoulli
+/* Reset every environment (Sec. 3.2, 3.3), each from its own Philox seed
+ * (env_seed, or the last eco_reset_seed): walls and food by Bernoulli
  * draws, founders on the K non-wall cells with the smallest placement keys
  * (slots 0..K-1 in ascending cell order), random facings, energy e_init,
  * weights N(0, 1/fan_in), zero biases; statistics cleared.  Asynchronous. */
 int eco_reset(eco_handle *h);
+
+/* eco_reset after re-seeding: environment e takes the Philox seed
+ * (uint32_t)(seed + e) (the low 32 bits; Philox keys are (seed, stream)
+ * word pairs) in place of its env_seed, for this reset and every step after
+ * it, until the next eco_reset_seed.  A new seed needs no new handle and no
+ * new capture of the step graphs.  Asynchronous, except that it waits for
+ * the host-to-device copy of the environment table. */
+int eco_reset_seed(eco_handle *h, uint64_t seed);
 
 /* Advance every environment by n_steps >= 0 steps.  Asynchronous; replays
  * CUDA graphs of 8 steps and of one step (built at the first call that
@@ -392,6 +401,14 @@ int eco_write_params(eco_handle *h, int32_t env, int32_t slot0, int32_t n, const
 int eco_read_streamed(eco_handle *h, int32_t env, int32_t slot0, int32_t n,
                       void *codes, float *row_scales);
 
+/* The FP32 biases (and tau) that the streamed copy of slots
+ * [slot0, slot0 + n) of env carries beside its codes, which the policy
+ * kernel reads instead of the masters' (Sec. 3.3: only the weights are
+ * streamed in the reduced precision).  Host array bias [n][nB], nB = P
+ * minus the weight count, each slot's values in ascending logical
+ * parameter position.  ECO_EINVAL for the FP32 precision.  Synchronises. */
+int eco_read_streamed_bias(eco_handle *h, int32_t env, int32_t slot0, int32_t n, float *bias);
+
 /* Logits [slots][A] (FP32) and actions [slots] of the last step's policy
  * phase for env (dead slots hold stale values).  Synchronises. */
 int eco_read_policy_io(eco_handle *h, int32_t env, float *logits, uint8_t *actions);
@@ -426,6 +443,21 @@ int eco_policy_timing(eco_handle *h, double *total_ms, int32_t *n_timed, int64_t
  * state does not change.  Asynchronous. */
 int eco_policy_only(eco_handle *h, int32_t n_iters);
 
+/* Failure-detection test hook (off unless called; cleared by eco_reset).
+ * The persistent environment kernel separates its phases with grid
+ * barriers whose waits are bounded; this arms the next steps so that CTA
+ * absent_cta leaves that kernel before its first barrier and every wait
+ * gives up after poll_budget polls (a few ms for 10^5).  The other CTAs'
+ * waits then run out: the status word records the timeout, every CTA
+ * leaves at its barrier, the later steps' environment kernels return at
+ * once, and the next eco_read_stats / eco_step_read returns ECO_ETIMEOUT.
+ * The world state is then partly stepped; eco_reset (or eco_reset_seed)
+ * clears the barrier, the status word and these test words.  ECO_EINVAL
+ * when the persistent form with more than one CTA is not in use
+ * (eco_launch_mode; it is decided at the first eco_step) or for an
+ * argument out of range.  Synchronises. */
+int eco_arm_barrier_timeout(eco_handle *h, int32_t absent_cta, int32_t poll_budget);
+
 /* Algorithmic bytes the policy phase must read for the current alive
  * population (weights of every alive agent in the streamed precision,
  * biases and scales in FP32); synchronises. */
@@ -443,15 +475,19 @@ int eco_policy_bytes(eco_handle *h, int64_t *bytes, int64_t *n_alive);
  * entries (8 MiB), which every GPU that loads the library holds until the
  * process exits.
  *
- * Rule (the movement phase of eco_step for one world): agent i at cell
- * pos[i] (y * side + x) with action act[i] and facing facing_in[i]; a move
- * action (1 N, 2 S, 3 E, 4 W) faces its direction and claims the
- * neighbouring cell unless blocked[cell] is nonzero (a wall, or an agent
- * there when the step began); among claimants of one cell the highest
- * Philox draw of stream CLAIM_MOVE at counter (step, i, 0, 0) under key
- * (seed, 7) wins, ties to the lower i; actions 6 / 7 turn left / right.
- * Outputs: facing_out[i], pos_out[i] (the new cell, or pos[i]) and
- * moved[i] (0/1).
+ * Rule (the movement phase of eco_step for one world, under
+ * ECO_RULES_SIMPLE without ECO_CANCEL_ALL; the paper and terrain rules'
+ * forward / rotate actions and the cancel-all rule are not covered): agent
+ * i at cell pos[i] (y * side + x) with action act[i] and facing
+ * facing_in[i]; a move action (1 N, 2 S, 3 E, 4 W) faces its direction and
+ * claims the neighbouring cell unless blocked[cell] is nonzero (a wall, or
+ * an agent there when the step began); among claimants of one cell the
+ * highest Philox draw of stream CLAIM_MOVE at counter (step, i, 0, 0)
+ * under key (seed, 7) wins, ties to the lower i; actions 6 / 7 turn left /
+ * right.  An agent whose pos[i] lies outside [0, side * side) does not
+ * move (its facing still follows its action).  Outputs: facing_out[i],
+ * pos_out[i] (the new cell, or pos[i]) and moved[i] (0/1).  pos_out may be
+ * pos and facing_out may be facing_in (an in-place update).
  *
  * All array arguments are device pointers the caller allocates: pos,
  * pos_out int32[n_agents]; act, facing_in, facing_out, moved
@@ -459,7 +495,10 @@ int eco_policy_bytes(eco_handle *h, int64_t *bytes, int64_t *n_alive);
  * stream (cudaStream_t or NULL) and is asynchronous.
  * Returns ECO_EINVAL if side is odd or < 4, if side * side exceeds
  * ECO_NOALLOC_MAX_CELLS, or for a null array with n_agents > 0;
- * ECO_ECUDA if a CUDA call fails.  It calls no cudaMalloc / cudaFree.
+ * ECO_ECUDA if a CUDA call or launch fails, and also, without launching
+ * anything or clearing it, when a CUDA error left by earlier work is
+ * already pending on the calling thread.  The message is
+ * eco_last_error(NULL).  It calls no cudaMalloc / cudaFree.
  *
  * The first call on each device looks up the scratch array's device
  * address (cudaGetSymbolAddress) with that device current; make that

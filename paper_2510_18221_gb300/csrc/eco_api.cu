@@ -85,6 +85,14 @@ static int fail(eco_handle *h, int code, const char *fmt, ...) {
   return code;
 }
 
+int eco::set_global_error(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
 #define CUDA_TRY(h, call)                                                                     \
   do {                                                                                        \
     cudaError_t e_ = (call);                                                                  \
@@ -269,7 +277,7 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.logits = k.take<float>((size_t)slots * L.A);
   D.alive_list = k.take<int32_t>(slots);
   D.tile_counts = k.take<int32_t>(compact_tiles((int)slots));
-  D.barrier = k.take<unsigned>(2);
+  D.barrier = k.take<unsigned>(BAR_N);
   D.births = k.take<int2>(slots);
   D.free_list = k.take<int32_t>(slots);
   D.bflag = k.take<uint8_t>(slots);
@@ -516,13 +524,28 @@ static int check_status(eco_handle *h) {
 
 extern "C" int eco_reset(eco_handle *h) {
   if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
-  // also clears the status word and the persistent form's barrier
-  CUDA_TRY(h, cudaMemsetAsync(h->d.barrier, 0, 2 * sizeof(unsigned), h->stream));
+  // also clears the status word, the persistent form's barrier and its
+  // failure-detection test words
+  CUDA_TRY(h, cudaMemsetAsync(h->d.barrier, 0, BAR_N * sizeof(unsigned), h->stream));
   CUDA_TRY(h, launch_reset(h->d, h->L, h->R, h->grid, h->stream));
   CUDA_TRY(h, launch_compact(h->d, h->stream));
   h->rd_pending = 0;  // eco_step_read starts over from the reset records
   h->steps_done = 0;
   return check_status(h);
+}
+
+extern "C" int eco_reset_seed(eco_handle *h, uint64_t seed) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  for (int e = 0; e < h->n_envs; ++e) {
+    const uint32_t se = (uint32_t)(seed + (uint64_t)e);
+    h->seed[e] = se;
+    h->env_host[e].seed = se;
+  }
+  // the step graphs read the environment table from device memory, so the
+  // new seeds reach them without a re-capture
+  CUDA_TRY(h, cudaMemcpyAsync(h->env_dev, h->env_host.data(), sizeof(EnvDesc) * h->n_envs,
+                              cudaMemcpyHostToDevice, h->stream));
+  return eco_reset(h);
 }
 
 // Choose the fastest policy variant on the current state (autotuner).
@@ -760,6 +783,18 @@ extern "C" int eco_policy_only(eco_handle *h, int32_t n_iters) {
   if (rc) return rc;
   CUDA_TRY(h, launch_compact(h->d, h->stream));
   for (int i = 0; i < n_iters; ++i) CUDA_TRY(h, policy_launch(h->pl, h->d, h->L, h->R, h->stream, false));
+  return ECO_OK;
+}
+
+extern "C" int eco_arm_barrier_timeout(eco_handle *h, int32_t absent_cta, int32_t poll_budget) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  const bool pers = h->grid.use_persistent && h->grid.persistent_blocks > 1;
+  if (!pers) return fail(h, ECO_EINVAL, "the persistent launch form with more than one CTA is not in use");
+  if (absent_cta < 0 || absent_cta >= h->grid.persistent_blocks) return fail(h, ECO_EINVAL, "absent_cta out of range");
+  if (poll_budget < 1) return fail(h, ECO_EINVAL, "poll_budget must be >= 1");
+  const unsigned words[2] = {(unsigned)absent_cta + 1u, (unsigned)poll_budget};
+  CUDA_TRY(h, cudaMemcpyAsync(h->d.barrier + BAR_ABSENT_CTA, words, sizeof words, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return ECO_OK;
 }
 
@@ -1109,6 +1144,29 @@ extern "C" int eco_read_streamed(eco_handle *h, int32_t env, int32_t slot0, int3
       }
     }
     if (row_scales && L.es == 1) memcpy(row_scales + (size_t)i * nB, blk + L.off_scale, 4 * (size_t)nB);
+  }
+  return ECO_OK;
+}
+
+extern "C" int eco_read_streamed_bias(eco_handle *h, int32_t env, int32_t slot0, int32_t n, float *bias) {
+  int rc = check_range(h, env, slot0, n);
+  if (rc) return rc;
+  if (h->R.precision == ECO_FP32) return fail(h, ECO_EINVAL, "no streamed copy in the FP32 form");
+  if (n == 0) return ECO_OK;
+  if (!bias) return fail(h, ECO_EINVAL, "null output");
+  const Layout &L = h->L;
+  std::vector<uint8_t> buf((size_t)n * L.stride);
+  const int g0 = h->env_host[env].slot_off + slot0;
+  CUDA_TRY(h, cudaMemcpyAsync(buf.data(), h->d.wq + (size_t)g0 * L.stride, buf.size(), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  // the block holds the biases in physical order k (master element nW + k);
+  // the caller gets them in ascending logical position
+  std::vector<std::pair<int, int>> order((size_t)L.nB);
+  for (int k = 0; k < L.nB; ++k) order[k] = {layout_logical(L, L.nW + k), k};
+  std::sort(order.begin(), order.end());
+  for (int i = 0; i < n; ++i) {
+    const uint8_t *blk = buf.data() + (size_t)i * L.stride + L.off_bias;
+    for (int r = 0; r < L.nB; ++r) memcpy(bias + (size_t)i * L.nB + r, blk + 4 * (size_t)order[r].second, 4);
   }
   return ECO_OK;
 }

@@ -1080,15 +1080,15 @@ constexpr unsigned kBarrierSpinLimit = 40u * 1000u * 1000u;  // x >= 64 ns: > 2.
 constexpr int kStatusTimeout = 4;
 
 // Grid-wide barrier for a co-resident (cooperative) grid: sense reversal
-// on a generation counter.  The wait is bounded: when it runs out, the
-// status word records a timeout and every CTA leaves the kernel at its next
-// barrier.  Returns false when the kernel must stop.
-__device__ bool grid_sync(const Dev &d, unsigned nblocks, int *s_flag) {
+// on a generation counter.  The wait is bounded by `budget` polls: when it
+// runs out, the status word records a timeout and every CTA leaves the
+// kernel at its next barrier.  Returns false when the kernel must stop.
+__device__ bool grid_sync(const Dev &d, unsigned nblocks, unsigned budget, int *s_flag) {
   __syncthreads();
   if (nblocks == 1) return true;  // one CTA: the block barrier is the grid barrier
   if (threadIdx.x == 0) {
-    cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(d.barrier[1]);
-    cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(d.barrier[0]);
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(d.barrier[BAR_GEN]);
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(d.barrier[BAR_COUNT]);
     cuda::atomic_ref<int, cuda::thread_scope_device> status(d.counters[CNT_STATUS]);
     const unsigned g = gen.load(cuda::memory_order_acquire);
     __threadfence();
@@ -1099,7 +1099,7 @@ __device__ bool grid_sync(const Dev &d, unsigned nblocks, int *s_flag) {
     } else {
       unsigned it = 0;
       while (gen.load(cuda::memory_order_acquire) == g) {
-        if (++it > kBarrierSpinLimit) {
+        if (++it > budget) {
           status.fetch_or(kStatusTimeout, cuda::memory_order_relaxed);
           ok = 0;
           break;
@@ -1121,22 +1121,34 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   __shared__ float s_scale[kMutRows];
   __shared__ int s_flag;
   const unsigned nb = gridDim.x;
+  // A timeout recorded by an earlier launch (the status word keeps it until
+  // eco_reset) stops this step at once, before any barrier count changes.
+  if (threadIdx.x == 0)
+    s_flag = cuda::atomic_ref<int, cuda::thread_scope_device>(d.counters[CNT_STATUS]).load(
+                 cuda::memory_order_relaxed) & kStatusTimeout;
+  __syncthreads();
+  if (s_flag) return;
+  // Failure-detection test words, 0 unless armed by eco_arm_barrier_timeout
+  // (cleared by eco_reset): a CTA that leaves before its first barrier, and
+  // the poll budget of every wait.
+  if (d.barrier[BAR_ABSENT_CTA] == blockIdx.x + 1u) return;
+  const unsigned budget = d.barrier[BAR_BUDGET] ? d.barrier[BAR_BUDGET] : kBarrierSpinLimit;
   const int g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   // each thread's first alive-list entry, loaded once for all phases
   const int first = g0 < d.counters[CNT_N_ALIVE] ? d.alive_list[g0] : -1;
   ph_move_apply_eat(d, R, L.A, g0, gs, first);
-  if (!grid_sync(d, nb, &s_flag)) return;
+  if (!grid_sync(d, nb, budget, &s_flag)) return;
   ph_attack_claim(d, R, g0, gs, first);
-  if (!grid_sync(d, nb, &s_flag)) return;
+  if (!grid_sync(d, nb, budget, &s_flag)) return;
   ph_metab_death(d, R, g0, gs, first);
-  if (!grid_sync(d, nb, &s_flag)) return;
+  if (!grid_sync(d, nb, budget, &s_flag)) return;
   // regrowth (with photosynthesis and the flow's transfers) needs only the
   // state after the deaths, and birth claims read only wall and agent bits,
   // which regrowth keeps: the two share an interval
   ph_birth_claim(d, R, g0, gs, first);
   ph_regrow(d, R, g0, gs);
   if (R.rules == RULES_TERRAIN) ph_flow_out(d, g0, gs);
-  if (!grid_sync(d, nb, &s_flag)) return;
+  if (!grid_sync(d, nb, budget, &s_flag)) return;
   // Every claim is in, and the count of claimants does not change again
   // before the last barrier, so every CTA takes the same branch.  On a step
   // without a birth claim, slot assignment and mutation have nothing to do
@@ -1144,11 +1156,11 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   if (cuda::atomic_ref<int, cuda::thread_scope_device>(d.counters[CNT_CONTENDERS]).load(
           cuda::memory_order_relaxed) != 0) {
     ph_birth_assign(d, R, blockIdx.x, gridDim.x, S);
-    if (!grid_sync(d, nb, &s_flag)) return;
+    if (!grid_sync(d, nb, budget, &s_flag)) return;
     ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale);
   }
   ph_compact_count(d, blockIdx.x, gridDim.x, S.sh);
-  if (!grid_sync(d, nb, &s_flag)) return;
+  if (!grid_sync(d, nb, budget, &s_flag)) return;
   if (R.rules == RULES_TERRAIN) ph_flow_in(d, g0, gs);
   ph_compact_scatter(d, blockIdx.x, gridDim.x, S.sh);
   if (blockIdx.x == gridDim.x - 1) ph_finish(d, R);

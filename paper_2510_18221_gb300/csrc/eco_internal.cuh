@@ -280,7 +280,7 @@ struct Dev {
   float *logits;
   int32_t *alive_list;
   int32_t *tile_counts;  // [compact tiles] alive slots per tile of 4096
-  unsigned *barrier;     // [2] grid barrier of the persistent form: count, generation
+  unsigned *barrier;     // [BAR_N] grid barrier of the persistent form and its test words
   int32_t *counters;    // [0] n_alive, [1] n_births, [2] status, [3..] spare
   int2 *births;         // (parent global, child global)
   int32_t *free_list;   // per env: slot_off + rank
@@ -313,6 +313,18 @@ struct Dev {
 };
 
 constexpr int kAliveRing = 4096;
+
+// Words of Dev::barrier: the persistent form's grid barrier (arrival count,
+// generation) and two failure-detection test words (0 = off): one more than
+// the index of a CTA that leaves before its first barrier, and the poll
+// budget of the barrier's waits.
+enum : int {
+  BAR_COUNT = 0,
+  BAR_GEN = 1,
+  BAR_ABSENT_CTA = 2,
+  BAR_BUDGET = 3,
+  BAR_N = 4,
+};
 
 enum : int {
   CNT_N_ALIVE = 0,
@@ -473,5 +485,9 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *total, int *sh /
 
 // Launch helpers (host).
 int grid_for(long long n, int threads, int max_blocks);
+
+// Record the message eco_last_error(NULL) returns (entry points without a
+// handle); returns code.
+int set_global_error(int code, const char *fmt, ...);
 
 }  // namespace eco

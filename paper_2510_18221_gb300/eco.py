@@ -111,6 +111,8 @@ def lib() -> ctypes.CDLL:
         L.eco_workspace_bytes.argtypes = [cp, ctypes.POINTER(ctypes.c_size_t)]
         L.eco_create.argtypes = [cp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]
         L.eco_reset.argtypes = [H]
+        L.eco_reset_seed.argtypes = [H, ctypes.c_uint64]
+        L.eco_arm_barrier_timeout.argtypes = [H, ctypes.c_int32, ctypes.c_int32]
         L.eco_step.argtypes = [H, ctypes.c_int32]
         L.eco_step_timed.argtypes = [H, ctypes.c_int32]
         L.eco_prepare.argtypes = [H]
@@ -125,6 +127,7 @@ def lib() -> ctypes.CDLL:
         L.eco_read_params.argtypes = [H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp]
         L.eco_write_params.argtypes = [H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp]
         L.eco_read_streamed.argtypes = [H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
+        L.eco_read_streamed_bias.argtypes = [H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp]
         L.eco_read_policy_io.argtypes = [H, ctypes.c_int32, _vp, _vp]
         L.eco_policy_variants.argtypes = [H, _i32p, _i32p]
         L.eco_policy_variant_name.argtypes = [ctypes.c_int32]
@@ -179,6 +182,15 @@ def eco_create(cfg: eco_config, workspace_ptr: int, nbytes: int, stream_ptr: int
 
 def eco_reset(h) -> None:
     _check(lib().eco_reset(h), h)
+
+
+def eco_reset_seed(h, seed: int) -> None:
+    _check(lib().eco_reset_seed(h, int(seed) & 0xFFFFFFFFFFFFFFFF), h)
+
+
+def eco_arm_barrier_timeout(h, absent_cta: int, poll_budget: int) -> None:
+    """Failure-detection test hook (see include/eco.h)."""
+    _check(lib().eco_arm_barrier_timeout(h, int(absent_cta), int(poll_budget)), h)
 
 
 def eco_step(h, n_steps: int) -> None:
@@ -345,6 +357,10 @@ class Env:
     def reset(self) -> None:
         eco_reset(self.h)
 
+    def reset_seed(self, seed: int) -> None:
+        """Reset with environment e seeded (seed + e) mod 2^32."""
+        eco_reset_seed(self.h, seed)
+
     def step(self, n: int = 1) -> None:
         eco_step(self.h, n)
 
@@ -444,6 +460,16 @@ class Env:
         _check(lib().eco_read_streamed(self.h, int(env), int(slot0), int(n), _p(codes),
                                        _p(scales)), self.h)
         return codes, (scales if prec == ECO_FP8_E4M3 else None)
+
+    def read_streamed_bias(self, env: int = 0, slot0: int = 0, n: int = 1) -> np.ndarray:
+        """FP32 biases of the streamed copy, [n][nB] in ascending logical
+        position (nB = P minus the weights)."""
+        H, A = self.H, self.A
+        layers = self.cfg.n_hidden if self.cfg.policy_form == ECO_POLICY_PAPER else 1
+        n_w = self.D * H + layers * H * H + A * H
+        out = np.zeros((n, self.P - n_w), np.float32)
+        _check(lib().eco_read_streamed_bias(self.h, int(env), int(slot0), int(n), _p(out)), self.h)
+        return out
 
     def read_policy_io(self, env: int = 0):
         S = self.envs[env]["slots"]

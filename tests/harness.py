@@ -18,7 +18,12 @@ Rules (written in the tests):
     (FP32 Box-Muller on the GPU vs FP64 in the oracle, a few ulp);
   * colour traits: bit-exact, except a newborn's, which is held to the
     child-parameter bound (the same Box-Muller difference) and then
-    replaced by the oracle's.
+    replaced by the oracle's;
+  * a child's streamed BF16 / FP8 copy, which the mutation kernel derives
+    from the child's new FP32 master: codes, FP8 row scales and FP32 biases
+    bit-exact against the oracle's quantiser applied to that same GPU
+    master (RNE and IEEE division are deterministic), checked before the
+    oracle's child replaces it.
 """
 import numpy as np
 
@@ -50,6 +55,44 @@ def runs(slots):
         else:
             out.append([s, s + 1])
     return out
+
+
+def read_rows(env, slots, e=0):
+    """GPU FP32 masters of `slots`, read run by run: {slot: row}."""
+    out = {}
+    for a, b in runs(slots):
+        rows = env.read_params(e, a, b - a)
+        for i in range(b - a):
+            out[a + i] = rows[i]
+    return out
+
+
+def check_streamed(env, orc, masters, e=0, where=""):
+    """The streamed copy of every slot in `masters` ({slot: GPU master row})
+    against the oracle's quantiser applied to that master: codes, FP8 row
+    scales and the FP32 biases, bit for bit.  Returns the slots checked."""
+    if orc.c.precision == oracle.FP32 or not masters:
+        return 0
+    wmask = orc.weight_mask()
+    for a, b in runs(masters):
+        m = np.stack([masters[s] for s in range(a, b)])
+        codes, scales = env.read_streamed(e, a, b - a)
+        bias = env.read_streamed_bias(e, a, b - a)
+        want_codes, want_scales = orc.quantise(m)
+        if not np.array_equal(codes, want_codes):
+            i, p = np.argwhere(codes != want_codes)[0]
+            raise AssertionError("%s: streamed code of slot %d param %d: gpu %d oracle %d (master %r)" %
+                                 (where, a + i, p, codes[i, p], want_codes[i, p], float(m[i, p])))
+        if want_scales is not None and not np.array_equal(scales.view(np.uint32), want_scales.view(np.uint32)):
+            i, r = np.argwhere(scales.view(np.uint32) != want_scales.view(np.uint32))[0]
+            raise AssertionError("%s: FP8 row scale %d of slot %d: gpu %r oracle %r" %
+                                 (where, r, a + i, float(scales[i, r]), float(want_scales[i, r])))
+        want_bias = np.ascontiguousarray(m[:, ~wmask])
+        if not np.array_equal(bias.view(np.uint32), want_bias.view(np.uint32)):
+            i, k = np.argwhere(bias.view(np.uint32) != want_bias.view(np.uint32))[0]
+            raise AssertionError("%s: streamed bias %d of slot %d: gpu %r master %r" %
+                                 (where, k, a + i, float(bias[i, k]), float(want_bias[i, k])))
+    return len(masters)
 
 
 def push_params(env, orc, slots, e=0, chunk=4096):
@@ -139,6 +182,68 @@ def check_policy(env, orc, pol, alive0, e=0, where=""):
     return err, act, diff
 
 
+def new_report(vs_master=False):
+    rep = {"steps": 0, "ambiguous": 0, "births": 0, "gpu_births": 0, "max_logit_err": 0.0,
+           "max_param_err": 0.0, "streamed_checked": 0}
+    if vs_master:
+        rep.update({"agents": 0, "agree": 0, "master_err_max": 0.0, "master_err_sum": 0.0})
+    return rep
+
+
+def check_step(env, orc, pol, alive0, rep, e=0, tag="", ref=None):
+    """After env stepped once from the state orc holds (pol: the oracle's
+    policy on that state, alive0 its alive mask): check world e of env
+    against the oracle's step, advance the oracle, and bring the GPU back
+    onto the oracle's trajectory where the two may differ (near-ties,
+    children's parameters).  ref: the oracle's policy on the FP32 masters,
+    for the precision report."""
+    err, act, diff = check_policy(env, orc, pol, alive0, e, tag)
+    rep["max_logit_err"] = max(rep["max_logit_err"], err)
+    if ref is not None and alive0.any():
+        lg, _ = env.read_policy_io(e)
+        r = ref["logits"][alive0]
+        rel = np.abs(lg[alive0].astype(np.float64) - r).max(axis=1) / np.maximum(1.0, np.abs(r).max(axis=1))
+        rep["master_err_max"] = max(rep["master_err_max"], float(rel.max()))
+        rep["master_err_sum"] += float(rel.sum())
+        rep["agents"] += int(alive0.sum())
+        rep["agree"] += int((act[alive0] == ref["action"][alive0]).sum())
+    last = env.stats("last")[e]
+    gs = env.read_state(e)
+    if diff.any():
+        rep["ambiguous"] += int(diff.sum())
+        alt = orc.copy()
+        alt_act = pol["action"].copy()
+        alt_act[diff] = act[diff]
+        st_alt, births_alt = alt.transition(alt_act)
+        compare_state(gs, alt, tag + " (valid alternative)")
+        compare_stats(last, st_alt, tag + " (valid alternative)")
+        compare_colours(gs, alt, births_alt, tag + " (valid alternative)")
+        rep["streamed_checked"] += check_streamed(
+            env, orc, read_rows(env, [c for _, c in births_alt], e), e, tag + " (valid alternative)")
+        rep["gpu_births"] += len(births_alt)
+        st, births = orc.transition(pol["action"])
+        env.write_state(e, orc.arrays())
+        push_params(env, orc, [c for _, c in births] + [c for _, c in births_alt], e)
+    else:
+        st, births = orc.transition(pol["action"])
+        compare_state(gs, orc, tag)
+        compare_stats(last, st, tag)
+        rep["max_param_err"] = max(rep["max_param_err"], compare_colours(gs, orc, births, tag))
+        rep["gpu_births"] += len(births)
+        if births:
+            push_colours(env, orc, e)
+            kids = [c for _, c in births]
+            got = read_rows(env, kids, e)
+            for p, c in births:
+                rep["max_param_err"] = max(rep["max_param_err"], check_params(
+                    got[c], orc.master[c], orc.master[p], tag + " child %d" % c))
+            rep["streamed_checked"] += check_streamed(env, orc, got, e, tag)
+            push_params(env, orc, kids, e)
+    rep["births"] += len(births)
+    rep["steps"] += 1
+    return st
+
+
 def lockstep(env, orc, steps, e=0, where="", vs_master=False):
     """Advance both sides `steps` steps in lock-step; returns a report.
 
@@ -146,52 +251,30 @@ def lockstep(env, orc, steps, e=0, where="", vs_master=False):
     parameters (the unquantised policy) and records how far the GPU's
     logits are from it and how often the GPU's action agrees with it
     (quantisation error: reported, not bounded)."""
-    rep = {"steps": 0, "ambiguous": 0, "births": 0, "max_logit_err": 0.0, "max_param_err": 0.0}
-    if vs_master:
-        rep.update({"agents": 0, "agree": 0, "master_err_max": 0.0, "master_err_sum": 0.0})
+    rep = new_report(vs_master)
     for t in range(steps):
         tag = "%s step %d" % (where, int(orc.step[0]))
         alive0 = orc.alive.astype(bool).copy()
         pol = orc.policy(tol=GAP_TOL)
         ref = orc.policy(use_master=True, tol=GAP_TOL) if vs_master else None
         env.step(1)
-        err, act, diff = check_policy(env, orc, pol, alive0, e, tag)
-        rep["max_logit_err"] = max(rep["max_logit_err"], err)
-        if vs_master and alive0.any():
-            lg, _ = env.read_policy_io(e)
-            r = ref["logits"][alive0]
-            rel = np.abs(lg[alive0].astype(np.float64) - r).max(axis=1) / np.maximum(1.0, np.abs(r).max(axis=1))
-            rep["master_err_max"] = max(rep["master_err_max"], float(rel.max()))
-            rep["master_err_sum"] += float(rel.sum())
-            rep["agents"] += int(alive0.sum())
-            rep["agree"] += int((act[alive0] == ref["action"][alive0]).sum())
-        last = env.stats("last")[e]
-        gs = env.read_state(e)
-        if diff.any():
-            rep["ambiguous"] += int(diff.sum())
-            alt = orc.copy()
-            alt_act = pol["action"].copy()
-            alt_act[diff] = act[diff]
-            st_alt, births_alt = alt.transition(alt_act)
-            compare_state(gs, alt, tag + " (valid alternative)")
-            compare_stats(last, st_alt, tag + " (valid alternative)")
-            compare_colours(gs, alt, births_alt, tag + " (valid alternative)")
-            st, births = orc.transition(pol["action"])
-            env.write_state(e, orc.arrays())
-            push_params(env, orc, [c for _, c in births] + [c for _, c in births_alt], e)
-        else:
-            st, births = orc.transition(pol["action"])
-            compare_state(gs, orc, tag)
-            compare_stats(last, st, tag)
-            rep["max_param_err"] = max(rep["max_param_err"], compare_colours(gs, orc, births, tag))
-            if births:
-                push_colours(env, orc, e)
-                kids = [c for _, c in births]
-                for p, c in births:
-                    got = env.read_params(e, c, 1)[0]
-                    rep["max_param_err"] = max(rep["max_param_err"], check_params(
-                        got, orc.master[c], orc.master[p], tag + " child %d" % c))
-                push_params(env, orc, kids, e)
-        rep["births"] += len(births)
-        rep["steps"] += 1
+        check_step(env, orc, pol, alive0, rep, e, tag, ref)
     return rep
+
+
+def lockstep_batch(env, orcs, steps, where=""):
+    """Lock-step of a batched handle: every step advances all its worlds at
+    once, then each world e is checked against its own oracle orcs[e] as
+    lockstep checks a single world.  Returns one report per world, each
+    with the statistics of every step ("per_step")."""
+    reps = [new_report() for _ in orcs]
+    for r in reps:
+        r["per_step"] = []
+    for t in range(steps):
+        alive0 = [o.alive.astype(bool).copy() for o in orcs]
+        pols = [o.policy(tol=GAP_TOL) for o in orcs]
+        env.step(1)
+        for e, o in enumerate(orcs):
+            tag = "%s world %d step %d" % (where, e, int(o.step[0]))
+            reps[e]["per_step"].append(check_step(env, o, pols[e], alive0[e], reps[e], e, tag))
+    return reps

@@ -8,8 +8,11 @@
   properties that hold at any size: the statistics equal a recount of the
   state, one agent per cell, the occupancy map equals the agents'
   positions, no agent on a wall, every alive energy positive.
+* The paper-scale workload in lock-step with the oracle for 1000 steps:
+  integer state, actions and statistics bit-exact, logits within 1e-5, and
+  every child's streamed BF16 copy bit-exact against the oracle's quantiser.
 * Opt-in (ECO_LONG=1): 1000-step lock-steps of the mid workload (seeds 0-3)
-  and of the paper-scale workload.
+  and 300-step lock-steps of the paper and terrain rule sets.
 """
 import os
 
@@ -118,10 +121,13 @@ def test_long_mid_1000_steps(seed):
     print("mid seed %d 1000-step lock-step:" % seed, rep)
 
 
-@pytest.mark.skipif(not LONG, reason="long lock-step runs only with ECO_LONG=1")
 def test_long_paper_1000_steps():
+    """1024x1024 torus, 65,536 slots, 50,000 founders, 371 -> 64 -> 64 -> 9
+    BF16, 1000 steps in lock-step with the oracle."""
     rep = _lockstep(workloads.get("paper"), 1000, sample=128)
     print("paper-scale 1000-step lock-step:", rep)
+    assert rep["steps"] == 1000 and rep["births"] > 1000
+    assert rep["streamed_checked"] == rep["gpu_births"]
 
 
 def test_paperform_workload_lockstep():

@@ -160,31 +160,151 @@ def test_batched_equals_single_and_oracle():
             assert np.array_equal(aa[alive], ab[alive])
             assert np.array_equal(la[b["alive"].astype(bool) | alive], lb[b["alive"].astype(bool) | alive])
             assert batch.stats("last")[e] == s.stats("last")[0]
-    # and every environment of the batch against its oracle for 3 steps
+    # and every environment of the batch against its oracle, with its
+    # statistics, through near-ties (the harness's valid-set rule)
     batch2 = eco.Env(envs)
+    for o in orcs:
+        o.reset()
     batch2.reset()
     for e, o in enumerate(orcs):
-        o.reset()
-        harness.push_params(batch2, o, range(o.S), e)
-    for e, o in enumerate(orcs):
         harness.compare_state(batch2.read_state(e), o, "batched reset env %d" % e)
-    for t in range(3):
-        pols = []
-        alive0 = []
-        for o in orcs:
-            alive0.append(o.alive.astype(bool).copy())
-            pols.append(o.policy())
-        batch2.step(1)
-        for e, o in enumerate(orcs):
-            err, act, diff = harness.check_policy(batch2, o, pols[e], alive0[e], e, "batched")
-            if diff.any():
-                pytest.skip("near-tie action in the batched oracle check")
-            o.transition(pols[e]["action"])
-            harness.compare_state(batch2.read_state(e), o, "batched env %d step %d" % (e, t))
+        harness.push_params(batch2, o, range(o.S), e)
+    reps = harness.lockstep_batch(batch2, orcs, 8, where="batched")
+    assert all(r["steps"] == 8 for r in reps)
+    assert sum(r["births"] for r in reps) > 0
     batch.close()
     batch2.close()
     for s in singles:
         s.close()
+
+
+@pytest.mark.parametrize("e_init", [100, 195])
+def test_batched_workload_lockstep(e_init):
+    """Twelve worlds of the batched workload's distribution (sides 128 to
+    1024, lognormal populations; the many-worlds shape of App. F.3) in one
+    handle, each in lock-step with its own oracle for 6 steps: state,
+    actions, logits and every statistic per world.  e_init 195 puts most
+    founders near the reproduction threshold, so births happen in every
+    world within the run."""
+    from paper_2510_18221_gb300 import eco
+    ws = [dict(w, e_init=e_init) for w in workloads.batched(n_envs=12, seed=0)]
+    assert {w["side"] for w in ws} == {128, 256, 512, 1024}
+    env = eco.Env(ws)
+    orcs = [oracle.Oracle(w) for w in ws]
+    try:
+        env.reset()
+        for e, o in enumerate(orcs):
+            o.reset()
+            harness.compare_state(env.read_state(e), o, "batched reset env %d" % e)
+            harness.push_params(env, o, range(o.S), e)
+        reps = harness.lockstep_batch(env, orcs, 6, where="batched-12")
+    finally:
+        env.close()
+    assert all(r["steps"] == 6 for r in reps)
+    if e_init == 195:
+        assert all(r["births"] > 0 for r in reps)
+        assert sum(r["streamed_checked"] for r in reps) == sum(r["gpu_births"] for r in reps)
+    print("batched lock-step:", [(r["births"], r["ambiguous"], r["max_logit_err"]) for r in reps])
+
+
+@pytest.mark.parametrize("slots,launch_mode", [(8192, 0), (8192, 1), (5000, 0)])
+def test_full_scan_birth_assignment(slots, launch_mode):
+    """More than 2,048 birth contenders in one world in one step: slot
+    assignment leaves the sorted-winner path for the full scan of the
+    world's slots (winners in ascending slot order take the free slots in
+    ascending order; Sec. 3.2, reproduction onto the cell behind).  4,000
+    founders at e_init 250 on a 128x128 world all reach the threshold in the
+    first step.  With 5,000 slots only 1,000 are free, so most winners fail
+    (counted) on the same path."""
+    w = workloads.scaled("mid", 128, slots, 4000, precision="bf16", e_init=250)
+    env, orc = _pair(w, launch_mode=launch_mode)
+    try:
+        harness.start_pair(env, orc)
+        rep = harness.lockstep(env, orc, 1, where=w["name"])
+        first = env.stats("last")[0]
+        assert first["births"] + first["failed_births"] > 2048, first
+        if slots == 5000:
+            assert first["births"] == 1000 and first["failed_births"] > 1000
+        rep2 = harness.lockstep(env, orc, 5, where=w["name"])
+        assert rep["streamed_checked"] + rep2["streamed_checked"] == rep["gpu_births"] + rep2["gpu_births"]
+    finally:
+        env.close()
+
+
+def test_barrier_timeout_is_reported_and_reset_recovers():
+    """Failure detection without a GPU fault: one CTA of the persistent
+    environment kernel leaves before its first grid barrier (the hook
+    eco_arm_barrier_timeout), so the other CTAs' bounded waits run out
+    after 10^5 polls.  The status word reaches the host as ECO_ETIMEOUT,
+    nothing waits without bound, and eco_reset clears the barrier, the
+    status and the hook: the next steps are in lock-step with the oracle."""
+    from paper_2510_18221_gb300 import eco
+    w = workloads.scaled("mid", 128, 8192, 4000, precision="bf16", e_init=190)
+    env, orc = _pair(w)
+    try:
+        env.reset()
+        env.step(2)
+        mode, blocks = env.launch_mode()
+        assert mode == 0 and blocks > 1
+        eco.eco_arm_barrier_timeout(env.h, blocks - 1, 100000)
+        env.step(9)          # a graph of 8 steps, then one more
+        with pytest.raises(eco.EcoError) as ex:
+            env.stats()
+        assert ex.value.code == eco.ECO_ETIMEOUT and "budget" in str(ex.value)
+        with pytest.raises(eco.EcoError) as ex:
+            eco.eco_step_read(env.h, 1)
+        assert ex.value.code == eco.ECO_ETIMEOUT
+        harness.start_pair(env, orc)
+        rep = harness.lockstep(env, orc, 6, where="after a timeout")
+        assert rep["steps"] == 6 and rep["births"] > 0
+        assert env.stats()[0]["step"] == 6
+    finally:
+        env.close()
+    b = eco.Env(w, launch_mode=1)   # the per-phase form has no grid barrier
+    try:
+        b.reset()
+        b.step(1)
+        with pytest.raises(eco.EcoError) as ex:
+            eco.eco_arm_barrier_timeout(b.h, 0, 1000)
+        assert ex.value.code == eco.ECO_EINVAL
+    finally:
+        b.close()
+
+
+def test_reset_seed_matches_config_seeds():
+    """eco_reset_seed(s) gives world e the seed s + e: the same reset and
+    steps as a handle created with those seeds in its configuration, and as
+    the oracle."""
+    from paper_2510_18221_gb300 import eco
+    ws = [workloads.scaled("mid", 64, 600, 500, precision="bf16", seed=1),
+          workloads.scaled("mid", 32, 300, 200, precision="bf16", seed=2)]
+    a = eco.Env(ws)
+    b = eco.Env([dict(w, seed=77 + e) for e, w in enumerate(ws)])
+    try:
+        a.reset()
+        a.step(3)
+        a.reset_seed(77)
+        b.reset()
+        for e in range(2):
+            harness.compare_state(a.read_state(e), _reset_oracle(dict(ws[e], seed=77 + e)),
+                                  "reset_seed env %d" % e)
+            assert np.array_equal(a.read_params(e), b.read_params(e))
+        a.step(5)
+        b.step(5)
+        for e in range(2):
+            sa, sb = a.read_state(e), b.read_state(e)
+            for k in harness.STATE_KEYS:
+                assert np.array_equal(sa[k], sb[k]), (e, k)
+            assert a.stats()[e] == b.stats()[e]
+    finally:
+        a.close()
+        b.close()
+
+
+def _reset_oracle(w):
+    o = oracle.Oracle(w)
+    o.reset()
+    return o
 
 
 def test_launch_forms_bit_identical():

@@ -80,3 +80,43 @@ def test_noalloc_rejects_oversized_grid():
     with pytest.raises(eco.EcoError) as ex:
         eco.eco_move_claims_noalloc(side, 1, 1, 1, 1, 1, 0, 0, 1, 1, 1, 0)
     assert ex.value.code == eco.ECO_EINVAL
+
+
+def test_noalloc_in_place_update_matches_separate_outputs():
+    """A caller may update positions and facings in place (pos_out is pos,
+    facing_out is facing_in): the result equals the call with separate
+    output arrays, on a world where many movers contest the same cells."""
+    import torch
+
+    cuda = torch.device("cuda")
+    side, n = 64, 1500
+    rng = np.random.default_rng(17)
+    cells = rng.choice(side * side, size=n, replace=False).astype(np.int32)
+    blocked = np.zeros(side * side, np.uint8)
+    blocked[cells] = 1
+    blocked[rng.choice(side * side, size=200, replace=False)] = 1      # walls
+    act = rng.choice([0, 1, 2, 3, 4, 5, 6, 7, 8], size=n).astype(np.uint8)
+    fac = rng.integers(0, 4, size=n).astype(np.uint8)
+    t_blk = torch.from_numpy(blocked).to(cuda)
+    t_act = torch.from_numpy(act).to(cuda)
+    outs = []
+    for in_place in (False, True):
+        t_pos = torch.from_numpy(cells.copy()).to(cuda)
+        t_fac = torch.from_numpy(fac.copy()).to(cuda)
+        if in_place:
+            t_pos_out, t_fac_out = t_pos, t_fac
+        else:
+            t_pos_out = torch.empty(n, dtype=torch.int32, device=cuda)
+            t_fac_out = torch.empty(n, dtype=torch.uint8, device=cuda)
+        t_moved = torch.empty(n, dtype=torch.uint8, device=cuda)
+        torch.cuda.synchronize()
+        eco.eco_move_claims_noalloc(side, n, t_pos.data_ptr(), t_act.data_ptr(), t_fac.data_ptr(),
+                                    t_blk.data_ptr(), 3, 9, t_fac_out.data_ptr(),
+                                    t_pos_out.data_ptr(), t_moved.data_ptr(), 0)
+        torch.cuda.synchronize()
+        outs.append((t_pos_out.cpu().numpy(), t_fac_out.cpu().numpy(), t_moved.cpu().numpy()))
+    (p0, f0, m0), (p1, f1, m1) = outs
+    assert np.array_equal(p0, p1) and np.array_equal(f0, f1) and np.array_equal(m0, m1)
+    assert 0 < int(m0.sum()) < int(((act >= 1) & (act <= 4)).sum())   # some won, some lost or were blocked
+    assert np.array_equal(p0[m0 == 0], cells[m0 == 0])
+    assert len(np.unique(p0)) == n                                     # one agent per cell
