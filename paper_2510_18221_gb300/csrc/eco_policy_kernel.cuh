@@ -162,10 +162,52 @@ struct Log2<1> {
   static constexpr int v = 0;
 };
 
-// One input-major layer: out[o] = act(s_o * sum_j W[j][o] x[j] + b_o) for
-// o in [0, H), written to shared memory by lanes 0 .. H/E - 1.  b_o is the
-// sum of nbias bias vectors (the paper form's per-sensor input biases);
-// act is ReLU or tanh.
+// Finish an input-major layer from each lane's E partial sums:
+// out[o] = act(s_o * sum + b_o) for o in [0, H), b_o the sum of nbias bias
+// vectors (the paper form's per-sensor input biases), act ReLU or tanh.
+// Reduce-scatter over the 32 / UPJ lanes that hold partial sums of the same
+// E outputs (xor partners at offsets UPJ, 2 UPJ, ..., 16): at each step a
+// lane keeps one half of its live sums, sends the other half to its partner
+// and adds the partner's half of what it keeps.  Afterwards every lane
+// holds H / 32 finished outputs, so the bias, scale and activation run on
+// all 32 lanes.
+template <int PREC, int H>
+__device__ __forceinline__ void layer_finish(float *acc, const float *__restrict__ bias, int nbias,
+                                             const float *__restrict__ scale, float *__restrict__ out,
+                                             int lane, int relu) {
+  constexpr int E = Unit<PREC>::E;
+  constexpr int UPJ = H / E;
+  int base = 0;
+#pragma unroll
+  for (int step = 0; (UPJ << step) < 32; ++step) {
+    const int off = UPJ << step;
+    constexpr int kE = E;
+    const int half = kE >> (step + 1);
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float lo = acc[i], hi = acc[i + half];
+      const float keep = upper ? hi : lo;
+      acc[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, upper ? lo : hi, off);
+    }
+    if (upper) base += half;
+  }
+  constexpr int NOUT = H / 32;
+  const int o0 = (lane & (UPJ - 1)) * E + base;
+#pragma unroll
+  for (int i = 0; i < NOUT; ++i) {
+    const int o = o0 + i;
+    const float s = (PREC == PREC_FP8) ? __ldg(scale + o) : 1.0f;
+    float b = __ldg(bias + o);
+    for (int k = 1; k < nbias; ++k) b += __ldg(bias + k * H + o);
+    const float v = fmaf(acc[i], s, b);
+    out[o] = relu ? fmaxf(v, 0.0f) : tanhf(v);
+  }
+}
+
+// One input-major layer streamed from global memory:
+// out[o] = act(s_o * sum_j W[j][o] x[j] + b_o) for o in [0, H), written to
+// shared memory.
 // SPARSE: stream only the rows of the n_in inputs listed in idx (the
 // nonzero entries of x): a row is the H outputs of one input, UPJ whole
 // units, so the loads stay 16-byte and contiguous per row.  Skipped inputs
@@ -213,38 +255,229 @@ __device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int 
       Unit<PREC>::fma(acc, v, x[u >> LG]);
     }
   }
-  // Reduce-scatter over the 32 / UPJ lanes that hold partial sums of the same
-  // E outputs (xor partners at offsets UPJ, 2 UPJ, ..., 16): at each step a
-  // lane keeps one half of its live sums, sends the other half to its
-  // partner and adds the partner's half of what it keeps.  Afterwards every
-  // lane holds H / 32 finished outputs, so the bias, scale and activation
-  // run on all 32 lanes.
-  int base = 0;
-#pragma unroll
-  for (int step = 0; (UPJ << step) < 32; ++step) {
-    const int off = UPJ << step;
-    constexpr int kE = E;
-    const int half = kE >> (step + 1);
-    const bool upper = (lane & off) != 0;
-#pragma unroll
-    for (int i = 0; i < half; ++i) {
-      const float lo = acc[i], hi = acc[i + half];
-      const float keep = upper ? hi : lo;
-      acc[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, upper ? lo : hi, off);
+  layer_finish<PREC, H>(acc, bias, nbias, scale, out, lane, relu);
+}
+
+// Cell one step from (px, py) in direction dir (N E S W) on a torus of side L.
+__device__ __forceinline__ int nbr_cell(int px, int py, int dir, int L) {
+  int x = px + dir_dx(dir), y = py + dir_dy(dir);
+  x += x < 0 ? L : (x >= L ? -L : 0);
+  y += y < 0 ? L : (y >= L ? -L : 0);
+  return y * L + x;
+}
+
+// Observation of one agent (Sec. 3.2 "Sensors"): the k x k x nch patch
+// (row, column, channel), then the scalars, into xs.  Lanes 0..3 also read
+// the flags of the four neighbouring cells (N E S W) for the move claim:
+// *nb_cell = env-local cell, *nb_flags = its cellf byte (lane d: direction d).
+__device__ __forceinline__ void gather_obs(const Dev &d, const Layout &L, const Rules &R, int slot,
+                                           int env, int pos, int f, float *xs, int lane,
+                                           uint32_t kdiv, int *nb_cell, uint32_t *nb_flags) {
+  const int k = R.patch_k, RR = k >> 1, kk = k * k;
+  const bool rotate = (R.flags & F_ROTATE_OBS) != 0;
+  const EnvDesc ed = d.env[env];
+  const int side = ed.side;
+  const int px = pos % side, py = pos / side;
+  const int rt = (f + 1) & 3;
+  const uint8_t *cellf = d.cellf + ed.cell_off;
+  if (lane < 4) {
+    *nb_cell = nbr_cell(px, py, lane, side);
+    *nb_flags = cellf[*nb_cell];
+  }
+  // rows run from far ahead (top) to behind (Around) or to the agent's
+  // own row (Front); columns from the agent's left to its right
+  const int fw0 = R.view == VIEW_FRONT ? k - 1 : RR;
+  const int nch = L.nch;
+  const bool terrain = R.rules == RULES_TERRAIN;
+  const int rock0 = terrain ? d.rock[ed.cell_off + pos] : 0;
+  for (int c = lane; c < kk; c += 32) {
+    // c / k by a multiply-high with ceil(2^32 / k): exact for c < 2^10
+    const int r = (int)__umulhi((uint32_t)c, kdiv), col = c - r * k;
+    int dx, dy;
+    if (rotate) {
+      const int fw = fw0 - r, ri = col - RR;
+      dx = fw * dir_dx(f) + ri * dir_dx(rt);
+      dy = fw * dir_dy(f) + ri * dir_dy(rt);
+    } else {
+      dx = col - RR;
+      dy = r - RR;
     }
-    if (upper) base += half;
+    // |dx|, |dy| <= k / 2 < side: one correction wraps the torus
+    int cx = px + dx, cy = py + dy;
+    cx += cx < 0 ? side : (cx >= side ? -side : 0);
+    cy += cy < 0 ? side : (cy >= side ? -side : 0);
+    const int gc = ed.cell_off + cy * side + cx;
+    const uint32_t cf = cellf[cy * side + cx];
+    if (R.vision == VISION_RGB) {
+      // rendered colours: the occupant's colour trait, else grey wall,
+      // else green food (terrain: the cell's biomass, energy and water)
+      float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (cf & CELL_AGENT) {
+        v = d.colour[d.occ[gc]];
+      } else if (cf & CELL_WALL) {
+        v = make_float4(0.5f, 0.5f, 0.5f, 0.0f);
+      } else if (terrain) {
+        const float b = (float)d.bio[gc], rr = (float)d.res[gc], w = (float)d.water[gc];
+        v = make_float4(b / (b + (float)R.b_bite), rr / (rr + (float)R.e_food), w / (w + (float)R.w_bite), 0.0f);
+      } else if (cf & CELL_FOOD) {
+        v.y = 1.0f;
+      }
+      xs[nch * c + 0] = v.x;
+      xs[nch * c + 1] = v.y;
+      xs[nch * c + 2] = v.z;
+      if (terrain) {  // elevation: rock difference d as d / (|d| + 16)
+        const float dz = (float)(d.rock[gc] - rock0);
+        xs[nch * c + 3] = dz / (fabsf(dz) + 16.0f);
+      }
+    } else {
+      xs[3 * c + 0] = (cf & CELL_FOOD) ? 1.0f : 0.0f;
+      xs[3 * c + 1] = (cf & CELL_AGENT) ? 1.0f : 0.0f;
+      xs[3 * c + 2] = (cf & CELL_WALL) ? 1.0f : 0.0f;
+    }
   }
-  constexpr int NOUT = H / 32;
-  const int o0 = (lane & (UPJ - 1)) * E + base;
+  if (lane < R.n_scalars) {
+    // [e / e_repro, one-hot facing (8-scalar form), zeros]; the paper
+    // rules fill the zeros with HP / hp_max, age / (age + age_div) and
+    // r / (r + e_food), r the energy lying on the agent's cell
+    float v = 0.0f;
+    if (lane == 0)
+      v = (float)d.energy[slot] / (float)R.e_repro;
+    else if (R.n_scalars >= 8 && lane == 1 + f)
+      v = 1.0f;
+    if (R.rules != RULES_SIMPLE) {
+      const int extra = lane - (R.n_scalars >= 8 ? 5 : 1);
+      if (extra == 0) {
+        v = (float)d.hp[slot] / (float)R.hp_max;
+      } else if (extra == 1) {
+        const float a = (float)d.age[slot];
+        v = a / (a + (float)R.age_div);
+      } else if (extra == 2) {
+        const float r = (float)d.res[ed.cell_off + pos];
+        v = r / (r + (float)R.e_food);
+      }
+    }
+    if (terrain) {  // carried water and biomass; the cell's water and biomass
+      if (lane == 8) {
+        v = (float)d.a_water[slot] / (float)R.w_cap;
+      } else if (lane == 9) {
+        v = (float)d.a_bio[slot] / (float)R.b_cap;
+      } else if (lane == 10) {
+        const float w = (float)d.water[ed.cell_off + pos];
+        v = w / (w + (float)R.w_bite);
+      } else if (lane == 11) {
+        const float b = (float)d.bio[ed.cell_off + pos];
+        v = b / (b + (float)R.b_bite);
+      }
+    }
+    xs[nch * kk + lane] = v;
+  }
+}
+
+// One group of 32 head units (output-major rows of UPJ units): unit u of
+// lane u % 32, valid when u < U3; the partial dot products of a row reduce
+// over its UPJ lanes, and the row's first lane writes logit a = u / UPJ:
+// (W_out h [+ b_out]) * s_a, times exp(-tau) in the paper form.
+template <int PREC, int H>
+__device__ __forceinline__ void head_group(const uint4 &v, int u, int U3, const float *cur,
+                                           const float *__restrict__ out_scale,
+                                           const float *__restrict__ hb, int out_bias, int temp,
+                                           float tmul, float *ls, int lane) {
+  constexpr int E = Unit<PREC>::E;
+  constexpr int UPJ = H / E;
+  constexpr int LG = Log2<UPJ>::v;
+  float part = 0.0f;
+  if (u < U3) part = Unit<PREC>::dot(v, cur + (u & (UPJ - 1)) * E);
 #pragma unroll
-  for (int i = 0; i < NOUT; ++i) {
-    const int o = o0 + i;
-    const float s = (PREC == PREC_FP8) ? __ldg(scale + o) : 1.0f;
-    float b = __ldg(bias + o);
-    for (int k = 1; k < nbias; ++k) b += __ldg(bias + k * H + o);
-    const float v = fmaf(acc[i], s, b);
-    out[o] = relu ? fmaxf(v, 0.0f) : tanhf(v);
+  for (int off = 1; off < UPJ; off <<= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, off);
+  if (u < U3 && (lane & (UPJ - 1)) == 0) {
+    const int a = u >> LG;
+    const float s = (PREC == PREC_FP8) ? __ldg(out_scale + a) : 1.0f;
+    const float val = out_bias ? fmaf(part, s, __ldg(hb + a)) : part * s;
+    ls[a] = temp ? val * tmul : val;
   }
+}
+
+// Sample the action (Sec. 3.3: argmax_a (logit_a + Gumbel_a), ties to the
+// lowest a; GREEDY: argmax of the logits), store the logits and the
+// action, and, with apply_moves, the fused part of A6: facing and turns,
+// and the move claim on a cell that is neither a wall nor occupied now, at
+// the start of the step (no cell changes while the policy phase runs).
+// Lane A draws the agent's CLAIM_MOVE number in the same pass as lanes
+// 0..A-1 draw their Gumbel noise; lanes 0..3 hold the neighbouring cells
+// and their flags (gather_obs).  Counts into the warp's counters: lane a <
+// 16 action a, lane 16 moves blocked by a wall or an agent.
+__device__ __forceinline__ void sample_and_claim(const Dev &d, const Rules &R, int A, int slot, int env,
+                                                 int pos, int f, const float *ls, int lane, uint32_t t,
+                                                 bool greedy, int apply_moves, int nb_cell,
+                                                 uint32_t nb_flags, int &cnt) {
+  float score = -INFINITY;
+  int best = lane;
+  uint32_t claim_r = 0;
+  if (lane <= A) {
+    const EnvDesc ed = d.env[env];
+    const bool claimer = lane == A;
+    float lg = 0.0f;
+    if (!claimer) {
+      lg = ls[lane];
+      d.logits[(int64_t)slot * A + lane] = lg;
+      score = lg;
+    }
+    if (claimer ? apply_moves != 0 : !greedy) {
+      const U4 r = philox(t, (uint32_t)(slot - ed.slot_off), claimer ? 0u : (uint32_t)(lane >> 2), 0u,
+                          ed.seed, claimer ? S_CLAIM_MOVE : S_SAMPLE);
+      if (claimer) {
+        claim_r = r.x;
+      } else {
+        const float u = uniform01(word_of(r, lane & 3));
+        score = lg + (-logf(-logf(u)));
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float os = __shfl_xor_sync(0xFFFFFFFFu, score, off);
+    const int oa = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+    if (os > score || (os == score && oa < best)) {
+      score = os;
+      best = oa;
+    }
+  }
+  if (apply_moves) {
+    int nf = f;
+    bool move = false;
+    if (R.rules != RULES_SIMPLE) {
+      // rotate clockwise / counter-clockwise, or one cell forward
+      if (best == PA_CW) nf = (f + 1) & 3;
+      else if (best == PA_CCW) nf = (f + 3) & 3;
+      move = best == PA_FORWARD;
+    } else if (best >= ACT_N && best <= ACT_W) {
+      nf = (best == ACT_N) ? 0 : (best == ACT_S) ? 2 : (best == ACT_E) ? 1 : 3;
+      move = true;
+    } else if (best == ACT_LEFT) {
+      nf = (f + 3) & 3;
+    } else if (best == ACT_RIGHT) {
+      nf = (f + 1) & 3;
+    }
+    const int c = __shfl_sync(0xFFFFFFFFu, nb_cell, nf);
+    const uint32_t cf = __shfl_sync(0xFFFFFFFFu, nb_flags, nf);
+    const uint32_t draw = __shfl_sync(0xFFFFFFFFu, claim_r, A);
+    const int blk = (move && (cf & (CELL_WALL | CELL_AGENT))) ? 1 : 0;
+    if (lane == 0) {
+      int tc = -1;
+      if (move && !blk) {
+        const EnvDesc ed = d.env[env];
+        const int local = slot - ed.slot_off;
+        atomicMax(&d.claim_move[ed.cell_off + c], claim_key(draw, local));
+        if (R.flags & F_CANCEL_ALL) atomicAdd(&d.cnt_move[ed.cell_off + c], 1u);
+        tc = c;
+      }
+      d.facing[slot] = (uint8_t)nf;
+      d.tgt[slot] = tc;
+    }
+    if (lane == best) ++cnt;
+    if (lane == 16 && blk) ++cnt;
+  }
+  if (lane == 0) d.act[slot] = (uint8_t)best;
 }
 
 // The weight stream is latency-bound per warp: the register budget is capped
@@ -256,7 +489,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     k_policy(Dev d, Layout L, Rules R, int xs_floats, int apply_moves) {
   constexpr int E = Unit<PREC>::E;
   constexpr int UPJ = H / E;
-  constexpr int LG = Log2<UPJ>::v;
   extern __shared__ __align__(16) float smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -270,10 +502,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
   const uint32_t t = (uint32_t)d.step[0];
   // the step's agent count, for the byte count of timed launches
   if (apply_moves && blockIdx.x == 0 && threadIdx.x == 0) d.alive_at_step[t & (kAliveRing - 1)] = n_alive;
-  const int k = R.patch_k, RR = k >> 1, kk = k * k;
+  const int k = R.patch_k;
   // ceil(2^32 / k) for odd k (k = 0: no patch, the gather loop is empty)
   const uint32_t kdiv = k > 0 ? 0xFFFFFFFFu / (uint32_t)k + 1u : 0u;
-  const bool rotate = (R.flags & F_ROTATE_OBS) != 0;
   const bool greedy = (R.flags & F_GREEDY) != 0;
 
   // Per-warp counters, flushed when the environment changes: lane a < 16
@@ -310,105 +541,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
       flush();
       e_cur = env;
     }
-    // -- observation: k x k x nch patch (row, column, channel), then scalars.
-    // Its locals end with this scope so that they do not stay live (in
-    // registers) through the weight stream below.
-    {
-    const EnvDesc ed = d.env[env];
-    const int side = ed.side;
     const int pos = d.pos[slot];
-    const int px = pos % side, py = pos / side;
     const int f = d.facing[slot];
-    const int rt = (f + 1) & 3;
-    const uint8_t *cellf = d.cellf + ed.cell_off;
-    // rows run from far ahead (top) to behind (Around) or to the agent's
-    // own row (Front); columns from the agent's left to its right
-    const int fw0 = R.view == VIEW_FRONT ? k - 1 : RR;
-    const int nch = L.nch;
-    const bool terrain = R.rules == RULES_TERRAIN;
-    const int rock0 = terrain ? d.rock[ed.cell_off + pos] : 0;
-    for (int c = lane; c < kk; c += 32) {
-      // c / k by a multiply-high with ceil(2^32 / k): exact for c < 2^10
-      const int r = (int)__umulhi((uint32_t)c, kdiv), col = c - r * k;
-      int dx, dy;
-      if (rotate) {
-        const int fw = fw0 - r, ri = col - RR;
-        dx = fw * dir_dx(f) + ri * dir_dx(rt);
-        dy = fw * dir_dy(f) + ri * dir_dy(rt);
-      } else {
-        dx = col - RR;
-        dy = r - RR;
-      }
-      // |dx|, |dy| <= k / 2 < side: one correction wraps the torus
-      int cx = px + dx, cy = py + dy;
-      cx += cx < 0 ? side : (cx >= side ? -side : 0);
-      cy += cy < 0 ? side : (cy >= side ? -side : 0);
-      const int gc = ed.cell_off + cy * side + cx;
-      const uint32_t cf = cellf[cy * side + cx];
-      if (R.vision == VISION_RGB) {
-        // rendered colours: the occupant's colour trait, else grey wall,
-        // else green food (terrain: the cell's biomass, energy and water)
-        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (cf & CELL_AGENT) {
-          v = d.colour[d.occ[gc]];
-        } else if (cf & CELL_WALL) {
-          v = make_float4(0.5f, 0.5f, 0.5f, 0.0f);
-        } else if (terrain) {
-          const float b = (float)d.bio[gc], r = (float)d.res[gc], w = (float)d.water[gc];
-          v = make_float4(b / (b + (float)R.b_bite), r / (r + (float)R.e_food), w / (w + (float)R.w_bite), 0.0f);
-        } else if (cf & CELL_FOOD) {
-          v.y = 1.0f;
-        }
-        xs[nch * c + 0] = v.x;
-        xs[nch * c + 1] = v.y;
-        xs[nch * c + 2] = v.z;
-        if (terrain) {  // elevation: rock difference d as d / (|d| + 16)
-          const float dz = (float)(d.rock[gc] - rock0);
-          xs[nch * c + 3] = dz / (fabsf(dz) + 16.0f);
-        }
-      } else {
-        xs[3 * c + 0] = (cf & CELL_FOOD) ? 1.0f : 0.0f;
-        xs[3 * c + 1] = (cf & CELL_AGENT) ? 1.0f : 0.0f;
-        xs[3 * c + 2] = (cf & CELL_WALL) ? 1.0f : 0.0f;
-      }
-    }
-    if (lane < R.n_scalars) {
-      // [e / e_repro, one-hot facing (8-scalar form), zeros]; the paper
-      // rules fill the zeros with HP / hp_max, age / (age + age_div) and
-      // r / (r + e_food), r the energy lying on the agent's cell
-      float v = 0.0f;
-      if (lane == 0)
-        v = (float)d.energy[slot] / (float)R.e_repro;
-      else if (R.n_scalars >= 8 && lane == 1 + f)
-        v = 1.0f;
-      if (R.rules != RULES_SIMPLE) {
-        const int extra = lane - (R.n_scalars >= 8 ? 5 : 1);
-        if (extra == 0) {
-          v = (float)d.hp[slot] / (float)R.hp_max;
-        } else if (extra == 1) {
-          const float a = (float)d.age[slot];
-          v = a / (a + (float)R.age_div);
-        } else if (extra == 2) {
-          const float r = (float)d.res[ed.cell_off + pos];
-          v = r / (r + (float)R.e_food);
-        }
-      }
-      if (terrain) {  // carried water and biomass; the cell's water and biomass
-        if (lane == 8) {
-          v = (float)d.a_water[slot] / (float)R.w_cap;
-        } else if (lane == 9) {
-          v = (float)d.a_bio[slot] / (float)R.b_cap;
-        } else if (lane == 10) {
-          const float w = (float)d.water[ed.cell_off + pos];
-          v = w / (w + (float)R.w_bite);
-        } else if (lane == 11) {
-          const float b = (float)d.bio[ed.cell_off + pos];
-          v = b / (b + (float)R.b_bite);
-        }
-      }
-      xs[nch * kk + lane] = v;
-    }
-    }
+    int nb_cell = 0;
+    uint32_t nb_flags = 0;
+    gather_obs(d, L, R, slot, env, pos, f, xs, lane, kdiv, &nb_cell, &nb_flags);
     __syncwarp();
 
     const uint8_t *blk = d.wq + (int64_t)slot * L.stride;
@@ -456,89 +593,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     const float tmul = L.temp ? expf(-__ldg(hb + (L.out_bias ? L.A : 0))) : 1.0f;
     for (int base = 0; base < U3; base += 32) {
       const int u = base + lane;
-      float part = 0.0f;
-      if (u < U3) part = Unit<PREC>::dot(ldg_stream(w3 + u), cur + (u & (UPJ - 1)) * E);
-#pragma unroll
-      for (int off = 1; off < UPJ; off <<= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, off);
-      if (u < U3 && (lane & (UPJ - 1)) == 0) {
-        const int a = u >> LG;
-        const float s = (PREC == PREC_FP8) ? __ldg(scale + H + L.L * H + a) : 1.0f;
-        const float v = L.out_bias ? fmaf(part, s, __ldg(hb + a)) : part * s;
-        ls[a] = L.temp ? v * tmul : v;
-      }
+      const uint4 v = u < U3 ? ldg_stream(w3 + u) : make_uint4(0u, 0u, 0u, 0u);
+      head_group<PREC, H>(v, u, U3, cur, scale + H + L.L * H, hb, L.out_bias, L.temp, tmul, ls, lane);
     }
     __syncwarp();
 
-    // -- sample: argmax_a (logit_a + Gumbel_a), ties to the lowest a
-    float score = -INFINITY;
-    int best = lane;
-    if (lane < L.A) {
-      const float lg = ls[lane];
-      d.logits[(int64_t)slot * L.A + lane] = lg;
-      score = lg;
-      if (!greedy) {
-        const EnvDesc ed = d.env[env];
-        const U4 r = philox(t, (uint32_t)(slot - ed.slot_off), (uint32_t)(lane >> 2), 0u, ed.seed,
-                            S_SAMPLE);
-        const float u = uniform01(word_of(r, lane & 3));
-        score = lg + (-logf(-logf(u)));
-      }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float os = __shfl_xor_sync(0xFFFFFFFFu, score, off);
-      const int oa = __shfl_xor_sync(0xFFFFFFFFu, best, off);
-      if (os > score || (os == score && oa < best)) {
-        score = os;
-        best = oa;
-      }
-    }
-    if (apply_moves) {
-      // A6 (part 1), fused: facing and turns, and the move claim on a cell
-      // that is neither a wall nor occupied now, at the start of the step
-      // (no cell changes while the policy phase runs).
-      int blk = 0;
-      if (lane == 0) {
-        const EnvDesc ed = d.env[env];
-        const int side = ed.side;
-        const int pos = d.pos[slot];
-        const int f = d.facing[slot];
-        const uint8_t *cellf = d.cellf + ed.cell_off;
-        int nf = f, tc = -1;
-        bool move = false;
-        if (R.rules != RULES_SIMPLE) {
-          // rotate clockwise / counter-clockwise, or one cell forward
-          if (best == PA_CW) nf = (f + 1) & 3;
-          else if (best == PA_CCW) nf = (f + 3) & 3;
-          move = best == PA_FORWARD;
-        } else if (best >= ACT_N && best <= ACT_W) {
-          nf = (best == ACT_N) ? 0 : (best == ACT_S) ? 2 : (best == ACT_E) ? 1 : 3;
-          move = true;
-        } else if (best == ACT_LEFT) {
-          nf = (f + 3) & 3;
-        } else if (best == ACT_RIGHT) {
-          nf = (f + 1) & 3;
-        }
-        if (move) {
-          const int c = step_cell(pos, nf, side);
-          if (cellf[c] & (CELL_WALL | CELL_AGENT)) {
-            blk = 1;
-          } else {
-            const int local = slot - ed.slot_off;
-            const U4 r = philox(t, (uint32_t)local, 0u, 0u, ed.seed, S_CLAIM_MOVE);
-            atomicMax(&d.claim_move[ed.cell_off + c], claim_key(r.x, local));
-            if (R.flags & F_CANCEL_ALL) atomicAdd(&d.cnt_move[ed.cell_off + c], 1u);
-            tc = c;
-          }
-        }
-        d.facing[slot] = (uint8_t)nf;
-        d.tgt[slot] = tc;
-      }
-      blk = __shfl_sync(0xFFFFFFFFu, blk, 0);
-      if (lane == best) ++cnt;
-      if (lane == 16 && blk) ++cnt;
-    }
-    if (lane == 0) d.act[slot] = (uint8_t)best;
+    sample_and_claim(d, R, L.A, slot, env, pos, f, ls, lane, t, greedy, apply_moves, nb_cell, nb_flags, cnt);
     __syncwarp();
   }
   flush();

@@ -60,14 +60,14 @@ def test_rule_flags(flags):
     _run(w, 10)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("variant", list(range(1, 11)))
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
 def test_every_policy_variant(variant, prec):
     w = workloads.scaled("mid", 64, 512, 450, precision=prec)
     _run(w, 3, policy_variant=variant)
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
 def test_policy_variants_bit_identical(prec):
     """Every dense variant computes each agent in the same order (units in
     ascending order per lane, a fixed reduce-scatter), whatever its warps,
@@ -75,7 +75,7 @@ def test_policy_variants_bit_identical(prec):
     autotuner's choice does not change a single bit of logits or state."""
     from paper_2510_18221_gb300 import eco
     w = workloads.scaled("mid", 128, 2048, 1500, precision=prec, e_init=185)
-    envs = [eco.Env(w, policy_variant=v) for v in (1, 2, 6, 9, 10)]
+    envs = [eco.Env(w, policy_variant=v) for v in (1, 2, 4, 6, 9, 10)]
     for x in envs:
         x.reset()
     for t in range(6):
