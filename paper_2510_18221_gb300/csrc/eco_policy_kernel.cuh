@@ -134,6 +134,25 @@ struct Unit<PREC_FP8> {
     fma4(acc + 8, v.z, x);
     fma4(acc + 12, v.w, x);
   }
+  // Products with an input x exactly representable in f16 (xh its bits):
+  // the decoded f16 weight times x is exact in FP32, and fma.rn.f32.f16
+  // rounds the sum once, like the FP32 FMA on the converted weight -- the
+  // same sums bit for bit, without converting each weight to FP32.
+  __device__ __forceinline__ static void fma4_h(float *acc, uint32_t w, unsigned short xh) {
+    const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xFFFFu), __NV_E4M3);
+    const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+    asm("{\n\t.reg .f16 x;\n\tmov.b16 x, %8;\n\t"
+        "fma.rn.f32.f16 %0, %4, x, %0;\n\tfma.rn.f32.f16 %1, %5, x, %1;\n\t"
+        "fma.rn.f32.f16 %2, %6, x, %2;\n\tfma.rn.f32.f16 %3, %7, x, %3;\n\t}"
+        : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3])
+        : "h"(lo.x), "h"(lo.y), "h"(hi.x), "h"(hi.y), "h"(xh));
+  }
+  __device__ __forceinline__ static void fma_h(float *acc, const uint4 &v, unsigned short xh) {
+    fma4_h(acc + 0, v.x, xh);
+    fma4_h(acc + 4, v.y, xh);
+    fma4_h(acc + 8, v.z, xh);
+    fma4_h(acc + 12, v.w, xh);
+  }
   __device__ __forceinline__ static float dot4(uint32_t w, const float *h, float s) {
     const float2 a = e4m3x2(w), b = e4m3x2(w >> 16);
     const float4 x = *reinterpret_cast<const float4 *>(h);
@@ -218,7 +237,7 @@ __device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int 
                                                const float *__restrict__ bias, int nbias,
                                                const float *__restrict__ scale,
                                                float *__restrict__ out, int lane, int relu,
-                                               const short *__restrict__ idx) {
+                                               const short *__restrict__ idx, int n_exact = 0) {
   constexpr int E = Unit<PREC>::E;
   constexpr int UPJ = H / E;  // units per input
   constexpr int LG = Log2<UPJ>::v;
@@ -228,6 +247,19 @@ __device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int 
   for (int e = 0; e < E; ++e) acc[e] = 0.0f;
   const int U = n_in * UPJ;
   int u = lane;
+  if constexpr (PREC == PREC_FP8 && !SPARSE) {
+    // FP8: whole batches whose inputs are all among the first n_exact
+    // (exact in f16: the one-hot patch) use the f16-input products
+    const int U1 = min(U, (n_exact * UPJ) / (32 * UNROLL) * (32 * UNROLL));
+    for (; u < U1; u += 32 * UNROLL) {
+      uint4 v[UNROLL];
+#pragma unroll
+      for (int k = 0; k < UNROLL; ++k) v[k] = ldg_stream(w + u + 32 * k);
+#pragma unroll
+      for (int k = 0; k < UNROLL; ++k)
+        Unit<PREC>::fma_h(acc, v[k], __half_as_ushort(__float2half_rn(x[(u + 32 * k) >> LG])));
+    }
+  }
   for (; u + 32 * (UNROLL - 1) < U; u += 32 * UNROLL) {
     uint4 v[UNROLL];
     int j[UNROLL];
@@ -569,8 +601,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
       layer_in_major<PREC, H, UNROLL, true>(wb + L.off_w1 / 16, n_nz, xs, bias, L.ns, scale, hs,
                                             lane, L.relu, idx);
     } else {
+      // one-hot vision: the patch inputs are 0 or 1, exact in f16
       layer_in_major<PREC, H, UNROLL, false>(wb + L.off_w1 / 16, L.D, xs, bias, L.ns, scale, hs,
-                                             lane, L.relu, nullptr);
+                                             lane, L.relu, nullptr,
+                                             R.vision == VISION_CHANNELS ? L.patch : 0);
     }
     __syncwarp();
     // -- hidden layers: h = act(W_l h + b_l), alternating between hs and xs
