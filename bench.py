@@ -36,9 +36,9 @@ METRIC = "agent-steps/sec at 65,536 agents (policy+env) and policy-kernel HBM GB
 UNIT = "agent-steps/s"
 # Kernels per step: the policy kernel (with the move claims) plus either one
 # persistent kernel for every environment phase, or one kernel per phase:
-# move+eat, attack claim, attack transfer+metabolism+death, birth claim,
-# birth assign, mutate, regrow, finish, and the two passes of the alive list.
-KERNELS_PER_STEP = {0: 2, 1: 11}
+# move+eat+attack claims, attack transfer+metabolism+death, birth claim,
+# birth assign, mutate, regrow, finish, and the alive list.
+KERNELS_PER_STEP = {0: 2, 1: 9}
 
 
 def kernels_per_step(launch_mode, rules):

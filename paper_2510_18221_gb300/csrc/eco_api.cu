@@ -263,6 +263,7 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.claim_move = k.take<unsigned long long>(cells);
   D.cnt_move = k.take<uint32_t>(cells);
   D.claim_birth = k.take<unsigned long long>(cells);
+  D.att_cell = k.take<unsigned long long>(cells);
   D.alive = k.take<uint8_t>(slots);
   D.pos = k.take<int32_t>(slots);
   D.facing = k.take<uint8_t>(slots);
@@ -273,7 +274,6 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.env_of = k.take<uint16_t>(slots);
   D.tgt = k.take<int32_t>(slots);
   D.gain = k.take<int32_t>(slots);
-  D.claim_att = k.take<unsigned long long>(slots);
   D.logits = k.take<float>((size_t)slots * L.A);
   D.alive_list = k.take<int32_t>(slots);
   D.tile_counts = k.take<int32_t>(compact_tiles((int)slots));
@@ -296,7 +296,6 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.place_remaining = k.take<int32_t>(E);
   D.hp = k.take<int32_t>(slots);
   D.age = k.take<int32_t>(slots);
-  D.dmg = k.take<int32_t>(slots);
   D.res = k.take<int32_t>(cells);
   D.colour = k.take<float4>(slots);
   D.rock = k.take<int32_t>(cells);

@@ -3,20 +3,20 @@
 // of the batch at once.
 //
 // Phase order: policy (+ facing, turns and move claims, fused into its
-// epilogue; eco_policy.cu) -> move apply + eat -> attack claims -> attack
-// transfers + metabolism + death -> birth claims (+ regrowth, which commutes
-// with them) -> slot assignment -> mutation of the children -> statistics +
-// the alive list of the next step.
+// epilogue; eco_policy.cu) -> move apply + eat + attack claims on cells ->
+// attack transfers + metabolism + death -> birth claims (+ regrowth, which
+// commutes with them) -> slot assignment -> mutation of the children, the
+// alive list of the next step and the statistics.
 //
 // Two launch forms run the same phase functions: one persistent kernel
 // (cooperative launch; phases separated by grid barriers whose waits are
 // bounded, so a stuck barrier sets the status word and every CTA exits), and
 // one kernel per phase.  Both give bit-identical results.
 //
-// Conflicts (two movers into one free cell, two attackers on one victim,
-// two parents onto one birth cell) are resolved by a 64-bit atomicMax of
-// (Philox draw << 32 | ~local slot): the highest draw wins, equal draws go
-// to the lower slot.  A maximum does not depend on the order of the
+// Conflicts (two movers into one free cell, two attackers on one victim's
+// cell, two parents onto one birth cell) are resolved by a 64-bit atomicMax
+// of (Philox draw << 32 | ~local slot): the highest draw wins, equal draws
+// go to the lower slot.  A maximum does not depend on the order of the
 // atomics, every other atomic is an integer add, and no phase's result
 // depends on the order in which agents are visited, so all integer state
 // is bit-identical from run to run and equal to the plain sequential rule.
@@ -41,6 +41,9 @@ int grid_for(long long n, int threads, int max_blocks) {
 // function names the alive agents).  Two passes over tiles of kCompactTile
 // slots: each tile counts its alive slots; then each tile adds up the
 // counts of the tiles before it (a few dozen numbers) and writes its slots.
+// The step itself runs only the second pass: every death and birth adjusts
+// its tile's count as it happens, so the counts are exact when the alive
+// set is final (the first pass runs after reset and state writes).
 // Slot order keeps the warps of the policy kernel streaming neighbouring
 // weight blocks at the same time.  Block-level: the first 256 threads of a
 // CTA of any size >= 256 cover a tile.
@@ -114,12 +117,14 @@ __device__ __forceinline__ int env_index(const Dev &d, int slot) {
 }
 
 
-// A6 (part 2) + A7: winners move (only the winner of a cell writes it, and
-// a winner's old cell was occupied when the step began, so nobody moves
-// into it); then every agent eats the food of its post-move cell, when the
-// rules say it eats.  Nobody else can be on that cell.
+// A6 (part 2) + A7 + A8 (part 1): winners move (only the winner of a cell
+// writes it, and a winner's old cell was occupied when the step began, so
+// nobody moves into it); then every agent eats the food of its post-move
+// cell, when the rules say it eats (nobody else can be on that cell); then
+// attackers claim their target cells.
 __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, int g0, int gs, int first) {
   const int n = d.counters[CNT_N_ALIVE];
+  const uint32_t t = (uint32_t)d.step[0];
   for (int i = g0; i < n; i += gs) {
     const int slot = agent_slot(d, i, g0, first);
     const int e = env_index(d, slot);
@@ -194,61 +199,33 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
     // from, kept where an attacker can read it while the owner updates its
     // own energy in the metabolism phase
     if (R.rules == RULES_SIMPLE) d.gain[slot] = d.energy[slot];
-  }
-}
-
-// A8 (part 1): clear this step's move claims; attackers claim the agent on
-// the faced cell (post-move occupancy).  Paper rules: an attacker adds
-// attack_damage to every agent in the 3x3 square in front of it (1..3 cells
-// ahead, one to either side); damage from several attackers adds up.
-__device__ void ph_attack_claim(const Dev &d, const Rules &R, int g0, int gs, int first) {
-  const int n = d.counters[CNT_N_ALIVE];
-  const uint32_t t = (uint32_t)d.step[0];
-  for (int i = g0; i < n; i += gs) {
-    const int slot = agent_slot(d, i, g0, first);
-    const int e = env_index(d, slot);
-    const EnvDesc ed = d.env[e];
-    const int tc = d.tgt[slot];
-    if (tc >= 0) {
-      d.claim_move[ed.cell_off + tc] = 0ull;
-      if (R.flags & F_CANCEL_ALL) d.cnt_move[ed.cell_off + tc] = 0u;
-    }
-    int victim = -1;
+    // A8 (part 1): attacks claim their target cells.  An attacker does not
+    // move (attack and move are different actions), so its cell and facing
+    // are final here, while the agents it hits are only known once every
+    // move is in; they are looked up after the barrier (metabolism phase).
+    // Simple rules: the faced cell, claimed by the highest CLAIM_ATTACK
+    // draw; paper rules: every cell of the 3x3 square in front (1..3 cells
+    // ahead, one to either side) counts one more attacker.
     if (R.rules != RULES_SIMPLE) {
-      if (d.act[slot] == PA_ATTACK) {
+      if (a == PA_ATTACK) {
         const int side = ed.side;
-        const int pos = d.pos[slot];
         const int px = pos % side, py = pos / side;
         const int f = d.facing[slot], rt = (f + 1) & 3;
-        int hits = 0;
-        for (int fw = 1; fw <= 3; ++fw) {
+        for (int fw = 1; fw <= 3; ++fw)
           for (int lat = -1; lat <= 1; ++lat) {
             const int cx = wrapi(px + fw * dir_dx(f) + lat * dir_dx(rt), side);
             const int cy = wrapi(py + fw * dir_dy(f) + lat * dir_dy(rt), side);
-            const int v = d.occ[ed.cell_off + cy * side + cx];
-            if (v >= 0) {
-              atomicAdd(&d.dmg[v], R.attack_damage);
-              ++hits;
-            }
+            atomicAdd(&d.att_cell[ed.cell_off + cy * side + cx], 1ull);
           }
-        }
-        stat_add(d.stats_step, e, ST_ATTACK_HITS, hits);
-        stat_add(d.stats_step, e, ST_DAMAGE, hits * R.attack_damage);
       }
-    } else if (d.act[slot] == ACT_ATTACK) {
-      const int c = step_cell(d.pos[slot], d.facing[slot], ed.side);
-      const int v = d.occ[ed.cell_off + c];
-      if (v >= 0) {
-        const int local = slot - ed.slot_off;
-        const U4 r = philox(t, (uint32_t)local, 0u, 0u, ed.seed, S_CLAIM_ATTACK);
-        atomicMax(&d.claim_att[v], claim_key(r.x, local));
-        victim = v;
-      }
+    } else if (a == ACT_ATTACK) {
+      const int c = step_cell(pos, d.facing[slot], ed.side);
+      const int local = slot - ed.slot_off;
+      const U4 r = philox(t, (uint32_t)local, 0u, 0u, ed.seed, S_CLAIM_ATTACK);
+      atomicMax(&d.att_cell[ed.cell_off + c], claim_key(r.x, local));
     }
-    d.tgt[slot] = victim;
   }
 }
-
 
 // Paper rules, one agent: pay the action's cost (starving when it exceeds
 // the energy), take the attack and age damage, heal from energy, and die at
@@ -284,8 +261,11 @@ __device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int s
     }
     aw -= spent;
   }
-  hp -= d.dmg[slot];
-  d.dmg[slot] = 0;
+  // every attacker whose square covers this cell takes attack_damage
+  const int hits = (int)d.att_cell[gpos];
+  hp -= hits * R.attack_damage;
+  stat_add(d.stats_step, e, ST_ATTACK_HITS, hits);
+  stat_add(d.stats_step, e, ST_DAMAGE, hits * R.attack_damage);
   hp -= age / R.age_div;
   if (hp > 0 && hp < R.hp_max && R.heal_rate > 0 && en >= R.heal_cost && (!terrain || aw >= R.heal_water)) {
     hp = min(hp + R.heal_rate, R.hp_max);
@@ -325,9 +305,9 @@ __device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int s
         stat_add(d.stats_step, e, ST_FOOD_REFILLED, 1);
       }
     }
-    d.cellf[gpos] = cf;
-    d.occ[gpos] = -1;
+    d.cellf[gpos] = cf;  // occ keeps the slot until the birth-claim phase
     d.alive[slot] = 0;
+    atomicSub(&d.tile_counts[slot / kCompactTile], 1);
     stat_add(d.stats_step, e, ST_DEATHS, 1);
     stat_add(d.stats_step, e, ST_DEAD_ENERGY, en);
     en = 0;
@@ -340,34 +320,49 @@ __device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int s
 }
 
 // A8 (part 2) + A9: the attack transfer, metabolism, death at e <= 0
-// (paper rules: health_paper).
+// (paper rules: health_paper).  Also clears this step's move claims.
+// A dying agent clears its alive flag and its cell's agent bit here, but
+// its occ entry only in the birth-claim phase, so that an attacker that
+// won the agent's cell still finds it in this phase.
 __device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs, int first) {
   const int n = d.counters[CNT_N_ALIVE];
   for (int i = g0; i < n; i += gs) {
     const int slot = agent_slot(d, i, g0, first);
+    const int e = env_index(d, slot);
+    const EnvDesc ed = d.env[e];
+    const int tc = d.tgt[slot];
+    if (tc >= 0) {
+      d.claim_move[ed.cell_off + tc] = 0ull;
+      if (R.flags & F_CANCEL_ALL) d.cnt_move[ed.cell_off + tc] = 0u;
+    }
     if (R.rules != RULES_SIMPLE) {
       health_paper(d, R, slot);
       continue;
     }
-    // A8 (part 2): a victim loses floor(e * num / den) of its post-eat
-    // energy to the attacker that won its claim, which gains the same amount
-    // (read from the victim's post-eat snapshot); claims are cleared in the
-    // birth-claim phase, after every attacker has read its victim's claim
+    // A8 (part 2): a victim -- an agent on a claimed cell -- loses
+    // floor(e * num / den) of its post-eat energy to the attacker that won
+    // the cell's claim, which gains the same amount (read from the victim's
+    // post-eat snapshot); claims are cleared in the birth-claim phase
     int en = d.energy[slot];
-    const int e = env_index(d, slot);
-    const int loss = d.claim_att[slot] ? (int)(((long long)en * R.attack_num) / R.attack_den) : 0;
+    const int pos = d.pos[slot];
+    const int loss = d.att_cell[ed.cell_off + pos] ? (int)(((long long)en * R.attack_num) / R.attack_den) : 0;
     int g = 0;
-    const int v = d.tgt[slot];
-    if (v >= 0 && claim_local_slot(d.claim_att[v]) == slot - d.env[e].slot_off) {
-      g = (int)(((long long)d.gain[v] * R.attack_num) / R.attack_den);
-      stat_add(d.stats_step, e, ST_ATTACK_HITS, 1);
-      stat_add(d.stats_step, e, ST_ENERGY_TRANSFERRED, g);
+    if (d.act[slot] == ACT_ATTACK) {
+      const int c = ed.cell_off + step_cell(pos, d.facing[slot], ed.side);
+      if (claim_local_slot(d.att_cell[c]) == slot - ed.slot_off) {
+        const int v = d.occ[c];
+        if (v >= 0) {
+          g = (int)(((long long)d.gain[v] * R.attack_num) / R.attack_den);
+          stat_add(d.stats_step, e, ST_ATTACK_HITS, 1);
+          stat_add(d.stats_step, e, ST_ENERGY_TRANSFERRED, g);
+        }
+      }
     }
     en = en - loss + g - R.e_metab;
     if (en <= 0) {
-      const int gpos = d.env[e].cell_off + d.pos[slot];
+      const int gpos = ed.cell_off + pos;
       d.alive[slot] = 0;
-      d.occ[gpos] = -1;
+      atomicSub(&d.tile_counts[slot / kCompactTile], 1);
       d.cellf[gpos] &= (uint8_t)~CELL_AGENT;
       stat_add(d.stats_step, e, ST_DEATHS, 1);
       stat_add(d.stats_step, e, ST_DEAD_ENERGY, en);
@@ -386,7 +381,29 @@ __device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs, int
   const uint32_t t = (uint32_t)d.step[0];
   for (int i = g0; i < n; i += gs) {
     const int slot = agent_slot(d, i, g0, first);
-    if (R.rules == RULES_SIMPLE && d.claim_att[slot]) d.claim_att[slot] = 0ull;
+    {
+      // clear this step's attack claims and, for an agent that died, its
+      // cell's occupant (kept for the attackers of the metabolism phase)
+      const EnvDesc ed = d.env[env_index(d, slot)];
+      const int pos = d.pos[slot];
+      const int a = d.act[slot];
+      if (!d.alive[slot]) d.occ[ed.cell_off + pos] = -1;
+      if (R.rules != RULES_SIMPLE) {
+        if (a == PA_ATTACK) {
+          const int side = ed.side;
+          const int px = pos % side, py = pos / side;
+          const int f = d.facing[slot], rt = (f + 1) & 3;
+          for (int fw = 1; fw <= 3; ++fw)
+            for (int lat = -1; lat <= 1; ++lat) {
+              const int cx = wrapi(px + fw * dir_dx(f) + lat * dir_dx(rt), side);
+              const int cy = wrapi(py + fw * dir_dy(f) + lat * dir_dy(rt), side);
+              d.att_cell[ed.cell_off + cy * side + cx] = 0ull;
+            }
+        }
+      } else if (a == ACT_ATTACK) {
+        d.att_cell[ed.cell_off + step_cell(pos, d.facing[slot], ed.side)] = 0ull;
+      }
+    }
     int bt = -1;
     if (d.alive[slot] && d.energy[slot] >= R.e_repro &&
         (R.rules == RULES_SIMPLE || d.act[slot] == PA_REPRODUCE) &&
@@ -453,6 +470,7 @@ __device__ __forceinline__ void make_child(const Dev &d, const Rules &R, const E
                               fminf(fmaxf(fmaf(R.sigma, n[2], pc.z), 0.0f), 1.0f), 0.0f);
   }
   d.alive[c] = 1;
+  atomicAdd(&d.tile_counts[c / kCompactTile], 1);
   d.pos[c] = bt;
   d.facing[c] = d.facing[p];
   d.parent[c] = p - ed.slot_off;
@@ -632,7 +650,7 @@ __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0,
   for (int w = b0; w < nb * items; w += bs) {
     const int b = w / items, it = w - b * items;
     const int2 pc = d.births[b];
-    const EnvDesc ed = d.env[d.env_of[pc.y]];
+    const EnvDesc ed = d.env[env_index(d, pc.y)];
     const uint32_t lp = (uint32_t)(pc.x - ed.slot_off);
     const float *pm = d.master + (int64_t)pc.x * mper;
     float *cm = d.master + (int64_t)pc.y * mper;
@@ -1056,7 +1074,6 @@ __global__ void __launch_bounds__(256) k_compact_scatter(Dev d) {
   ph_compact_scatter(d, blockIdx.x, gridDim.x, sh);
 }
 __global__ void k_move_apply_eat(Dev d, Rules R, int A) { ph_move_apply_eat(d, R, A, GRID_ARGS, -1); }
-__global__ void k_attack_claim(Dev d, Rules R) { ph_attack_claim(d, R, GRID_ARGS, -1); }
 __global__ void k_metab_death(Dev d, Rules R) { ph_metab_death(d, R, GRID_ARGS, -1); }
 __global__ void k_birth_claim(Dev d, Rules R) { ph_birth_claim(d, R, GRID_ARGS, -1); }
 __global__ void __launch_bounds__(1024) k_birth_assign(Dev d, Rules R) {
@@ -1079,40 +1096,66 @@ __global__ void k_finish(Dev d, Rules R) { ph_finish(d, R); }
 constexpr unsigned kBarrierSpinLimit = 40u * 1000u * 1000u;  // x >= 64 ns: > 2.5 s
 constexpr int kStatusTimeout = 4;
 
-// Grid-wide barrier for a co-resident (cooperative) grid: sense reversal
-// on a generation counter.  The wait is bounded by `budget` polls: when it
-// runs out, the status word records a timeout and every CTA leaves the
-// kernel at its next barrier.  Returns false when the kernel must stop.
-__device__ bool grid_sync(const Dev &d, unsigned nblocks, unsigned budget, int *s_flag) {
+// Grid-wide barrier for a co-resident (cooperative) grid.  One arrival
+// count per launch: at its k-th barrier every CTA adds 1 (a reduction whose
+// result it does not wait for) and waits until the count reaches
+// k * nblocks; the launch's last CTA clears the count (finish_if_last).  The
+// wait is bounded by `budget` polls: when it runs out, the status word
+// records a timeout and the CTA adds kBroken to the count, which releases
+// every present and later wait of the launch as failed, so every CTA leaves
+// the kernel at its next barrier.  Returns false when the kernel must stop.
+constexpr unsigned kBroken = 1u << 30;  // above any k * nblocks
+
+__device__ bool grid_sync(const Dev &d, unsigned nblocks, unsigned budget, unsigned &k, int *s_flag) {
   __syncthreads();
+  ++k;
   if (nblocks == 1) return true;  // one CTA: the block barrier is the grid barrier
   if (threadIdx.x == 0) {
-    cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(d.barrier[BAR_GEN]);
     cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(d.barrier[BAR_COUNT]);
-    cuda::atomic_ref<int, cuda::thread_scope_device> status(d.counters[CNT_STATUS]);
-    const unsigned g = gen.load(cuda::memory_order_acquire);
+    const unsigned target = k * nblocks;
     __threadfence();
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(d.barrier + BAR_COUNT) : "memory");
+    unsigned it = 0, v;
     int ok = 1;
-    if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == nblocks - 1) {
-      cnt.store(0u, cuda::memory_order_relaxed);
-      gen.fetch_add(1u, cuda::memory_order_release);
-    } else {
-      unsigned it = 0;
-      while (gen.load(cuda::memory_order_acquire) == g) {
-        if (++it > budget) {
-          status.fetch_or(kStatusTimeout, cuda::memory_order_relaxed);
-          ok = 0;
-          break;
-        }
-        if (it > 2048) __nanosleep(64);  // spin first: most waits are short
+    while ((v = cnt.load(cuda::memory_order_acquire)) < target) {
+      if (++it > budget) {
+        cuda::atomic_ref<int, cuda::thread_scope_device>(d.counters[CNT_STATUS])
+            .fetch_or(kStatusTimeout, cuda::memory_order_relaxed);
+        cnt.fetch_add(kBroken, cuda::memory_order_relaxed);
+        ok = 0;
+        break;
       }
+      if (it > 2048) __nanosleep(64);  // spin first: most waits are short
     }
-    __threadfence();
-    if (status.load(cuda::memory_order_relaxed) & kStatusTimeout) ok = 0;
+    if (v >= kBroken) ok = 0;
     *s_flag = ok;
   }
   __syncthreads();
   return *s_flag != 0;
+}
+
+// The last CTA of the launch to arrive here (an arrival count, no wait)
+// folds the step's statistics: every other CTA has finished its work, and
+// its atomics are visible, when it arrives.
+__device__ void finish_if_last(const Dev &d, const Rules &R, unsigned nblocks, int *s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> done(d.barrier[BAR_DONE]);
+    const unsigned prev = done.fetch_add(1u, cuda::memory_order_acq_rel);
+    *s_flag = prev == nblocks - 1;
+    if (*s_flag) {
+      // every other CTA has passed its last barrier: the next launch's
+      // arrivals start from zero
+      done.store(0u, cuda::memory_order_relaxed);
+      cuda::atomic_ref<unsigned, cuda::thread_scope_device>(d.barrier[BAR_COUNT]).store(0u, cuda::memory_order_relaxed);
+    }
+  }
+  __syncthreads();
+  if (*s_flag) {
+    __threadfence();
+    ph_finish(d, R);
+  }
 }
 
 __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rules R) {
@@ -1133,37 +1176,41 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   // the poll budget of every wait.
   if (d.barrier[BAR_ABSENT_CTA] == blockIdx.x + 1u) return;
   const unsigned budget = d.barrier[BAR_BUDGET] ? d.barrier[BAR_BUDGET] : kBarrierSpinLimit;
+  unsigned bar = 0;  // barriers passed in this launch (the same sequence in every CTA)
   const int g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   // each thread's first alive-list entry, loaded once for all phases
   const int first = g0 < d.counters[CNT_N_ALIVE] ? d.alive_list[g0] : -1;
   ph_move_apply_eat(d, R, L.A, g0, gs, first);
-  if (!grid_sync(d, nb, budget, &s_flag)) return;
-  ph_attack_claim(d, R, g0, gs, first);
-  if (!grid_sync(d, nb, budget, &s_flag)) return;
+  if (!grid_sync(d, nb, budget, bar, &s_flag)) return;
   ph_metab_death(d, R, g0, gs, first);
-  if (!grid_sync(d, nb, budget, &s_flag)) return;
+  if (!grid_sync(d, nb, budget, bar, &s_flag)) return;
   // regrowth (with photosynthesis and the flow's transfers) needs only the
   // state after the deaths, and birth claims read only wall and agent bits,
   // which regrowth keeps: the two share an interval
   ph_birth_claim(d, R, g0, gs, first);
   ph_regrow(d, R, g0, gs);
   if (R.rules == RULES_TERRAIN) ph_flow_out(d, g0, gs);
-  if (!grid_sync(d, nb, budget, &s_flag)) return;
+  if (!grid_sync(d, nb, budget, bar, &s_flag)) return;
   // Every claim is in, and the count of claimants does not change again
-  // before the last barrier, so every CTA takes the same branch.  On a step
-  // without a birth claim, slot assignment and mutation have nothing to do
-  // and their barrier is skipped.
-  if (cuda::atomic_ref<int, cuda::thread_scope_device>(d.counters[CNT_CONTENDERS]).load(
-          cuda::memory_order_relaxed) != 0) {
+  // in this launch, so every CTA takes the same branch.  On a step without
+  // a birth claim, slot assignment and mutation have nothing to do and
+  // their barrier is skipped.
+  const bool births = cuda::atomic_ref<int, cuda::thread_scope_device>(d.counters[CNT_CONTENDERS]).load(
+                          cuda::memory_order_relaxed) != 0;
+  if (births) {
     ph_birth_assign(d, R, blockIdx.x, gridDim.x, S);
-    if (!grid_sync(d, nb, budget, &s_flag)) return;
-    ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale);
+    if (!grid_sync(d, nb, budget, bar, &s_flag)) return;
   }
-  ph_compact_count(d, blockIdx.x, gridDim.x, S.sh);
-  if (!grid_sync(d, nb, budget, &s_flag)) return;
+  // The alive set is final.  The rest -- the water flow's second pass, the
+  // next step's alive list (from the tile counts that deaths and births
+  // kept), the children's weights -- writes nothing that another CTA reads
+  // in this launch, so no barrier follows: the last CTA to get here folds
+  // the statistics.  Mutation work starts from the last CTA, the alive list
+  // from the first.
   if (R.rules == RULES_TERRAIN) ph_flow_in(d, g0, gs);
   ph_compact_scatter(d, blockIdx.x, gridDim.x, S.sh);
-  if (blockIdx.x == gridDim.x - 1) ph_finish(d, R);
+  if (births) ph_mutate(d, L, R, gridDim.x - 1 - blockIdx.x, gridDim.x, msm, s_scale);
+  finish_if_last(d, R, nb, &s_flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -1215,7 +1262,6 @@ cudaError_t launch_env_phases(const Dev &d, const Layout &L, const Rules &R, con
   }
   const int T = 256;
   k_move_apply_eat<<<g.slot_blocks, T, 0, s>>>(d, R, L.A);
-  k_attack_claim<<<g.slot_blocks, T, 0, s>>>(d, R);
   k_metab_death<<<g.slot_blocks, T, 0, s>>>(d, R);
   k_birth_claim<<<g.slot_blocks, T, 0, s>>>(d, R);
   k_birth_assign<<<d.n_envs, 1024, 0, s>>>(d, R);
@@ -1227,9 +1273,9 @@ cudaError_t launch_env_phases(const Dev &d, const Layout &L, const Rules &R, con
     k_flow_in<<<fb, T, 0, s>>>(d);
   }
   k_finish<<<1, 1024, 0, s>>>(d, R);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return launch_compact(d, s);
+  // the tile counts are current: the second pass of the compaction only
+  k_compact_scatter<<<compact_tiles(d.total_slots), 256, 0, s>>>(d);
+  return cudaGetLastError();
 }
 
 }  // namespace eco

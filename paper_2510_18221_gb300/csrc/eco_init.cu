@@ -50,6 +50,7 @@ __global__ void k_init_cells(Dev d, Rules R) {
     d.claim_move[c] = 0ull;
     d.cnt_move[c] = 0u;
     d.claim_birth[c] = 0ull;
+    d.att_cell[c] = 0ull;
   }
 }
 
@@ -77,12 +78,10 @@ __global__ void k_init_agents(Dev d, Rules R) {
     d.act[s] = 0;
     d.tgt[s] = -1;
     d.gain[s] = 0;
-    d.claim_att[s] = 0ull;
     d.hp[s] = (founder && R.rules != RULES_SIMPLE) ? R.hp_max : 0;
     d.a_water[s] = (founder && R.rules == RULES_TERRAIN) ? R.w_init : 0;
     d.a_bio[s] = (founder && R.rules == RULES_TERRAIN) ? R.b_body : 0;
     d.age[s] = 0;
-    d.dmg[s] = 0;
     // colour trait (Sec. 3.3): three uniforms of COLOUR at counter (slot, 0, 0, 0)
     float4 col = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (founder) {

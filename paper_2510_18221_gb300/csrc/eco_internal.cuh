@@ -4,11 +4,11 @@
 // Layout in HBM (one workspace, carved at create):
 //   per cell (all environments concatenated): cellf u8 (bit0 food, bit1
 //     wall, bit2 agent), occ i32 (global slot or -1), claim_move u64,
-//     cnt_move u32, claim_birth u64;
+//     cnt_move u32, claim_birth u64, att_cell u64 (this step's attack claim);
 //   per slot (all environments concatenated): alive u8, pos i32 (env-local
 //     cell y*L+x), facing u8, energy i32, parent i32 (env-local), birth i32,
-//     act u8, env u16, tgt i32, gain i32, claim_att u64, logits f32[A],
-//     hp i32, age i32, dmg i32 (paper rules);
+//     act u8, env u16, tgt i32, gain i32, logits f32[A], hp i32, age i32
+//     (paper rules);
 //   per cell, paper rules: res i32 (energy lying on the cell; the food bit
 //     of cellf is res > 0);
 //   per slot: colour f32x4 (the colour trait, RGB + padding);
@@ -276,10 +276,11 @@ struct Dev {
   uint16_t *env_of;
   int32_t *tgt;
   int32_t *gain;
-  unsigned long long *claim_att;
+  unsigned long long *att_cell;  // [total_cells] this step's attack claim (simple rules:
+                                 // the best key; paper rules: the attacker count)
   float *logits;
   int32_t *alive_list;
-  int32_t *tile_counts;  // [compact tiles] alive slots per tile of 4096
+  int32_t *tile_counts;  // [compact tiles] alive slots per tile of 4096 (kept by deaths and births)
   unsigned *barrier;     // [BAR_N] grid barrier of the persistent form and its test words
   int32_t *counters;    // [0] n_alive, [1] n_births, [2] status, [3..] spare
   int2 *births;         // (parent global, child global)
@@ -299,7 +300,6 @@ struct Dev {
   uint8_t *bflag;          // [total_slots] birth pass flags
   int32_t *hp;             // [total_slots] paper rules: HP (quarter points)
   int32_t *age;            // [total_slots] paper rules: steps survived
-  int32_t *dmg;            // [total_slots] paper rules: attack damage this step
   int32_t *res;            // [total_cells] paper rules: energy on the cell
   float4 *colour;          // [total_slots] colour trait (x, y, z = RGB; w = 0)
   // terrain rules
@@ -314,16 +314,17 @@ struct Dev {
 
 constexpr int kAliveRing = 4096;
 
-// Words of Dev::barrier: the persistent form's grid barrier (arrival count,
-// generation) and two failure-detection test words (0 = off): one more than
-// the index of a CTA that leaves before its first barrier, and the poll
-// budget of the barrier's waits.
+// Words of Dev::barrier: the persistent form's grid barrier (the launch's
+// arrival count; word 1 is unused), two failure-detection test words (0 =
+// off: one more than the index of a CTA that leaves before its first
+// barrier, and the poll budget of the barrier's waits), and the count of
+// CTAs done with the launch (the last one folds the statistics).
 enum : int {
   BAR_COUNT = 0,
-  BAR_GEN = 1,
   BAR_ABSENT_CTA = 2,
   BAR_BUDGET = 3,
-  BAR_N = 4,
+  BAR_DONE = 4,
+  BAR_N = 5,
 };
 
 enum : int {
