@@ -276,13 +276,14 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.gain = k.take<int32_t>(slots);
   D.logits = k.take<float>((size_t)slots * L.A);
   D.alive_list = k.take<int32_t>(slots);
-  D.tile_counts = k.take<int32_t>(compact_tiles((int)slots));
+  D.tile_counts = k.take<int32_t>(2 * compact_tiles((int)slots));
   D.barrier = k.take<unsigned>(BAR_N);
   D.births = k.take<int2>(slots);
   D.free_list = k.take<int32_t>(slots);
   D.bflag = k.take<uint8_t>(slots);
   D.birth_contenders = k.take<int32_t>(E);
   D.contenders = k.take<int32_t>(slots);
+  D.bcell = k.take<int32_t>(slots);
   D.stats_step = k.take<long long>((size_t)E * N_ST);
   D.stats_total = k.take<long long>((size_t)E * N_ST);
   D.stats_last = k.take<long long>((size_t)E * N_ST);
@@ -1027,6 +1028,9 @@ extern "C" int eco_write_state(eco_handle *h, int32_t env, const eco_state_view 
   }
   CUDA_TRY(h, launch_recount(h->d, h->R, s));
   CUDA_TRY(h, launch_compact(h->d, s));
+  // the persistent form's arrival counts are kept per step parity, which a
+  // written step may change: both start from zero
+  CUDA_TRY(h, cudaMemsetAsync(h->d.barrier + BAR_COUNT0, 0, 2 * sizeof(unsigned), s));
   CUDA_TRY(h, cudaStreamSynchronize(s));
   return ECO_OK;
 }

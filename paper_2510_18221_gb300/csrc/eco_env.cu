@@ -42,8 +42,9 @@ int grid_for(long long n, int threads, int max_blocks) {
 // slots: each tile counts its alive slots; then each tile adds up the
 // counts of the tiles before it (a few dozen numbers) and writes its slots.
 // The step itself runs only the second pass: every death and birth adjusts
-// its tile's count as it happens, so the counts are exact when the alive
-// set is final (the first pass runs after reset and state writes).
+// its tile's count as it happens (the fast birth path's children are added
+// by the scatter itself), so the counts are exact when the alive set is
+// final (the first pass runs after reset and state writes).
 // Slot order keeps the warps of the policy kernel streaming neighbouring
 // weight blocks at the same time.  Block-level: the first 256 threads of a
 // CTA of any size >= 256 cover a tile.
@@ -70,26 +71,52 @@ __device__ __forceinline__ uint32_t alive_mask16(const Dev &d, int s0) {
   return mask;
 }
 
+// Tile counts are kept per step parity: step t's deaths and births adjust
+// counts[t & 1], and its scatter writes counts[(t + 1) & 1] for the next
+// step (so a scatter never reads a count another CTA is writing).
+__device__ __forceinline__ int32_t *tile_counts_of(const Dev &d, uint32_t t) {
+  return d.tile_counts + (t & 1u) * compact_tiles(d.total_slots);
+}
+
 __device__ void ph_compact_count(const Dev &d, int b0, int bs, int *sh) {
   const int tiles = compact_tiles(d.total_slots);
+  int32_t *cur = tile_counts_of(d, (uint32_t)d.step[0]);
   for (int tile = b0; tile < tiles; tile += bs) {
     const uint32_t mask =
         threadIdx.x < kCompactTile / 16 ? alive_mask16(d, tile * kCompactTile + threadIdx.x * 16) : 0u;
     int total;
     block_exclusive_scan(__popc(mask), &total, sh);
-    if (threadIdx.x == 0) d.tile_counts[tile] = total;
+    if (threadIdx.x == 0) cur[tile] = total;
   }
 }
 
-__device__ void ph_compact_scatter(const Dev &d, int b0, int bs, int *sh) {
+// children (global slots, ascending, nchild of them) are this step's
+// births that the alive bytes may not show yet (the fast birth path writes
+// them concurrently); cmask is a 4096-bit shared-memory scratch.
+__device__ void ph_compact_scatter(const Dev &d, int b0, int bs, int *sh, uint32_t t, const int *children,
+                                   int nchild, uint32_t *cmask) {
   const int tiles = compact_tiles(d.total_slots);
+  const int32_t *cur = tile_counts_of(d, t);
+  int32_t *nxt = tile_counts_of(d, t + 1u);
   for (int tile = b0; tile < tiles; tile += bs) {
+    const int t0 = tile * kCompactTile;
     int before = 0;
-    for (int k = threadIdx.x; k < tile; k += blockDim.x) before += d.tile_counts[k];
+    for (int k = threadIdx.x; k < tile; k += blockDim.x) before += cur[k];
+    for (int i = threadIdx.x; i < nchild; i += blockDim.x) before += children[i] < t0 ? 1 : 0;
+    if (nchild > 0) {
+      for (int w = threadIdx.x; w < kCompactTile / 32; w += blockDim.x) cmask[w] = 0u;
+      __syncthreads();
+      for (int i = threadIdx.x; i < nchild; i += blockDim.x) {
+        const int c = children[i] - t0;
+        if (c >= 0 && c < kCompactTile) atomicOr(&cmask[c >> 5], 1u << (c & 31));
+      }
+    }
     int base;
     block_exclusive_scan(before, &base, sh);  // base = sum over the earlier tiles
-    const int s0 = tile * kCompactTile + threadIdx.x * 16;
+    const int s0 = t0 + threadIdx.x * 16;
     uint32_t mask = threadIdx.x < kCompactTile / 16 ? alive_mask16(d, s0) : 0u;
+    if (nchild > 0 && threadIdx.x < kCompactTile / 16)
+      mask |= (cmask[threadIdx.x >> 1] >> ((threadIdx.x & 1) * 16)) & 0xFFFFu;
     int total;
     int at = base + block_exclusive_scan(__popc(mask), &total, sh);
     while (mask) {
@@ -97,6 +124,7 @@ __device__ void ph_compact_scatter(const Dev &d, int b0, int bs, int *sh) {
       d.alive_list[at++] = s0 + k;
       mask &= mask - 1;
     }
+    if (threadIdx.x == 0) nxt[tile] = total;
     if (tile == tiles - 1 && threadIdx.x == 0) d.counters[CNT_N_ALIVE] = base + total;
   }
 }
@@ -122,15 +150,27 @@ __device__ __forceinline__ int env_index(const Dev &d, int slot) {
 // nobody moves into it); then every agent eats the food of its post-move
 // cell, when the rules say it eats (nobody else can be on that cell); then
 // attackers claim their target cells.
-__device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, int g0, int gs, int first) {
+__device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, int g0, int gs, int first,
+                                  uint32_t t) {
   const int n = d.counters[CNT_N_ALIVE];
-  const uint32_t t = (uint32_t)d.step[0];
   for (int i = g0; i < n; i += gs) {
     const int slot = agent_slot(d, i, g0, first);
     const int e = env_index(d, slot);
     const EnvDesc ed = d.env[e];
     const int tc = d.tgt[slot];
     int pos = d.pos[slot];
+    const int a = d.act[slot];
+    // simple rules: the food bits of the cells this agent can end on, read
+    // with the claim (no other agent changes them in this phase: only the
+    // agent on a cell eats its food, and regrowth comes later)
+    const bool eats_simple = R.rules == RULES_SIMPLE &&
+                             ((R.flags & F_AUTO_EAT) || (n_actions > ACT_EAT && a == ACT_EAT));
+    uint32_t cf_stay = 0u, cf_move = 0u;
+    if (eats_simple) {
+      cf_stay = d.cellf[ed.cell_off + pos];
+      if (tc >= 0) cf_move = d.cellf[ed.cell_off + tc];
+    }
+    bool moved = false;
     if (tc >= 0) {
       const int gc = ed.cell_off + tc;
       bool won = claim_local_slot(d.claim_move[gc]) == slot - ed.slot_off;
@@ -143,12 +183,12 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
         d.cellf[gc] |= (uint8_t)CELL_AGENT;
         d.pos[slot] = tc;
         pos = tc;
+        moved = true;
         stat_add(d.stats_step, e, ST_MOVES, 1);
       } else {
         stat_add(d.stats_step, e, ST_MOVE_LOST, 1);
       }
     }
-    const int a = d.act[slot];
     if (R.rules == RULES_TERRAIN && (a == TA_DRINK || a == TA_EAT_BIO)) {
       // terrain rules: drink or eat biomass, min(bite, on the cell, room)
       const int gpos = ed.cell_off + pos;
@@ -186,11 +226,11 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
           }
         }
       }
-    } else if ((R.flags & F_AUTO_EAT) || (n_actions > ACT_EAT && a == ACT_EAT)) {
-      const int gpos = ed.cell_off + pos;
-      const uint8_t cf = d.cellf[gpos];
+    } else if (eats_simple) {
+      const uint32_t cf = moved ? cf_move : cf_stay;
       if (cf & CELL_FOOD) {
-        d.cellf[gpos] = (uint8_t)(cf & ~CELL_FOOD);
+        // the agent stands on this cell: its agent bit is set
+        d.cellf[ed.cell_off + pos] = (uint8_t)((cf & ~CELL_FOOD) | CELL_AGENT);
         d.energy[slot] += R.e_food;
         stat_add(d.stats_step, e, ST_EATEN, 1);
       }
@@ -234,7 +274,7 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
 // is, and starve_damage HP), heal only with heal_water water (spent onto the
 // cell too), and drop water and biomass at death.  One agent per cell, so
 // the cell's counters are this agent's to change here.
-__device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int slot) {
+__device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int slot, uint32_t t) {
   int en = d.energy[slot];
   int hp = d.hp[slot];
   const int age = d.age[slot];
@@ -307,7 +347,7 @@ __device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int s
     }
     d.cellf[gpos] = cf;  // occ keeps the slot until the birth-claim phase
     d.alive[slot] = 0;
-    atomicSub(&d.tile_counts[slot / kCompactTile], 1);
+    atomicSub(&tile_counts_of(d, t)[slot / kCompactTile], 1);
     stat_add(d.stats_step, e, ST_DEATHS, 1);
     stat_add(d.stats_step, e, ST_DEAD_ENERGY, en);
     en = 0;
@@ -324,7 +364,7 @@ __device__ __forceinline__ void health_paper(const Dev &d, const Rules &R, int s
 // A dying agent clears its alive flag and its cell's agent bit here, but
 // its occ entry only in the birth-claim phase, so that an attacker that
 // won the agent's cell still finds it in this phase.
-__device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs, int first) {
+__device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs, int first, uint32_t t) {
   const int n = d.counters[CNT_N_ALIVE];
   for (int i = g0; i < n; i += gs) {
     const int slot = agent_slot(d, i, g0, first);
@@ -336,7 +376,7 @@ __device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs, int
       if (R.flags & F_CANCEL_ALL) d.cnt_move[ed.cell_off + tc] = 0u;
     }
     if (R.rules != RULES_SIMPLE) {
-      health_paper(d, R, slot);
+      health_paper(d, R, slot, t);
       continue;
     }
     // A8 (part 2): a victim -- an agent on a claimed cell -- loses
@@ -362,7 +402,7 @@ __device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs, int
     if (en <= 0) {
       const int gpos = ed.cell_off + pos;
       d.alive[slot] = 0;
-      atomicSub(&d.tile_counts[slot / kCompactTile], 1);
+      atomicSub(&tile_counts_of(d, t)[slot / kCompactTile], 1);
       d.cellf[gpos] &= (uint8_t)~CELL_AGENT;
       stat_add(d.stats_step, e, ST_DEATHS, 1);
       stat_add(d.stats_step, e, ST_DEAD_ENERGY, en);
@@ -376,9 +416,8 @@ __device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs, int
 // reproduce; terrain rules: that also carry b_body + b_child biomass and
 // w_child water) claim the free non-wall cell behind them and join their
 // environment's contender list.
-__device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs, int first) {
+__device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs, int first, uint32_t t) {
   const int n = d.counters[CNT_N_ALIVE];
-  const uint32_t t = (uint32_t)d.step[0];
   for (int i = g0; i < n; i += gs) {
     const int slot = agent_slot(d, i, g0, first);
     {
@@ -420,6 +459,7 @@ __device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs, int
         const int k = atomicAdd(&d.birth_contenders[e], 1);
         atomicAdd(&d.counters[CNT_CONTENDERS], 1);
         d.contenders[ed.slot_off + k] = slot;
+        d.bcell[ed.slot_off + k] = c;
         bt = c;
       }
     }
@@ -436,16 +476,24 @@ __device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs, int
 // contenders than kBirthCap fall back to a full scan of the slots.
 // ---------------------------------------------------------------------------
 constexpr int kBirthCap = 2048;
+// Claimants of one step up to which a single world takes the fast birth
+// path (its free-slot list holds this many slots).
+constexpr int kFastBirths = 256;
 
 struct BirthSmem {
   int sh[33];
   int win[kBirthCap];
   int free_[kBirthCap];
-  int nwin;
+  int nwin, nborn;
+  uint32_t cmask[kCompactTile / 32];  // the scatter's children of one tile
 };
 
+// A child at the free slot c (global) of the parent p (global), on the birth
+// cell bt (env-local).  record: also bump the tile count of step t and
+// append (p, c) to the births list (the general path; the fast path's
+// scatter and mutation take the pairs from shared memory instead).
 __device__ __forceinline__ void make_child(const Dev &d, const Rules &R, const EnvDesc &ed, int p,
-                                           int c, int bt, uint32_t t) {
+                                           int c, int bt, uint32_t t, bool record) {
   const bool paper = R.rules != RULES_SIMPLE;
   const int en = d.energy[p];
   const int ce = paper ? R.e_child : en / 2;
@@ -470,96 +518,117 @@ __device__ __forceinline__ void make_child(const Dev &d, const Rules &R, const E
                               fminf(fmaxf(fmaf(R.sigma, n[2], pc.z), 0.0f), 1.0f), 0.0f);
   }
   d.alive[c] = 1;
-  atomicAdd(&d.tile_counts[c / kCompactTile], 1);
   d.pos[c] = bt;
   d.facing[c] = d.facing[p];
   d.parent[c] = p - ed.slot_off;
   d.birth[c] = (int)t;
   d.occ[ed.cell_off + bt] = c;
   d.cellf[ed.cell_off + bt] |= (uint8_t)CELL_AGENT;
-  const int b = atomicAdd(&d.counters[CNT_N_BIRTHS], 1);
-  d.births[b] = make_int2(p, c);
+  if (record) {
+    atomicAdd(&tile_counts_of(d, t)[c / kCompactTile], 1);
+    const int b = atomicAdd(&d.counters[CNT_N_BIRTHS], 1);
+    d.births[b] = make_int2(p, c);
+  }
 }
 
-__device__ void birth_assign_env(const Dev &d, const Rules &R, int e, BirthSmem &S) {
+// Block-level: the nc contenders of environment e that won their birth
+// cell's claim, in ascending slot order, into S.win (INT_MAX fills the
+// sorted tail up to a power of two); returns their count (every thread).
+__device__ int sort_winners(const Dev &d, const EnvDesc &ed, int nc, BirthSmem &S) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int p2 = 1;
+  while (p2 < nc) p2 <<= 1;
+  for (int i = tid; i < p2; i += nt) {
+    int v = 0x7FFFFFFF;
+    if (i < nc) {
+      const int g = d.contenders[ed.slot_off + i];
+      const int bt = d.bcell[ed.slot_off + i];
+      if (claim_local_slot(d.claim_birth[ed.cell_off + bt]) == g - ed.slot_off) v = g;
+    }
+    S.win[i] = v;
+  }
+  __syncthreads();
+  for (int k = 2; k <= p2; k <<= 1) {  // bitonic sort, ascending
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < p2; i += nt) {
+        const int l = i ^ j;
+        if (l > i) {
+          const int a = S.win[i], b = S.win[l];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            S.win[i] = b;
+            S.win[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    int nw = 0;
+    while (nw < p2 && S.win[nw] != 0x7FFFFFFF) ++nw;
+    S.nwin = nw;
+  }
+  __syncthreads();
+  return S.nwin;
+}
+
+// Block-level: the first (at most limit) free slots of environment e, env-
+// local and ascending, into out; returns how many (every thread).  64
+// slots per thread per pass.
+__device__ int scan_free_slots(const Dev &d, const EnvDesc &ed, int limit, int *out, int *sh) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int found = 0;
+  for (int base = 0; base < ed.n_slots && found < limit; base += nt * 64) {
+    const int s0 = base + tid * 64;
+    unsigned long long mask = 0ull;
+    const uint8_t *al = d.alive + ed.slot_off + s0;
+    if (s0 + 64 <= ed.n_slots && ((reinterpret_cast<uintptr_t>(al) & 15) == 0)) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint4 v = reinterpret_cast<const uint4 *>(al)[q];
+        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          // 0xFF in each byte that is 0 (a free slot); its top bits, gathered
+          // by the multiply, are the four slots' free bits
+          const uint32_t z = __vcmpeq4(w4[k], 0u) & 0x80808080u;
+          mask |= (unsigned long long)((z * 0x00204081u) >> 28) << (q * 16 + 4 * k);
+        }
+      }
+    } else {
+      for (int k = 0; k < 64; ++k)
+        if (s0 + k < ed.n_slots && !al[k]) mask |= 1ull << k;
+    }
+    int total;
+    int r = found + block_exclusive_scan(__popcll(mask), &total, sh);
+    while (mask && r < limit) {
+      const int k = __ffsll(mask) - 1;
+      out[r++] = s0 + k;
+      mask &= mask - 1;
+    }
+    found += total;
+    __syncthreads();
+  }
+  return found < limit ? found : limit;
+}
+
+__device__ void birth_assign_env(const Dev &d, const Rules &R, int e, BirthSmem &S, uint32_t t) {
   const int nc = d.birth_contenders[e];
   if (nc == 0) return;  // uniform across the CTA
   const EnvDesc ed = d.env[e];
-  const uint32_t t = (uint32_t)d.step[0];
   const int tid = threadIdx.x, nt = blockDim.x;
   int born = 0, failed = 0;
 
   if (nc <= kBirthCap) {
-    int p2 = 1;
-    while (p2 < nc) p2 <<= 1;
-    for (int i = tid; i < p2; i += nt) {
-      int v = 0x7FFFFFFF;
-      if (i < nc) {
-        const int g = d.contenders[ed.slot_off + i];
-        const int bt = d.tgt[g];
-        if (claim_local_slot(d.claim_birth[ed.cell_off + bt]) == g - ed.slot_off) v = g;
-      }
-      S.win[i] = v;
-    }
-    __syncthreads();
-    for (int k = 2; k <= p2; k <<= 1) {  // bitonic sort, ascending
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int i = tid; i < p2; i += nt) {
-          const int l = i ^ j;
-          if (l > i) {
-            const int a = S.win[i], b = S.win[l];
-            const bool up = (i & k) == 0;
-            if ((a > b) == up) {
-              S.win[i] = b;
-              S.win[l] = a;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
-    if (tid == 0) {
-      int nw = 0;
-      while (nw < p2 && S.win[nw] != 0x7FFFFFFF) ++nw;
-      S.nwin = nw;
-    }
-    __syncthreads();
-    const int nwin = S.nwin;
-    int found = 0;  // the first nwin free slots, 64 slots per thread per pass
-    for (int base = 0; base < ed.n_slots && found < nwin; base += nt * 64) {
-      const int s0 = base + tid * 64;
-      unsigned long long mask = 0ull;
-      const uint8_t *al = d.alive + ed.slot_off + s0;
-      if (s0 + 64 <= ed.n_slots && ((reinterpret_cast<uintptr_t>(al) & 15) == 0)) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint4 v = reinterpret_cast<const uint4 *>(al)[q];
-          const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-          for (int k = 0; k < 16; ++k)
-            if (!((w4[k >> 2] >> ((k & 3) * 8)) & 0xFFu)) mask |= 1ull << (q * 16 + k);
-        }
-      } else {
-        for (int k = 0; k < 64; ++k)
-          if (s0 + k < ed.n_slots && !al[k]) mask |= 1ull << k;
-      }
-      int total;
-      int r = found + block_exclusive_scan(__popcll(mask), &total, S.sh);
-      while (mask && r < nwin) {
-        const int k = __ffsll(mask) - 1;
-        S.free_[r++] = s0 + k;
-        mask &= mask - 1;
-      }
-      found += total;
-      __syncthreads();
-    }
-    const int nfree = found < nwin ? found : nwin;
+    const int nwin = sort_winners(d, ed, nc, S);
+    const int nfree = scan_free_slots(d, ed, nwin, S.free_, S.sh);
     for (int i = tid; i < nwin; i += nt) {
       const int p = S.win[i];
       const int bt = d.tgt[p];
       d.claim_birth[ed.cell_off + bt] = 0ull;
       if (i < nfree) {
-        make_child(d, R, ed, p, ed.slot_off + S.free_[i], bt, t);
+        make_child(d, R, ed, p, ed.slot_off + S.free_[i], bt, t, true);
         ++born;
       } else {
         ++failed;
@@ -602,7 +671,7 @@ __device__ void birth_assign_env(const Dev &d, const Rules &R, int e, BirthSmem 
         ++failed;
         continue;
       }
-      make_child(d, R, ed, p, ed.slot_off + d.free_list[ed.slot_off + r], bt, t);
+      make_child(d, R, ed, p, ed.slot_off + d.free_list[ed.slot_off + r], bt, t, true);
       ++born;
     }
   }
@@ -612,8 +681,8 @@ __device__ void birth_assign_env(const Dev &d, const Rules &R, int e, BirthSmem 
   __syncthreads();  // S is reused by the next environment of this CTA
 }
 
-__device__ void ph_birth_assign(const Dev &d, const Rules &R, int b0, int bs, BirthSmem &S) {
-  for (int e = b0; e < d.n_envs; e += bs) birth_assign_env(d, R, e, S);
+__device__ void ph_birth_assign(const Dev &d, const Rules &R, int b0, int bs, BirthSmem &S, uint32_t t) {
+  for (int e = b0; e < d.n_envs; e += bs) birth_assign_env(d, R, e, S, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -622,34 +691,38 @@ __device__ void ph_birth_assign(const Dev &d, const Rules &R, int b0, int bs, Bi
 // slot, p / 4) for logical parameter p; then the child's streamed BF16 /
 // FP8 copy is re-derived from its new master.
 //
-// Work items per birth: H/16 tiles of W1 (16 output rows x all D inputs),
-// H/16 tiles of W2, and one item for W3 and the biases.  A tile draws its
+// Work items per birth: H/8 tiles of W_in (8 output rows x all D inputs),
+// H/8 tiles of each hidden layer, and one item for W_out and the biases
+// (small tiles: a step's few births spread over many CTAs).  A tile draws its
 // normals in logical order (one Philox block per four parameters) into
 // shared memory, then walks the master in its physical (input-major) order
 // so global reads and writes are contiguous; FP8 row scales come from the
 // tile's complete rows.  Block-level (any multiple of 32 threads).
 // ---------------------------------------------------------------------------
-constexpr int kMutRows = 16;
+constexpr int kMutRows = 8;
+constexpr int kMutRowsLog2 = 3;
+static_assert((1 << kMutRowsLog2) == kMutRows, "kMutRows is a power of two");
 
 __device__ __forceinline__ uint8_t e4m3_sat(float v) {
   return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
 }
 
+// The births are (par[b], chi[b]) for b < nbirths when par is given (the
+// fast path's pairs in shared memory), else the births list.
 __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0, int bs, float *msm,
-                          float *s_scale) {
+                          float *s_scale, uint32_t t, const int *par, const int *chi, int nbirths) {
   const int D = L.D, H = L.H, A = L.A;
-  const int nb = d.counters[CNT_N_BIRTHS];
+  const int nb = par ? nbirths : d.counters[CNT_N_BIRTHS];
   const int tiles = H / kMutRows;
   const int wtiles = (1 + L.L) * tiles;  // W_in, then each hidden layer
   const int items = wtiles + 1;
-  const uint32_t t = (uint32_t)d.step[0];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int64_t mper = L.mstride / 4;
 
   for (int w = b0; w < nb * items; w += bs) {
     const int b = w / items, it = w - b * items;
-    const int2 pc = d.births[b];
+    const int2 pc = par ? make_int2(par[b], chi[b]) : d.births[b];
     const EnvDesc ed = d.env[env_index(d, pc.y)];
     const uint32_t lp = (uint32_t)(pc.x - ed.slot_off);
     const float *pm = d.master + (int64_t)pc.x * mper;
@@ -671,20 +744,29 @@ __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0,
         const U4 r = philox(t, lp, (uint32_t)g, 0u, ed.seed, S_MUTATE);
         float n4[4];
         normals4(r, n4);
+        // tile position (row rr, input j) of the group's first element,
+        // then stepped: a group of four crosses at most one row end
+        const int off0 = 4 * g - lbase;
+        int rr = off0 >= 0 ? off0 / nin : 0, j = off0 - rr * nin;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const int off = 4 * g + k - lbase;
-          if (off >= 0 && off < nel) {
-            const int rr = off / nin, j = off - rr * nin;
-            msm[rr * rs + j] = n4[k];
+          const int off = off0 + k;
+          if (off >= 0 && off < nel) msm[rr * rs + j] = n4[k];
+          if (++j == nin) {
+            j = 0;
+            ++rr;
           }
         }
       }
       __syncthreads();
+      // the parent's master is read-only in this launch (parents and
+      // children are different slots), so its loads need not wait for the
+      // child's stores
+#pragma unroll 4
       for (int idx = tid; idx < nel; idx += nt) {
-        const int j = idx >> 4, rr = idx & (kMutRows - 1);
+        const int j = idx >> kMutRowsLog2, rr = idx & (kMutRows - 1);
         const int q = qbase + j * H + o0 + rr;
-        const float v = fmaf(R.sigma, msm[rr * rs + j], pm[q]);
+        const float v = fmaf(R.sigma, msm[rr * rs + j], __ldg(pm + q));
         cm[q] = v;
         msm[rr * rs + j] = v;
       }
@@ -692,7 +774,7 @@ __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0,
       if (R.precision == PREC_BF16) {
         __nv_bfloat16 *qw = reinterpret_cast<__nv_bfloat16 *>(cq);
         for (int idx = tid; idx < nel; idx += nt) {
-          const int j = idx >> 4, rr = idx & (kMutRows - 1);
+          const int j = idx >> kMutRowsLog2, rr = idx & (kMutRows - 1);
           qw[qbase + j * H + o0 + rr] = __float2bfloat16_rn(msm[rr * rs + j]);
         }
       } else if (R.precision == PREC_FP8) {
@@ -710,7 +792,7 @@ __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0,
         }
         __syncthreads();
         for (int idx = tid; idx < nel; idx += nt) {
-          const int j = idx >> 4, rr = idx & (kMutRows - 1);
+          const int j = idx >> kMutRowsLog2, rr = idx & (kMutRows - 1);
           cq[qbase + j * H + o0 + rr] = e4m3_sat(__fdiv_rn(msm[rr * rs + j], s_scale[rr]));
         }
       }
@@ -724,7 +806,7 @@ __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0,
         const int q = e < n3 ? q3 + e : L.nW + (e - n3);
         const int p = layout_logical(L, q);
         const U4 r = philox(t, lp, (uint32_t)(p >> 2), 0u, ed.seed, S_MUTATE);
-        const float v = fmaf(R.sigma, normal_of(r, p & 3), pm[q]);
+        const float v = fmaf(R.sigma, normal_of(r, p & 3), __ldg(pm + q));
         cm[q] = v;
         if (e < n3) msm[e] = v;
         else if (R.precision != PREC_FP32) reinterpret_cast<float *>(cq + L.off_bias)[e - n3] = v;
@@ -761,9 +843,8 @@ size_t mutate_smem_bytes(const Layout &L) {
 
 // A12: regrowth of food on non-wall food-less cells; four cells per thread
 // share one Philox block (counter (step, local cell / 4)).
-__device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs) {
+__device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs, uint32_t t) {
   const int groups = d.total_cells >> 2;
-  const uint32_t t = (uint32_t)d.step[0];
   for (int g = g0; g < groups; g += gs) {
     const int c0 = g << 2;
     const int e = env_of_cell(d.env, d.n_envs, c0);
@@ -999,10 +1080,31 @@ __device__ void ph_flow_in(const Dev &d, int g0, int gs) {
   }
 }
 
+// The step's birth counters back to zero (block-level), after clearing the
+// birth-cell claims of the step's claimants (the fast birth path leaves
+// them: its CTAs read them until the launch ends).
+__device__ void reset_birth_counters(const Dev &d) {
+  for (int e = 0; e < d.n_envs; ++e) {
+    const EnvDesc ed = d.env[e];
+    const int nc = d.birth_contenders[e];
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) d.claim_birth[ed.cell_off + d.bcell[ed.slot_off + i]] = 0ull;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < d.n_envs; i += blockDim.x) d.birth_contenders[i] = 0;
+  if (threadIdx.x == 0) {
+    d.counters[CNT_N_BIRTHS] = 0;
+    d.counters[CNT_CONTENDERS] = 0;
+    d.counters[CNT_N_FREE] = 0;
+  }
+}
+
 // A13: fold this step's counters into the per-environment records and
 // advance the step counter (one CTA).  Agent-steps and attacks come from the
 // action histogram the policy kernel counted.
-__device__ void ph_finish(const Dev &d, const Rules &R) {
+// reset_counters: also clear this step's birth counters (the one-kernel-
+// per-phase form; the persistent form clears them at its next launch's
+// start, because its other CTAs may still read them here).
+__device__ void ph_finish(const Dev &d, const Rules &R, bool reset_counters) {
   const long long t = d.step[0];
   for (int i = threadIdx.x; i < d.n_envs; i += blockDim.x) {
     long long *st = d.stats_step + i * N_ST;
@@ -1052,12 +1154,8 @@ __device__ void ph_finish(const Dev &d, const Rules &R) {
   }
   __syncthreads();
   for (int i = threadIdx.x; i < d.n_envs * N_ST; i += blockDim.x) d.stats_step[i] = 0;
-  for (int i = threadIdx.x; i < d.n_envs; i += blockDim.x) d.birth_contenders[i] = 0;
-  if (threadIdx.x == 0) {
-    d.step[0] = t + 1;
-    d.counters[CNT_N_BIRTHS] = 0;
-    d.counters[CNT_CONTENDERS] = 0;
-  }
+  if (threadIdx.x == 0) d.step[0] = t + 1;
+  if (reset_counters) reset_birth_counters(d);
 }
 
 // ---------------------------------------------------------------------------
@@ -1071,24 +1169,26 @@ __global__ void __launch_bounds__(256) k_compact_count(Dev d) {
 }
 __global__ void __launch_bounds__(256) k_compact_scatter(Dev d) {
   __shared__ int sh[33];
-  ph_compact_scatter(d, blockIdx.x, gridDim.x, sh);
+  ph_compact_scatter(d, blockIdx.x, gridDim.x, sh, (uint32_t)d.step[0], nullptr, 0, nullptr);
 }
-__global__ void k_move_apply_eat(Dev d, Rules R, int A) { ph_move_apply_eat(d, R, A, GRID_ARGS, -1); }
-__global__ void k_metab_death(Dev d, Rules R) { ph_metab_death(d, R, GRID_ARGS, -1); }
-__global__ void k_birth_claim(Dev d, Rules R) { ph_birth_claim(d, R, GRID_ARGS, -1); }
+#define STEP_T ((uint32_t)d.step[0])
+__global__ void k_move_apply_eat(Dev d, Rules R, int A) { ph_move_apply_eat(d, R, A, GRID_ARGS, -1, STEP_T); }
+__global__ void k_metab_death(Dev d, Rules R) { ph_metab_death(d, R, GRID_ARGS, -1, STEP_T); }
+__global__ void k_birth_claim(Dev d, Rules R) { ph_birth_claim(d, R, GRID_ARGS, -1, STEP_T); }
 __global__ void __launch_bounds__(1024) k_birth_assign(Dev d, Rules R) {
   __shared__ BirthSmem S;
-  ph_birth_assign(d, R, blockIdx.x, gridDim.x, S);
+  ph_birth_assign(d, R, blockIdx.x, gridDim.x, S, STEP_T);
 }
 __global__ void __launch_bounds__(256) k_mutate(Dev d, Layout L, Rules R) {
   extern __shared__ __align__(16) float msm[];
   __shared__ float s_scale[kMutRows];
-  ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale);
+  ph_mutate(d, L, R, blockIdx.x, gridDim.x, msm, s_scale, STEP_T, nullptr, nullptr, 0);
 }
-__global__ void k_regrow(Dev d, Rules R) { ph_regrow(d, R, GRID_ARGS); }
+__global__ void k_regrow(Dev d, Rules R) { ph_regrow(d, R, GRID_ARGS, STEP_T); }
 __global__ void k_flow_out(Dev d) { ph_flow_out(d, GRID_ARGS); }
 __global__ void k_flow_in(Dev d) { ph_flow_in(d, GRID_ARGS); }
-__global__ void k_finish(Dev d, Rules R) { ph_finish(d, R); }
+__global__ void k_finish(Dev d, Rules R) { ph_finish(d, R, true); }
+#undef STEP_T
 
 // ---------------------------------------------------------------------------
 // The persistent form: all phases in one cooperative launch.
@@ -1097,29 +1197,31 @@ constexpr unsigned kBarrierSpinLimit = 40u * 1000u * 1000u;  // x >= 64 ns: > 2.
 constexpr int kStatusTimeout = 4;
 
 // Grid-wide barrier for a co-resident (cooperative) grid.  One arrival
-// count per launch: at its k-th barrier every CTA adds 1 (a reduction whose
-// result it does not wait for) and waits until the count reaches
-// k * nblocks; the launch's last CTA clears the count (finish_if_last).  The
-// wait is bounded by `budget` polls: when it runs out, the status word
-// records a timeout and the CTA adds kBroken to the count, which releases
-// every present and later wait of the launch as failed, so every CTA leaves
-// the kernel at its next barrier.  Returns false when the kernel must stop.
+// count per launch (count = the word of the step's parity; the launch of
+// step t clears the word of step t + 1 at its start): at its k-th barrier
+// every CTA adds 1 (a reduction whose result it does not wait for) and
+// waits until the count reaches k * nblocks.  The wait is bounded by
+// `budget` polls: when it runs out, the status word records a timeout and
+// the CTA adds kBroken to the count, which releases every present and
+// later wait of the launch as failed, so every CTA leaves the kernel at its
+// next barrier.  Returns false when the kernel must stop.
 constexpr unsigned kBroken = 1u << 30;  // above any k * nblocks
 
-__device__ bool grid_sync(const Dev &d, unsigned nblocks, unsigned budget, unsigned &k, int *s_flag) {
+__device__ bool grid_sync(unsigned *count, int *status_word, unsigned nblocks, unsigned budget, unsigned &k,
+                          int *s_flag) {
   __syncthreads();
   ++k;
   if (nblocks == 1) return true;  // one CTA: the block barrier is the grid barrier
   if (threadIdx.x == 0) {
-    cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(d.barrier[BAR_COUNT]);
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(*count);
     const unsigned target = k * nblocks;
     __threadfence();
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(d.barrier + BAR_COUNT) : "memory");
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
     unsigned it = 0, v;
     int ok = 1;
     while ((v = cnt.load(cuda::memory_order_acquire)) < target) {
       if (++it > budget) {
-        cuda::atomic_ref<int, cuda::thread_scope_device>(d.counters[CNT_STATUS])
+        cuda::atomic_ref<int, cuda::thread_scope_device>(*status_word)
             .fetch_or(kStatusTimeout, cuda::memory_order_relaxed);
         cnt.fetch_add(kBroken, cuda::memory_order_relaxed);
         ok = 0;
@@ -1134,28 +1236,23 @@ __device__ bool grid_sync(const Dev &d, unsigned nblocks, unsigned budget, unsig
   return *s_flag != 0;
 }
 
-// The last CTA of the launch to arrive here (an arrival count, no wait)
-// folds the step's statistics: every other CTA has finished its work, and
-// its atomics are visible, when it arrives.
-__device__ void finish_if_last(const Dev &d, const Rules &R, unsigned nblocks, int *s_flag) {
+// The fast birth path (one environment, at most kFastBirths claimants):
+// every CTA derives the same births from the claims and the free-slot list
+// (written in the birth-claim phase, when the deaths were final), so no
+// barrier separates the slot assignment
+// from the mutation and the alive list: pair i is (S.win[i], S.free_[i]),
+// i < S.nborn, of S.nwin winners.
+__device__ void fast_births(const Dev &d, BirthSmem &S, int nc) {
+  const EnvDesc ed = d.env[0];
+  // the free list is read with the claims, not after the sort: at most nc
+  // slots are needed
+  const int nfree = d.counters[CNT_N_FREE];
+  for (int i = threadIdx.x; i < nc && i < nfree; i += blockDim.x)
+    S.free_[i] = ed.slot_off + d.free_list[ed.slot_off + i];
+  const int nwin = sort_winners(d, ed, nc, S);  // synchronises the CTA
+  const int nborn = nwin < nfree ? nwin : nfree;
+  if (threadIdx.x == 0) S.nborn = nborn;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    cuda::atomic_ref<unsigned, cuda::thread_scope_device> done(d.barrier[BAR_DONE]);
-    const unsigned prev = done.fetch_add(1u, cuda::memory_order_acq_rel);
-    *s_flag = prev == nblocks - 1;
-    if (*s_flag) {
-      // every other CTA has passed its last barrier: the next launch's
-      // arrivals start from zero
-      done.store(0u, cuda::memory_order_relaxed);
-      cuda::atomic_ref<unsigned, cuda::thread_scope_device>(d.barrier[BAR_COUNT]).store(0u, cuda::memory_order_relaxed);
-    }
-  }
-  __syncthreads();
-  if (*s_flag) {
-    __threadfence();
-    ph_finish(d, R);
-  }
 }
 
 __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rules R) {
@@ -1164,53 +1261,99 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   __shared__ float s_scale[kMutRows];
   __shared__ int s_flag;
   const unsigned nb = gridDim.x;
+  const int g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  // The launch's first reads, issued together: the step, the failure-
+  // detection test words (0 unless armed by eco_arm_barrier_timeout,
+  // cleared by eco_reset: a CTA that leaves before its first barrier, and the
+  // poll budget of every wait), the alive count and each thread's first
+  // alive-list entry (loaded once for all phases; the list has total_slots
+  // entries, so the read stays in bounds even past the count).  Every phase
+  // takes the step from here: CTA 0 advances the step word in the last
+  // interval while other CTAs still work on this step.
+  const uint32_t t = (uint32_t)d.step[0];
+  const unsigned absent = d.barrier[BAR_ABSENT_CTA], budget_word = d.barrier[BAR_BUDGET];
+  const int n_alive = d.counters[CNT_N_ALIVE];
+  const int first_entry = g0 < d.total_slots ? d.alive_list[g0] : -1;
   // A timeout recorded by an earlier launch (the status word keeps it until
-  // eco_reset) stops this step at once, before any barrier count changes.
-  if (threadIdx.x == 0)
+  // eco_reset) stops this step at once, before any barrier count changes;
+  // one read per CTA decides for all its threads.
+  if (threadIdx.x == 0) {
     s_flag = cuda::atomic_ref<int, cuda::thread_scope_device>(d.counters[CNT_STATUS]).load(
                  cuda::memory_order_relaxed) & kStatusTimeout;
+  }
   __syncthreads();
   if (s_flag) return;
-  // Failure-detection test words, 0 unless armed by eco_arm_barrier_timeout
-  // (cleared by eco_reset): a CTA that leaves before its first barrier, and
-  // the poll budget of every wait.
-  if (d.barrier[BAR_ABSENT_CTA] == blockIdx.x + 1u) return;
-  const unsigned budget = d.barrier[BAR_BUDGET] ? d.barrier[BAR_BUDGET] : kBarrierSpinLimit;
+  if (absent == blockIdx.x + 1u) return;
+  const unsigned budget = budget_word ? budget_word : kBarrierSpinLimit;
+  unsigned *count = d.barrier + BAR_COUNT0 + (t & 1u);
   unsigned bar = 0;  // barriers passed in this launch (the same sequence in every CTA)
-  const int g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  // each thread's first alive-list entry, loaded once for all phases
-  const int first = g0 < d.counters[CNT_N_ALIVE] ? d.alive_list[g0] : -1;
-  ph_move_apply_eat(d, R, L.A, g0, gs, first);
-  if (!grid_sync(d, nb, budget, bar, &s_flag)) return;
-  ph_metab_death(d, R, g0, gs, first);
-  if (!grid_sync(d, nb, budget, bar, &s_flag)) return;
+  if (blockIdx.x == 0) {
+    // the previous launch is over: clear its birth counters and the next
+    // launch's arrival count (this launch's was cleared by the previous one,
+    // or by eco_reset); nothing reads them before the second barrier
+    reset_birth_counters(d);
+    if (threadIdx.x == 0) d.barrier[BAR_COUNT0 + ((t + 1u) & 1u)] = 0u;
+  }
+  const int first = g0 < n_alive ? first_entry : -1;
+  ph_move_apply_eat(d, R, L.A, g0, gs, first, t);
+  if (!grid_sync(count, d.counters + CNT_STATUS, nb, budget, bar, &s_flag)) return;
+  ph_metab_death(d, R, g0, gs, first, t);
+  if (!grid_sync(count, d.counters + CNT_STATUS, nb, budget, bar, &s_flag)) return;
   // regrowth (with photosynthesis and the flow's transfers) needs only the
   // state after the deaths, and birth claims read only wall and agent bits,
   // which regrowth keeps: the two share an interval
-  ph_birth_claim(d, R, g0, gs, first);
-  ph_regrow(d, R, g0, gs);
-  if (R.rules == RULES_TERRAIN) ph_flow_out(d, g0, gs);
-  if (!grid_sync(d, nb, budget, bar, &s_flag)) return;
-  // Every claim is in, and the count of claimants does not change again
-  // in this launch, so every CTA takes the same branch.  On a step without
-  // a birth claim, slot assignment and mutation have nothing to do and
-  // their barrier is skipped.
-  const bool births = cuda::atomic_ref<int, cuda::thread_scope_device>(d.counters[CNT_CONTENDERS]).load(
-                          cuda::memory_order_relaxed) != 0;
-  if (births) {
-    ph_birth_assign(d, R, blockIdx.x, gridDim.x, S);
-    if (!grid_sync(d, nb, budget, bar, &s_flag)) return;
+  ph_birth_claim(d, R, g0, gs, first, t);
+  if (d.n_envs == 1 && blockIdx.x == gridDim.x - 1) {
+    // one world: list its first free slots for the fast birth path (the
+    // deaths are final, no birth has happened yet), on the CTA with the
+    // least grid-stride work in this interval
+    const int m = scan_free_slots(d, d.env[0], kFastBirths, d.free_list, S.sh);
+    if (threadIdx.x == 0) d.counters[CNT_N_FREE] = m;
   }
-  // The alive set is final.  The rest -- the water flow's second pass, the
-  // next step's alive list (from the tile counts that deaths and births
-  // kept), the children's weights -- writes nothing that another CTA reads
-  // in this launch, so no barrier follows: the last CTA to get here folds
-  // the statistics.  Mutation work starts from the last CTA, the alive list
-  // from the first.
+  ph_regrow(d, R, g0, gs, t);
+  if (R.rules == RULES_TERRAIN) ph_flow_out(d, g0, gs);
+  if (!grid_sync(count, d.counters + CNT_STATUS, nb, budget, bar, &s_flag)) return;
+  // Every claim is in, and the count of claimants does not change again
+  // in this launch, so every CTA takes the same branch.
+  const int claimants = cuda::atomic_ref<int, cuda::thread_scope_device>(d.counters[CNT_CONTENDERS]).load(
+      cuda::memory_order_relaxed);
+  const bool fast = claimants > 0 && d.n_envs == 1 && claimants <= kFastBirths;
+  if (claimants > 0 && !fast) {
+    // general path: one CTA per environment assigns the slots, then a barrier
+    ph_birth_assign(d, R, blockIdx.x, gridDim.x, S, t);
+    if (!grid_sync(count, d.counters + CNT_STATUS, nb, budget, bar, &s_flag)) return;
+  } else if (fast) {
+    fast_births(d, S, claimants);
+  }
+  // Every statistic of the step is in (the fast path's births are counted
+  // here): CTA 0 folds them while the others go on.
+  if (blockIdx.x == 0) {
+    if (fast && threadIdx.x == 0) {
+      d.stats_step[ST_BIRTHS] += S.nborn;
+      d.stats_step[ST_FAILED_BIRTHS] += S.nwin - S.nborn;
+    }
+    __syncthreads();
+    ph_finish(d, R, false);
+  }
+  if (fast) {
+    // the births' side effects, pair by pair over every thread of the grid
+    // (the claims stay until the next launch clears them: other CTAs may
+    // still be reading them in fast_births)
+    const EnvDesc ed = d.env[0];
+    for (int i = g0; i < S.nborn; i += gs) {
+      const int p = S.win[i];
+      make_child(d, R, ed, p, S.free_[i], d.tgt[p], t, false);
+    }
+  }
+  // The rest -- the water flow's second pass, the next step's alive list,
+  // the children's weights -- writes nothing that another CTA reads in this
+  // launch, so no barrier follows.  Mutation work starts from the last CTA,
+  // the alive list from the first.
   if (R.rules == RULES_TERRAIN) ph_flow_in(d, g0, gs);
-  ph_compact_scatter(d, blockIdx.x, gridDim.x, S.sh);
-  if (births) ph_mutate(d, L, R, gridDim.x - 1 - blockIdx.x, gridDim.x, msm, s_scale);
-  finish_if_last(d, R, nb, &s_flag);
+  ph_compact_scatter(d, blockIdx.x, gridDim.x, S.sh, t, fast ? S.free_ : nullptr, fast ? S.nborn : 0, S.cmask);
+  if (claimants > 0)
+    ph_mutate(d, L, R, gridDim.x - 1 - blockIdx.x, gridDim.x, msm, s_scale, t, fast ? S.win : nullptr,
+              fast ? S.free_ : nullptr, fast ? S.nborn : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1272,9 +1415,10 @@ cudaError_t launch_env_phases(const Dev &d, const Layout &L, const Rules &R, con
     k_flow_out<<<fb, T, 0, s>>>(d);
     k_flow_in<<<fb, T, 0, s>>>(d);
   }
-  k_finish<<<1, 1024, 0, s>>>(d, R);
-  // the tile counts are current: the second pass of the compaction only
+  // the tile counts are current: the second pass of the compaction only,
+  // before k_finish advances the step (the counts are kept per step parity)
   k_compact_scatter<<<compact_tiles(d.total_slots), 256, 0, s>>>(d);
+  k_finish<<<1, 1024, 0, s>>>(d, R);
   return cudaGetLastError();
 }
 

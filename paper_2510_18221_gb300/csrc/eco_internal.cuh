@@ -280,13 +280,15 @@ struct Dev {
                                  // the best key; paper rules: the attacker count)
   float *logits;
   int32_t *alive_list;
-  int32_t *tile_counts;  // [compact tiles] alive slots per tile of 4096 (kept by deaths and births)
+  int32_t *tile_counts;  // [2][compact tiles] alive slots per tile of 4096, per step parity
+                         // (kept by deaths and births)
   unsigned *barrier;     // [BAR_N] grid barrier of the persistent form and its test words
   int32_t *counters;    // [0] n_alive, [1] n_births, [2] status, [3..] spare
   int2 *births;         // (parent global, child global)
-  int32_t *free_list;   // per env: slot_off + rank
+  int32_t *free_list;   // per env: slot_off + rank (free slots in ascending order)
   int32_t *birth_contenders;  // [n_envs] count of this step's birth claimants
   int32_t *contenders;        // per env: slot_off + k -> k-th claimant (global slot)
+  int32_t *bcell;             // per env: slot_off + k -> its birth cell (env-local)
   long long *stats_step;   // [n_envs][N_ST] this step
   long long *stats_total;  // [n_envs][N_ST]
   long long *stats_last;   // [n_envs][N_ST]
@@ -314,17 +316,17 @@ struct Dev {
 
 constexpr int kAliveRing = 4096;
 
-// Words of Dev::barrier: the persistent form's grid barrier (the launch's
-// arrival count; word 1 is unused), two failure-detection test words (0 =
-// off: one more than the index of a CTA that leaves before its first
-// barrier, and the poll budget of the barrier's waits), and the count of
-// CTAs done with the launch (the last one folds the statistics).
+// Words of Dev::barrier: the persistent form's grid-barrier arrival counts
+// (one per step parity: a launch uses its step's word and clears the other
+// for the next launch) and two failure-detection test words (0 = off: one
+// more than the index of a CTA that leaves before its first barrier, and the
+// poll budget of the barrier's waits).
 enum : int {
-  BAR_COUNT = 0,
+  BAR_COUNT0 = 0,
+  BAR_COUNT1 = 1,
   BAR_ABSENT_CTA = 2,
   BAR_BUDGET = 3,
-  BAR_DONE = 4,
-  BAR_N = 5,
+  BAR_N = 4,
 };
 
 enum : int {
@@ -332,6 +334,7 @@ enum : int {
   CNT_N_BIRTHS = 1,
   CNT_STATUS = 2,
   CNT_CONTENDERS = 3,  // this step's birth claimants over all environments
+  CNT_N_FREE = 4,      // free slots listed for the fast birth path
   CNT_N = 8,
 };
 
