@@ -279,7 +279,8 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.tile_counts = k.take<int32_t>(2 * compact_tiles((int)slots));
   D.barrier = k.take<unsigned>(BAR_N);
   D.births = k.take<int2>(slots);
-  D.free_list = k.take<int32_t>(slots);
+  D.free_list = k.take<int32_t>(std::max((long long)slots, (long long)compact_tiles((int)slots) * 256));
+  D.free_tiles = k.take<int32_t>(compact_tiles((int)slots));
   D.bflag = k.take<uint8_t>(slots);
   D.birth_contenders = k.take<int32_t>(E);
   D.contenders = k.take<int32_t>(slots);

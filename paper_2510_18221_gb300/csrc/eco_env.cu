@@ -477,14 +477,17 @@ __device__ void ph_birth_claim(const Dev &d, const Rules &R, int g0, int gs, int
 // ---------------------------------------------------------------------------
 constexpr int kBirthCap = 2048;
 // Claimants of one step up to which a single world takes the fast birth
-// path (its free-slot list holds this many slots).
+// path (each compaction tile lists this many of its free slots), and the
+// most compaction tiles (4096 slots each) such a world may have.
 constexpr int kFastBirths = 256;
+constexpr int kMaxFastTiles = 256;
 
 struct BirthSmem {
   int sh[33];
   int win[kBirthCap];
   int free_[kBirthCap];
-  int nwin, nborn;
+  int nwin, nborn, nfree;
+  int tile_first[kMaxFastTiles];  // fast path: free slots before each tile
   uint32_t cmask[kCompactTile / 32];  // the scatter's children of one tile
 };
 
@@ -1094,7 +1097,6 @@ __device__ void reset_birth_counters(const Dev &d) {
   if (threadIdx.x == 0) {
     d.counters[CNT_N_BIRTHS] = 0;
     d.counters[CNT_CONTENDERS] = 0;
-    d.counters[CNT_N_FREE] = 0;
   }
 }
 
@@ -1236,6 +1238,38 @@ __device__ bool grid_sync(unsigned *count, int *status_word, unsigned nblocks, u
   return *s_flag != 0;
 }
 
+// One world, for the fast birth path: the first free slots of every
+// compaction tile of 4096 slots (at most kFastBirths, env-local, ascending)
+// into free_list[tile * kFastBirths + i], and the tile's free count into
+// free_tiles[tile]; once the deaths are final and before any birth.  Tile k
+// is scanned by CTA nb - 1 - k (the last CTAs have the least grid-stride
+// work in the birth-claim interval), four slots per thread.
+__device__ void list_free_slots(const Dev &d, int *sh) {
+  const int n = d.env[0].n_slots;
+  const int tiles = (n + kCompactTile - 1) / kCompactTile;
+  for (int tile = (int)gridDim.x - 1 - (int)blockIdx.x; tile >= 0 && tile < tiles; tile += gridDim.x) {
+    const int s0 = tile * kCompactTile + threadIdx.x * 4;
+    uint32_t mask = 0u;  // free bits of slots s0 .. s0 + 3
+    if (threadIdx.x < kCompactTile / 4) {
+      if (s0 + 4 <= n) {
+        const uint32_t w = *reinterpret_cast<const uint32_t *>(d.alive + s0);  // 4-byte aligned
+        mask = ((__vcmpeq4(w, 0u) & 0x80808080u) * 0x00204081u) >> 28;
+      } else {
+        for (int k = 0; k < 4; ++k)
+          if (s0 + k < n && !d.alive[s0 + k]) mask |= 1u << k;
+      }
+    }
+    int total;
+    int r = block_exclusive_scan(__popc(mask), &total, sh);
+    while (mask && r < kFastBirths) {
+      const int k = __ffs(mask) - 1;
+      d.free_list[tile * kFastBirths + r++] = s0 + k;
+      mask &= mask - 1;
+    }
+    if (threadIdx.x == 0) d.free_tiles[tile] = total;
+  }
+}
+
 // The fast birth path (one environment, at most kFastBirths claimants):
 // every CTA derives the same births from the claims and the free-slot list
 // (written in the birth-claim phase, when the deaths were final), so no
@@ -1244,13 +1278,27 @@ __device__ bool grid_sync(unsigned *count, int *status_word, unsigned nblocks, u
 // i < S.nborn, of S.nwin winners.
 __device__ void fast_births(const Dev &d, BirthSmem &S, int nc) {
   const EnvDesc ed = d.env[0];
-  // the free list is read with the claims, not after the sort: at most nc
-  // slots are needed
-  const int nfree = d.counters[CNT_N_FREE];
-  for (int i = threadIdx.x; i < nc && i < nfree; i += blockDim.x)
-    S.free_[i] = ed.slot_off + d.free_list[ed.slot_off + i];
+  // The first nc free slots (at most nc are needed), read with the claims
+  // rather than after the sort: from the per-tile lists of list_free_slots,
+  // tile k's entries covering ranks [before_k, before_k + min(free_k, cap)).
+  const int tiles = (ed.n_slots + kCompactTile - 1) / kCompactTile;
+  if (threadIdx.x == 0) {
+    int before = 0;
+    for (int k = 0; k < tiles; ++k) {
+      S.tile_first[k] = before;
+      before += d.free_tiles[k];
+    }
+    S.nfree = before;
+  }
+  __syncthreads();
+  const int want = nc < S.nfree ? nc : S.nfree;
+  for (int i = threadIdx.x; i < want; i += blockDim.x) {
+    int k = 0;
+    while (k + 1 < tiles && S.tile_first[k + 1] <= i) ++k;
+    S.free_[i] = ed.slot_off + d.free_list[k * kFastBirths + (i - S.tile_first[k])];
+  }
   const int nwin = sort_winners(d, ed, nc, S);  // synchronises the CTA
-  const int nborn = nwin < nfree ? nwin : nfree;
+  const int nborn = nwin < S.nfree ? nwin : S.nfree;
   if (threadIdx.x == 0) S.nborn = nborn;
   __syncthreads();
 }
@@ -1303,13 +1351,7 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   // state after the deaths, and birth claims read only wall and agent bits,
   // which regrowth keeps: the two share an interval
   ph_birth_claim(d, R, g0, gs, first, t);
-  if (d.n_envs == 1 && blockIdx.x == gridDim.x - 1) {
-    // one world: list its first free slots for the fast birth path (the
-    // deaths are final, no birth has happened yet), on the CTA with the
-    // least grid-stride work in this interval
-    const int m = scan_free_slots(d, d.env[0], kFastBirths, d.free_list, S.sh);
-    if (threadIdx.x == 0) d.counters[CNT_N_FREE] = m;
-  }
+  if (d.n_envs == 1 && compact_tiles(d.total_slots) <= kMaxFastTiles) list_free_slots(d, S.sh);
   ph_regrow(d, R, g0, gs, t);
   if (R.rules == RULES_TERRAIN) ph_flow_out(d, g0, gs);
   if (!grid_sync(count, d.counters + CNT_STATUS, nb, budget, bar, &s_flag)) return;
@@ -1317,7 +1359,8 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   // in this launch, so every CTA takes the same branch.
   const int claimants = cuda::atomic_ref<int, cuda::thread_scope_device>(d.counters[CNT_CONTENDERS]).load(
       cuda::memory_order_relaxed);
-  const bool fast = claimants > 0 && d.n_envs == 1 && claimants <= kFastBirths;
+  const bool fast = claimants > 0 && d.n_envs == 1 && claimants <= kFastBirths &&
+                    compact_tiles(d.total_slots) <= kMaxFastTiles;
   if (claimants > 0 && !fast) {
     // general path: one CTA per environment assigns the slots, then a barrier
     ph_birth_assign(d, R, blockIdx.x, gridDim.x, S, t);

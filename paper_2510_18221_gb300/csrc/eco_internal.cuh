@@ -285,7 +285,9 @@ struct Dev {
   unsigned *barrier;     // [BAR_N] grid barrier of the persistent form and its test words
   int32_t *counters;    // [0] n_alive, [1] n_births, [2] status, [3..] spare
   int2 *births;         // (parent global, child global)
-  int32_t *free_list;   // per env: slot_off + rank (free slots in ascending order)
+  int32_t *free_list;   // per env: slot_off + rank (free slots in ascending order); one
+                        // world's fast birth path: tile * 256 + rank, per tile of 4096 slots
+  int32_t *free_tiles;  // [compact tiles] one world: free slots per tile of 4096
   int32_t *birth_contenders;  // [n_envs] count of this step's birth claimants
   int32_t *contenders;        // per env: slot_off + k -> k-th claimant (global slot)
   int32_t *bcell;             // per env: slot_off + k -> its birth cell (env-local)
@@ -334,7 +336,6 @@ enum : int {
   CNT_N_BIRTHS = 1,
   CNT_STATUS = 2,
   CNT_CONTENDERS = 3,  // this step's birth claimants over all environments
-  CNT_N_FREE = 4,      // free slots listed for the fast birth path
   CNT_N = 8,
 };
 
