@@ -367,7 +367,11 @@ int eco_prepare(eco_handle *h);
  * pointer may be NULL).  Synchronises the stream. */
 int eco_read_stats(eco_handle *h, eco_stats *total, eco_stats *last, int32_t n_envs);
 
-/* Copy environment env's world state to / from the host.  Writing replaces
+/* Copy environment env's world state to / from the host (App. E,
+ * "Simulator design": the simulator's population-level interface hands the
+ * map state and the agent states to the population algorithm and takes
+ * them back; here they also serve checkpoints and the oracle's lock-step).
+ * Writing replaces
  * the listed arrays (NULL arrays are left unchanged; food, wall and occ
  * must be written together if any of them is written, as must alive / x /
  * y), then re-derives the derived device tables.  Both synchronise. */
@@ -386,7 +390,9 @@ int eco_set_rock(eco_handle *h, int32_t env, const int32_t *rock);
 int eco_get_rock(eco_handle *h, int32_t env, int32_t *rock);
 
 /* FP32 master parameters of slots [slot0, slot0 + n) of env, logical
- * order, host array [n][P].  Writing also re-derives the streamed
+ * order, host array [n][P]: the agents' heritable traits that App. E's
+ * population-level interface exchanges with the population algorithm
+ * (Sec. 3.3: the per-agent policy weights that mutation perturbs).  Writing also re-derives the streamed
  * BF16/FP8 copy of those slots.  Both synchronise. */
 int eco_read_params(eco_handle *h, int32_t env, int32_t slot0, int32_t n, float *out);
 int eco_write_params(eco_handle *h, int32_t env, int32_t slot0, int32_t n, const float *in);
