@@ -256,6 +256,7 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
     D.wq = reinterpret_cast<uint8_t *>(D.master);
   else
     D.wq = k.take<uint8_t>((size_t)slots * L.stride);
+  const size_t wq_end = k.off;
   *env_dev = k.take<EnvDesc>(E);
   D.env = *env_dev;
   D.cellf = k.take<uint8_t>(cells);
@@ -307,6 +308,11 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.flow = k.take<uint32_t>(cells);
   D.a_water = k.take<int32_t>(slots);
   D.a_bio = k.take<int32_t>(slots);
+  // The policy kernel's FP8 tail batches load up to kStreamSlack bytes past
+  // the last weight block (their products are skipped): the regions after
+  // the weights (the histogram alone is 256 KB per world) keep those loads
+  // inside the workspace, and this keeps that true for any layout.
+  if (k.off < wq_end + kStreamSlack) k.take<uint8_t>(wq_end + kStreamSlack - k.off);
   return (k.off + 255) & ~(size_t)255;
 }
 

@@ -317,6 +317,10 @@ struct Dev {
 };
 
 constexpr int kAliveRing = 4096;
+// Readable workspace bytes after the last slot's weight block: the policy
+// kernel's last, partial FP8 batch of a layer loads up to 32 lanes x 8 units
+// x 16 B past the layer's end (and skips those products).
+constexpr int kStreamSlack = 4096;
 
 // Words of Dev::barrier: the persistent form's grid-barrier arrival counts
 // (one per step parity: a launch uses its step's word and clears the other

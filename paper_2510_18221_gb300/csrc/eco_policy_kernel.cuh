@@ -242,6 +242,7 @@ __device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int 
   constexpr int UPJ = H / E;  // units per input
   constexpr int LG = Log2<UPJ>::v;
   static_assert((1 << LG) == UPJ && UPJ <= 32, "H / E must be a power of two <= 32");
+  static_assert(32 * UNROLL * 16 <= kStreamSlack, "a tail batch reads past the layer's end");
   float acc[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) acc[e] = 0.0f;
@@ -277,14 +278,41 @@ __device__ __forceinline__ void layer_in_major(const uint4 *__restrict__ w, int 
 #pragma unroll
     for (int k = 0; k < UNROLL; ++k) Unit<PREC>::fma(acc, v[k], x[j[k]]);
   }
-  for (; u < U; u += 32) {
-    if constexpr (SPARSE) {
-      const int jj = idx[u >> LG];
-      const uint4 v = ldg_stream(w + jj * UPJ + (u & (UPJ - 1)));
-      Unit<PREC>::fma(acc, v, x[jj]);
-    } else {
-      const uint4 v = ldg_stream(w + u);
-      Unit<PREC>::fma(acc, v, x[u >> LG]);
+  if constexpr (PREC == PREC_FP8) {
+    // FP8: the last, partial batch (fewer than UNROLL units left for this
+    // lane) issues every load before its first product, so the tail costs
+    // one memory latency.  Loads run up to 32 * UNROLL units past the
+    // layer's end (into the rest of the agent's block, or, after the last
+    // block, into the workspace's next kStreamSlack bytes), and the products
+    // of those units are skipped, so the products run in the same order as
+    // the single-unit loop below.
+    if (u < U) {
+      uint4 v[UNROLL];
+#pragma unroll
+      for (int k = 0; k < UNROLL; ++k) {
+        if constexpr (SPARSE) {
+          const int uu = min(u + 32 * k, U - 1);
+          v[k] = ldg_stream(w + idx[uu >> LG] * UPJ + (uu & (UPJ - 1)));
+        } else {
+          v[k] = ldg_stream(w + u + 32 * k);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < UNROLL; ++k) {
+        const int uu = u + 32 * k;
+        if (uu < U) Unit<PREC>::fma(acc, v[k], x[SPARSE ? idx[uu >> LG] : uu >> LG]);
+      }
+    }
+  } else {
+    for (; u < U; u += 32) {
+      if constexpr (SPARSE) {
+        const int jj = idx[u >> LG];
+        const uint4 v = ldg_stream(w + jj * UPJ + (u & (UPJ - 1)));
+        Unit<PREC>::fma(acc, v, x[jj]);
+      } else {
+        const uint4 v = ldg_stream(w + u);
+        Unit<PREC>::fma(acc, v, x[u >> LG]);
+      }
     }
   }
   layer_finish<PREC, H>(acc, bias, nbias, scale, out, lane, relu);
@@ -566,15 +594,26 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
   // are requested into L2 before that gather.
   if (lane == 0 && w0 < G_eff && w0 < n_alive)
     prefetch_l2(d.wq + (int64_t)d.alive_list[w0] * L.stride, (uint32_t)min((int64_t)4096, (int64_t)L.off_w2));
-  for (int i = w0 < G_eff ? w0 : n_alive; i < n_alive; i += G_eff) {
-    const int slot = d.alive_list[i];
-    const int env = d.env_of[slot];
+  // The next agent's slot is read one agent ahead, and its environment,
+  // cell and facing while the current agent's head is computed, so a new
+  // agent starts with its observation gather.  (A slot's facing is written
+  // only by the warp that computes it, in its own iteration.)
+  int i = w0 < G_eff ? w0 : n_alive;
+  int slot_n = 0, env_n = 0, pos_n = 0, f_n = 0;
+  if (i < n_alive) {
+    slot_n = d.alive_list[i];
+    env_n = d.env_of[slot_n];
+    pos_n = d.pos[slot_n];
+    f_n = d.facing[slot_n];
+  }
+  for (; i < n_alive; i += G_eff) {
+    const int slot = slot_n, env = env_n, pos = pos_n, f = f_n;
+    const bool more = i + G_eff < n_alive;
+    if (more) slot_n = d.alive_list[i + G_eff];
     if (env != e_cur) {
       flush();
       e_cur = env;
     }
-    const int pos = d.pos[slot];
-    const int f = d.facing[slot];
     int nb_cell = 0;
     uint32_t nb_flags = 0;
     gather_obs(d, L, R, slot, env, pos, f, xs, lane, kdiv, &nb_cell, &nb_flags);
@@ -619,16 +658,32 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
       nxt = tmp;
     }
 
+    if (more) {
+      env_n = d.env_of[slot_n];
+      pos_n = d.pos[slot_n];
+      f_n = d.facing[slot_n];
+    }
     // -- head: logits = (W_out h [+ b_out]) / exp(tau) (output-major rows of
     //    H / E units; the temperature only in the paper form)
     const uint4 *w3 = wb + L.off_w3 / 16;
     const int U3 = L.A * UPJ;
     const float *hb = bias + L.ns * H + L.L * H;  // head bias, then tau
     const float tmul = L.temp ? expf(-__ldg(hb + (L.out_bias ? L.A : 0))) : 1.0f;
-    for (int base = 0; base < U3; base += 32) {
-      const int u = base + lane;
-      const uint4 v = u < U3 ? ldg_stream(w3 + u) : make_uint4(0u, 0u, 0u, 0u);
-      head_group<PREC, H>(v, u, U3, cur, scale + H + L.L * H, hb, L.out_bias, L.temp, tmul, ls, lane);
+    // the head's groups of 32 units, up to kHeadBatch of them requested
+    // before the first one is reduced
+    constexpr int kHeadBatch = 4;
+    for (int base = 0; base < U3; base += 32 * kHeadBatch) {
+      uint4 hv[kHeadBatch];
+#pragma unroll
+      for (int g = 0; g < kHeadBatch; ++g) {
+        const int u = base + 32 * g + lane;
+        hv[g] = u < U3 ? ldg_stream(w3 + u) : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int g = 0; g < kHeadBatch; ++g)
+        if (base + 32 * g < U3)
+          head_group<PREC, H>(hv[g], base + 32 * g + lane, U3, cur, scale + H + L.L * H, hb, L.out_bias,
+                              L.temp, tmul, ls, lane);
     }
     __syncwarp();
 
