@@ -160,6 +160,10 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
     const int tc = d.tgt[slot];
     int pos = d.pos[slot];
     const int a = d.act[slot];
+    // read with the slot's other words, before this phase's stores: only
+    // this thread writes them in this phase
+    int en = d.energy[slot];
+    const int fac = d.facing[slot];
     // simple rules: the food bits of the cells this agent can end on, read
     // with the claim (no other agent changes them in this phase: only the
     // agent on a cell eats its food, and regrowth comes later)
@@ -231,14 +235,15 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
       if (cf & CELL_FOOD) {
         // the agent stands on this cell: its agent bit is set
         d.cellf[ed.cell_off + pos] = (uint8_t)((cf & ~CELL_FOOD) | CELL_AGENT);
-        d.energy[slot] += R.e_food;
+        en += R.e_food;
+        d.energy[slot] = en;
         stat_add(d.stats_step, e, ST_EATEN, 1);
       }
     }
     // simple rules: the post-eat energy, which attack transfers are computed
     // from, kept where an attacker can read it while the owner updates its
     // own energy in the metabolism phase
-    if (R.rules == RULES_SIMPLE) d.gain[slot] = d.energy[slot];
+    if (R.rules == RULES_SIMPLE) d.gain[slot] = en;
     // A8 (part 1): attacks claim their target cells.  An attacker does not
     // move (attack and move are different actions), so its cell and facing
     // are final here, while the agents it hits are only known once every
@@ -250,7 +255,7 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
       if (a == PA_ATTACK) {
         const int side = ed.side;
         const int px = pos % side, py = pos / side;
-        const int f = d.facing[slot], rt = (f + 1) & 3;
+        const int f = fac, rt = (f + 1) & 3;
         for (int fw = 1; fw <= 3; ++fw)
           for (int lat = -1; lat <= 1; ++lat) {
             const int cx = wrapi(px + fw * dir_dx(f) + lat * dir_dx(rt), side);
@@ -259,7 +264,7 @@ __device__ void ph_move_apply_eat(const Dev &d, const Rules &R, int n_actions, i
           }
       }
     } else if (a == ACT_ATTACK) {
-      const int c = step_cell(pos, d.facing[slot], ed.side);
+      const int c = step_cell(pos, fac, ed.side);
       const int local = slot - ed.slot_off;
       const U4 r = philox(t, (uint32_t)local, 0u, 0u, ed.seed, S_CLAIM_ATTACK);
       atomicMax(&d.att_cell[ed.cell_off + c], claim_key(r.x, local));
@@ -371,32 +376,41 @@ __device__ void ph_metab_death(const Dev &d, const Rules &R, int g0, int gs, int
     const int e = env_index(d, slot);
     const EnvDesc ed = d.env[e];
     const int tc = d.tgt[slot];
-    if (tc >= 0) {
-      d.claim_move[ed.cell_off + tc] = 0ull;
-      if (R.flags & F_CANCEL_ALL) d.cnt_move[ed.cell_off + tc] = 0u;
-    }
     if (R.rules != RULES_SIMPLE) {
+      if (tc >= 0) {
+        d.claim_move[ed.cell_off + tc] = 0ull;
+        if (R.flags & F_CANCEL_ALL) d.cnt_move[ed.cell_off + tc] = 0u;
+      }
       health_paper(d, R, slot, t);
       continue;
     }
     // A8 (part 2): a victim -- an agent on a claimed cell -- loses
     // floor(e * num / den) of its post-eat energy to the attacker that won
     // the cell's claim, which gains the same amount (read from the victim's
-    // post-eat snapshot); claims are cleared in the birth-claim phase
+    // post-eat snapshot); claims are cleared in the birth-claim phase.
+    // Every word this needs is final in this phase (attack claims, cells'
+    // occupants and the snapshots were written before the barrier), so all
+    // are requested before the phase's first store: the slot's own words,
+    // then the claims on its own and its target cell with the target's
+    // occupant, then the occupant's snapshot.
     int en = d.energy[slot];
     const int pos = d.pos[slot];
-    const int loss = d.att_cell[ed.cell_off + pos] ? (int)(((long long)en * R.attack_num) / R.attack_den) : 0;
+    const bool attacker = d.act[slot] == ACT_ATTACK;
+    const int fac = d.facing[slot];
+    const unsigned long long hit = d.att_cell[ed.cell_off + pos];
+    const int c = ed.cell_off + step_cell(pos, fac, ed.side);
+    const bool won = attacker && claim_local_slot(d.att_cell[c]) == slot - ed.slot_off;
+    const int v = attacker ? d.occ[c] : -1;
+    if (tc >= 0) {
+      d.claim_move[ed.cell_off + tc] = 0ull;
+      if (R.flags & F_CANCEL_ALL) d.cnt_move[ed.cell_off + tc] = 0u;
+    }
+    const int loss = hit ? (int)(((long long)en * R.attack_num) / R.attack_den) : 0;
     int g = 0;
-    if (d.act[slot] == ACT_ATTACK) {
-      const int c = ed.cell_off + step_cell(pos, d.facing[slot], ed.side);
-      if (claim_local_slot(d.att_cell[c]) == slot - ed.slot_off) {
-        const int v = d.occ[c];
-        if (v >= 0) {
-          g = (int)(((long long)d.gain[v] * R.attack_num) / R.attack_den);
-          stat_add(d.stats_step, e, ST_ATTACK_HITS, 1);
-          stat_add(d.stats_step, e, ST_ENERGY_TRANSFERRED, g);
-        }
-      }
+    if (won && v >= 0) {
+      g = (int)(((long long)d.gain[v] * R.attack_num) / R.attack_den);
+      stat_add(d.stats_step, e, ST_ATTACK_HITS, 1);
+      stat_add(d.stats_step, e, ST_ENERGY_TRANSFERRED, g);
     }
     en = en - loss + g - R.e_metab;
     if (en <= 0) {
@@ -1335,7 +1349,14 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   const unsigned budget = budget_word ? budget_word : kBarrierSpinLimit;
   unsigned *count = d.barrier + BAR_COUNT0 + (t & 1u);
   unsigned bar = 0;  // barriers passed in this launch (the same sequence in every CTA)
-  if (blockIdx.x == 0) {
+  // Housekeeping goes to CTAs with little else to do in its interval: the
+  // per-agent phases take one agent per thread from CTA 0 on, and the
+  // alive list's tiles go to CTAs 0 .. tiles - 1.
+  const int tiles = compact_tiles(d.total_slots);
+  const unsigned last = nb - 1u;
+  const unsigned fold_cta = (unsigned)tiles < nb ? (unsigned)tiles : 0u;      // statistics
+  const unsigned birth_cta = fold_cta + 1u < nb ? fold_cta + 1u : 0u;         // fast-path births
+  if (blockIdx.x == last) {
     // the previous launch is over: clear its birth counters and the next
     // launch's arrival count (this launch's was cleared by the previous one,
     // or by eco_reset); nothing reads them before the second barrier
@@ -1369,8 +1390,8 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
     fast_births(d, S, claimants);
   }
   // Every statistic of the step is in (the fast path's births are counted
-  // here): CTA 0 folds them while the others go on.
-  if (blockIdx.x == 0) {
+  // here): one CTA folds them while the others go on.
+  if (blockIdx.x == fold_cta) {
     if (fast && threadIdx.x == 0) {
       d.stats_step[ST_BIRTHS] += S.nborn;
       d.stats_step[ST_FAILED_BIRTHS] += S.nwin - S.nborn;
@@ -1383,7 +1404,8 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
     // (the claims stay until the next launch clears them: other CTAs may
     // still be reading them in fast_births)
     const EnvDesc ed = d.env[0];
-    for (int i = g0; i < S.nborn; i += gs) {
+    const int gb = (int)((blockIdx.x + nb - birth_cta) % nb) * (int)blockDim.x + (int)threadIdx.x;
+    for (int i = gb; i < S.nborn; i += gs) {
       const int p = S.win[i];
       make_child(d, R, ed, p, S.free_[i], d.tgt[p], t, false);
     }
