@@ -464,6 +464,30 @@ int eco_policy_only(eco_handle *h, int32_t n_iters);
  * argument out of range.  Synchronises. */
 int eco_arm_barrier_timeout(eco_handle *h, int32_t absent_cta, int32_t poll_budget);
 
+/* Phase trace of the persistent environment kernel (a tracing aid; App. E
+ * describes the simulator's measurement tooling, not this).  on = 1 clears
+ * the trace table and makes every following step record, in the row
+ * step % ECO_TRACE_STEPS, ECO_TRACE_WORDS globaltimer values in ns:
+ *   [0] CTA 0's start; [1 + k] the last CTA's arrival at grid barrier k
+ *   (k = 0..3, 0 when unused; a CTA arrives once all its threads are
+ *   there); [5 + k] CTA 0's pass through barrier k; [9] the last CTA's end;
+ *   [10] the step; [11] the step's birth claimants; [12] the number of grid
+ *   barriers the step used; [13..15] 0.
+ * on = 0 clears the table and stops recording.  Traced steps compute the
+ * same results (the stamps add a block barrier and a few stores per grid
+ * barrier).  eco_reset switches the trace off.  ECO_EINVAL when the
+ * persistent form is not in use (eco_launch_mode; it is decided by
+ * eco_prepare or the first eco_step).  Synchronises. */
+#define ECO_TRACE_STEPS 64
+#define ECO_TRACE_WORDS 16
+int eco_trace_phases(eco_handle *h, int32_t on);
+
+/* Copy the first max_rows (at most ECO_TRACE_STEPS) rows of the trace
+ * table to rows[max_rows][ECO_TRACE_WORDS] (host); *n_rows = rows copied.
+ * Rows of steps not traced since the last eco_trace_phases hold 0.
+ * Synchronises. */
+int eco_read_phase_trace(eco_handle *h, uint64_t *rows, int32_t max_rows, int32_t *n_rows);
+
 /* Algorithmic bytes the policy phase must read for the current alive
  * population (weights of every alive agent in the streamed precision,
  * biases and scales in FP32); synchronises. */

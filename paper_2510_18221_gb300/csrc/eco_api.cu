@@ -308,6 +308,7 @@ static size_t carve(const eco_config *c, const Layout &L, uint8_t *base, Dev *d,
   D.flow = k.take<uint32_t>(cells);
   D.a_water = k.take<int32_t>(slots);
   D.a_bio = k.take<int32_t>(slots);
+  D.trace = k.take<unsigned long long>((size_t)kTraceSteps * kTraceWords);
   // The policy kernel's FP8 tail batches load up to kStreamSlack bytes past
   // the last weight block (their products are skipped): the regions after
   // the weights (the histogram alone is 256 KB per world) keep those loads
@@ -802,6 +803,28 @@ extern "C" int eco_arm_barrier_timeout(eco_handle *h, int32_t absent_cta, int32_
   const unsigned words[2] = {(unsigned)absent_cta + 1u, (unsigned)poll_budget};
   CUDA_TRY(h, cudaMemcpyAsync(h->d.barrier + BAR_ABSENT_CTA, words, sizeof words, cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return ECO_OK;
+}
+
+extern "C" int eco_trace_phases(eco_handle *h, int32_t on) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  const bool pers = h->grid.use_persistent && h->grid.persistent_blocks > 0;
+  if (!pers) return fail(h, ECO_EINVAL, "the phase trace needs the persistent launch form");
+  const unsigned word = on ? 1u : 0u;
+  CUDA_TRY(h, cudaMemsetAsync(h->d.trace, 0, sizeof(unsigned long long) * kTraceSteps * kTraceWords, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d.barrier + BAR_TRACE, &word, sizeof word, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return ECO_OK;
+}
+
+extern "C" int eco_read_phase_trace(eco_handle *h, uint64_t *rows, int32_t max_rows, int32_t *n_rows) {
+  if (!h) return fail(nullptr, ECO_EINVAL, "null handle");
+  if (!rows || max_rows < 0) return fail(h, ECO_EINVAL, "null rows or negative max_rows");
+  const int n = max_rows < kTraceSteps ? max_rows : kTraceSteps;
+  CUDA_TRY(h, cudaMemcpyAsync(rows, h->d.trace, sizeof(uint64_t) * kTraceWords * (size_t)n, cudaMemcpyDeviceToHost,
+                              h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (n_rows) *n_rows = n;
   return ECO_OK;
 }
 

@@ -1317,6 +1317,12 @@ __device__ void fast_births(const Dev &d, BirthSmem &S, int nc) {
   __syncthreads();
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  return v;
+}
+
 __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rules R) {
   extern __shared__ __align__(16) float msm[];
   __shared__ BirthSmem S;
@@ -1334,6 +1340,7 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   // interval while other CTAs still work on this step.
   const uint32_t t = (uint32_t)d.step[0];
   const unsigned absent = d.barrier[BAR_ABSENT_CTA], budget_word = d.barrier[BAR_BUDGET];
+  const unsigned trace_on = d.barrier[BAR_TRACE];
   const int n_alive = d.counters[CNT_N_ALIVE];
   const int first_entry = g0 < d.total_slots ? d.alive_list[g0] : -1;
   // A timeout recorded by an earlier launch (the status word keeps it until
@@ -1349,6 +1356,26 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   const unsigned budget = budget_word ? budget_word : kBarrierSpinLimit;
   unsigned *count = d.barrier + BAR_COUNT0 + (t & 1u);
   unsigned bar = 0;  // barriers passed in this launch (the same sequence in every CTA)
+  // Phase trace (eco_trace_phases): this step's row; CTA 0 clears the next
+  // step's row (its maxima must start at 0).
+  unsigned long long *trow = trace_on ? d.trace + (size_t)(t % kTraceSteps) * kTraceWords : nullptr;
+  if (trow && blockIdx.x == 0) {
+    if (threadIdx.x < kTraceWords) d.trace[(size_t)((t + 1u) % kTraceSteps) * kTraceWords + threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) {
+      trow[TR_START] = global_ns();
+      trow[TR_STEP] = (unsigned long long)t;
+    }
+  }
+  // the grid barrier, with the trace's arrival and pass stamps
+  auto sync = [&]() -> bool {
+    if (trow) {
+      __syncthreads();
+      if (threadIdx.x == 0) atomicMax(trow + TR_ARRIVE0 + bar, global_ns());
+    }
+    const bool ok = grid_sync(count, d.counters + CNT_STATUS, nb, budget, bar, &s_flag);
+    if (trow && blockIdx.x == 0 && threadIdx.x == 0) trow[TR_PASS0 + bar - 1] = global_ns();
+    return ok;
+  };
   // Housekeeping goes to CTAs with little else to do in its interval: the
   // per-agent phases take one agent per thread from CTA 0 on, and the
   // alive list's tiles go to CTAs 0 .. tiles - 1.
@@ -1365,9 +1392,9 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   }
   const int first = g0 < n_alive ? first_entry : -1;
   ph_move_apply_eat(d, R, L.A, g0, gs, first, t);
-  if (!grid_sync(count, d.counters + CNT_STATUS, nb, budget, bar, &s_flag)) return;
+  if (!sync()) return;
   ph_metab_death(d, R, g0, gs, first, t);
-  if (!grid_sync(count, d.counters + CNT_STATUS, nb, budget, bar, &s_flag)) return;
+  if (!sync()) return;
   // regrowth (with photosynthesis and the flow's transfers) needs only the
   // state after the deaths, and birth claims read only wall and agent bits,
   // which regrowth keeps: the two share an interval
@@ -1375,17 +1402,18 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   if (d.n_envs == 1 && compact_tiles(d.total_slots) <= kMaxFastTiles) list_free_slots(d, S.sh);
   ph_regrow(d, R, g0, gs, t);
   if (R.rules == RULES_TERRAIN) ph_flow_out(d, g0, gs);
-  if (!grid_sync(count, d.counters + CNT_STATUS, nb, budget, bar, &s_flag)) return;
+  if (!sync()) return;
   // Every claim is in, and the count of claimants does not change again
   // in this launch, so every CTA takes the same branch.
   const int claimants = cuda::atomic_ref<int, cuda::thread_scope_device>(d.counters[CNT_CONTENDERS]).load(
       cuda::memory_order_relaxed);
   const bool fast = claimants > 0 && d.n_envs == 1 && claimants <= kFastBirths &&
                     compact_tiles(d.total_slots) <= kMaxFastTiles;
+  if (trow && blockIdx.x == 0 && threadIdx.x == 0) trow[TR_CLAIMANTS] = (unsigned long long)claimants;
   if (claimants > 0 && !fast) {
     // general path: one CTA per environment assigns the slots, then a barrier
     ph_birth_assign(d, R, blockIdx.x, gridDim.x, S, t);
-    if (!grid_sync(count, d.counters + CNT_STATUS, nb, budget, bar, &s_flag)) return;
+    if (!sync()) return;
   } else if (fast) {
     fast_births(d, S, claimants);
   }
@@ -1419,6 +1447,13 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   if (claimants > 0)
     ph_mutate(d, L, R, gridDim.x - 1 - blockIdx.x, gridDim.x, msm, s_scale, t, fast ? S.win : nullptr,
               fast ? S.free_ : nullptr, fast ? S.nborn : 0);
+  if (trow) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicMax(trow + TR_END, global_ns());
+      if (blockIdx.x == 0) trow[TR_BARRIERS] = bar;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

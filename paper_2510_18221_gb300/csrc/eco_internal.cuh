@@ -34,6 +34,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "eco.h"
+
 namespace eco {
 
 enum : uint32_t {
@@ -283,6 +285,7 @@ struct Dev {
   int32_t *tile_counts;  // [2][compact tiles] alive slots per tile of 4096, per step parity
                          // (kept by deaths and births)
   unsigned *barrier;     // [BAR_N] grid barrier of the persistent form and its test words
+  unsigned long long *trace;  // [kTraceSteps][kTraceWords] phase trace (written only when on)
   int32_t *counters;    // [0] n_alive, [1] n_births, [2] status, [3..] spare
   int2 *births;         // (parent global, child global)
   int32_t *free_list;   // per env: slot_off + rank (free slots in ascending order); one
@@ -326,13 +329,33 @@ constexpr int kStreamSlack = 4096;
 // (one per step parity: a launch uses its step's word and clears the other
 // for the next launch) and two failure-detection test words (0 = off: one
 // more than the index of a CTA that leaves before its first barrier, and the
-// poll budget of the barrier's waits).
+// poll budget of the barrier's waits), and the phase-trace switch (0 = off).
 enum : int {
   BAR_COUNT0 = 0,
   BAR_COUNT1 = 1,
   BAR_ABSENT_CTA = 2,
   BAR_BUDGET = 3,
-  BAR_N = 4,
+  BAR_TRACE = 4,
+  BAR_N = 5,
+};
+
+// Phase trace of the persistent environment kernel (off unless switched
+// on): one row of kTraceWords globaltimer values (ns) per step, row
+// step % kTraceSteps.  Words: TR_START CTA 0's start; TR_ARRIVE0 + k the
+// last CTA's arrival at grid barrier k (0..3; a CTA records its arrival once
+// all its threads are there); TR_PASS0 + k CTA 0's pass through barrier k;
+// TR_END the last CTA's end; TR_STEP the step; TR_CLAIMANTS this step's
+// birth claimants; TR_BARRIERS the grid barriers the step used.
+constexpr int kTraceSteps = ECO_TRACE_STEPS;
+constexpr int kTraceWords = ECO_TRACE_WORDS;
+enum : int {
+  TR_START = 0,
+  TR_ARRIVE0 = 1,  // .. 4
+  TR_PASS0 = 5,    // .. 8
+  TR_END = 9,
+  TR_STEP = 10,
+  TR_CLAIMANTS = 11,
+  TR_BARRIERS = 12,
 };
 
 enum : int {

@@ -113,6 +113,8 @@ def lib() -> ctypes.CDLL:
         L.eco_reset.argtypes = [H]
         L.eco_reset_seed.argtypes = [H, ctypes.c_uint64]
         L.eco_arm_barrier_timeout.argtypes = [H, ctypes.c_int32, ctypes.c_int32]
+        L.eco_trace_phases.argtypes = [H, ctypes.c_int32]
+        L.eco_read_phase_trace.argtypes = [H, _vp, ctypes.c_int32, _i32p]
         L.eco_step.argtypes = [H, ctypes.c_int32]
         L.eco_step_timed.argtypes = [H, ctypes.c_int32]
         L.eco_prepare.argtypes = [H]
@@ -191,6 +193,23 @@ def eco_reset_seed(h, seed: int) -> None:
 def eco_arm_barrier_timeout(h, absent_cta: int, poll_budget: int) -> None:
     """Failure-detection test hook (see include/eco.h)."""
     _check(lib().eco_arm_barrier_timeout(h, int(absent_cta), int(poll_budget)), h)
+
+
+ECO_TRACE_STEPS = 64
+ECO_TRACE_WORDS = 16
+
+
+def eco_trace_phases(h, on: bool) -> None:
+    """Switch the environment kernel's phase trace on or off (see include/eco.h)."""
+    _check(lib().eco_trace_phases(h, 1 if on else 0), h)
+
+
+def eco_read_phase_trace(h) -> np.ndarray:
+    """The trace table, uint64 [ECO_TRACE_STEPS][ECO_TRACE_WORDS]."""
+    rows = np.zeros((ECO_TRACE_STEPS, ECO_TRACE_WORDS), np.uint64)
+    n = ctypes.c_int32()
+    _check(lib().eco_read_phase_trace(h, rows.ctypes.data, ECO_TRACE_STEPS, ctypes.byref(n)), h)
+    return rows[:n.value]
 
 
 def eco_step(h, n_steps: int) -> None:
@@ -378,6 +397,12 @@ class Env:
 
     def policy_bytes(self):
         return eco_policy_bytes(self.h)
+
+    def trace_phases(self, on: bool = True) -> None:
+        eco_trace_phases(self.h, on)
+
+    def phase_trace(self) -> np.ndarray:
+        return eco_read_phase_trace(self.h)
 
     def launch_mode(self):
         """(0 persistent / 1 one kernel per phase, persistent CTAs)."""

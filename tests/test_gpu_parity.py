@@ -231,6 +231,51 @@ def test_full_scan_birth_assignment(slots, launch_mode):
         env.close()
 
 
+def test_phase_trace_changes_nothing_and_is_ordered():
+    """Steps with the environment kernel's phase trace on give the same
+    state and statistics bit for bit as steps without it, and every traced
+    row is ordered: the last CTA arrives at a barrier before CTA 0 passes
+    it, arrives at the next barrier after that, and ends last."""
+    from paper_2510_18221_gb300 import eco
+    w = workloads.scaled("mid", 256, 8192, 6000, precision="bf16", e_init=185, seed=3)
+    a, b = eco.Env(w), eco.Env(w)
+    try:
+        for x in (a, b):
+            x.reset()
+            x.prepare()
+        if a.launch_mode()[0] != 0:
+            pytest.skip("the persistent launch form is not in use")
+        a.trace_phases(True)
+        a.step(12)
+        b.step(12)
+        sa, sb = a.read_state(0), b.read_state(0)
+        for k in harness.STATE_KEYS:
+            assert np.array_equal(sa[k], sb[k]), k
+        assert a.stats()[0] == b.stats()[0]
+        assert np.array_equal(a.read_params(0), b.read_params(0))
+        rows = a.phase_trace().astype(np.int64)
+        rows = rows[rows[:, 0] > 0]
+        assert len(rows) == 12
+        assert sorted(rows[:, 10].tolist()) == list(range(int(rows[:, 10].min()), int(rows[:, 10].min()) + 12))
+        for r in rows:
+            nbar = int(r[12])
+            assert nbar in (3, 4)
+            prev = r[0]                         # CTA 0's start
+            for k in range(nbar):
+                # the last arrival at k follows CTA 0's pass through k - 1
+                # (CTA 0 arrives at k after it), and CTA 0 passes k after it
+                assert r[1 + k] >= prev and r[5 + k] >= r[1 + k], (r.tolist(), k)
+                prev = r[5 + k]
+            assert r[9] >= prev
+        assert (rows[:, 11] > 0).any()          # births were claimed in some traced steps
+        a.trace_phases(False)
+        a.step(2)
+        assert (a.phase_trace() == 0).all()     # off: nothing recorded
+    finally:
+        a.close()
+        b.close()
+
+
 def test_barrier_timeout_is_reported_and_reset_recovers():
     """Failure detection without a GPU fault: one CTA of the persistent
     environment kernel leaves before its first grid barrier (the hook
