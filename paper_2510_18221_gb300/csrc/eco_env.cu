@@ -849,6 +849,38 @@ __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0,
   }
 }
 
+// The mutation on one CTA (the persistent kernel's one-CTA form, for small
+// batches), FP32 and BF16 forms: every parameter of every child is an
+// independent element -- its normal comes from the Philox block of its
+// logical index, as in ph_mutate -- so the CTA's threads take elements
+// across children and layers with no block barrier between tiles.  The
+// same draws and fmaf as ph_mutate, so the same values bit for bit; each
+// element draws its own Philox block (four times the arithmetic of the
+// tiled form, which a lone CTA's latency outweighs).
+__device__ void ph_mutate_flat(const Dev &d, const Layout &L, const Rules &R, uint32_t t, const int *par,
+                               const int *chi, int nbirths) {
+  const int nb = par ? nbirths : d.counters[CNT_N_BIRTHS];
+  const int P = L.nW + L.nB;  // physical master elements: weights, then biases (and tau)
+  const int64_t mper = L.mstride / 4;
+  for (int w = threadIdx.x; w < nb * P; w += blockDim.x) {
+    const int b = w / P, q = w - b * P;
+    const int2 pc = par ? make_int2(par[b], chi[b]) : d.births[b];
+    const EnvDesc ed = d.env[env_index(d, pc.y)];
+    const uint32_t lp = (uint32_t)(pc.x - ed.slot_off);
+    const int p = layout_logical(L, q);
+    const U4 r = philox(t, lp, (uint32_t)(p >> 2), 0u, ed.seed, S_MUTATE);
+    const float v = fmaf(R.sigma, normal_of(r, p & 3), __ldg(d.master + (int64_t)pc.x * mper + q));
+    d.master[(int64_t)pc.y * mper + q] = v;
+    if (R.precision == PREC_BF16) {
+      uint8_t *cq = d.wq + (int64_t)pc.y * L.stride;
+      if (q < L.nW)
+        reinterpret_cast<__nv_bfloat16 *>(cq)[q] = __float2bfloat16_rn(v);
+      else
+        reinterpret_cast<float *>(cq + L.off_bias)[q - L.nW] = v;
+    }
+  }
+}
+
 // Shared memory of the mutation: a tile of kMutRows rows of nin + 1 floats,
 // where nin is D for W_in and H for the hidden layers (D may be below H: an
 // agent without a vision sensor), or the head's A x H rows.
@@ -1444,9 +1476,13 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   // the alive list from the first.
   if (R.rules == RULES_TERRAIN) ph_flow_in(d, g0, gs);
   ph_compact_scatter(d, blockIdx.x, gridDim.x, S.sh, t, fast ? S.free_ : nullptr, fast ? S.nborn : 0, S.cmask);
-  if (claimants > 0)
-    ph_mutate(d, L, R, gridDim.x - 1 - blockIdx.x, gridDim.x, msm, s_scale, t, fast ? S.win : nullptr,
-              fast ? S.free_ : nullptr, fast ? S.nborn : 0);
+  if (claimants > 0) {
+    if (nb == 1 && R.precision != PREC_FP8)
+      ph_mutate_flat(d, L, R, t, fast ? S.win : nullptr, fast ? S.free_ : nullptr, fast ? S.nborn : 0);
+    else
+      ph_mutate(d, L, R, gridDim.x - 1 - blockIdx.x, gridDim.x, msm, s_scale, t, fast ? S.win : nullptr,
+                fast ? S.free_ : nullptr, fast ? S.nborn : 0);
+  }
   if (trow) {
     __syncthreads();
     if (threadIdx.x == 0) {
