@@ -849,20 +849,21 @@ __device__ void ph_mutate(const Dev &d, const Layout &L, const Rules &R, int b0,
   }
 }
 
-// The mutation on one CTA (the persistent kernel's one-CTA form, for small
-// batches), FP32 and BF16 forms: every parameter of every child is an
-// independent element -- its normal comes from the Philox block of its
-// logical index, as in ph_mutate -- so the CTA's threads take elements
-// across children and layers with no block barrier between tiles.  The
-// same draws and fmaf as ph_mutate, so the same values bit for bit; each
-// element draws its own Philox block (four times the arithmetic of the
-// tiled form, which a lone CTA's latency outweighs).
+// The mutation in the persistent kernel, FP32 and BF16 forms (FP8 needs
+// each row's maximum first and keeps ph_mutate's tiles): every parameter of
+// every child is an independent element -- its normal comes from the
+// Philox block of its logical index, as in ph_mutate -- so the grid's
+// threads (g0, stride gs) take elements across children and layers with
+// no block barrier between tiles.  The same draws and fmaf as ph_mutate,
+// so the same values bit for bit; each element draws its own Philox block
+// (four times the arithmetic of the tiled form, which the tiles' barriers
+// and dependent loads outweigh).
 __device__ void ph_mutate_flat(const Dev &d, const Layout &L, const Rules &R, uint32_t t, const int *par,
-                               const int *chi, int nbirths) {
+                               const int *chi, int nbirths, int g0, int gs) {
   const int nb = par ? nbirths : d.counters[CNT_N_BIRTHS];
   const int P = L.nW + L.nB;  // physical master elements: weights, then biases (and tau)
   const int64_t mper = L.mstride / 4;
-  for (int w = threadIdx.x; w < nb * P; w += blockDim.x) {
+  for (int w = g0; w < nb * P; w += gs) {
     const int b = w / P, q = w - b * P;
     const int2 pc = par ? make_int2(par[b], chi[b]) : d.births[b];
     const EnvDesc ed = d.env[env_index(d, pc.y)];
@@ -894,6 +895,53 @@ size_t mutate_smem_bytes(const Layout &L) {
 // share one Philox block (counter (step, local cell / 4)).
 __device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs, uint32_t t) {
   const int groups = d.total_cells >> 2;
+  if (R.rules != RULES_TERRAIN) {
+    // kRG of this thread's groups per round, their cell bytes loaded
+    // together (the loop's stores would otherwise hold each load behind the
+    // previous group's); the regrown count is kept per environment and
+    // added once per environment (groups ascend, so environments do).
+    constexpr int kRG = 4;
+    int e = -1, grown_e = 0;
+    EnvDesc ed = d.env[0];
+    for (int gb = g0; gb < groups; gb += kRG * gs) {
+      uchar4 cfv[kRG];
+#pragma unroll
+      for (int k = 0; k < kRG; ++k) {
+        const int g = gb + k * gs;
+        cfv[k] = g < groups ? reinterpret_cast<const uchar4 *>(d.cellf)[g] : make_uchar4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int k = 0; k < kRG; ++k) {
+        const int g = gb + k * gs;
+        if (g >= groups) break;
+        const int c0 = g << 2;
+        if (e < 0 || (e + 1 < d.n_envs && d.env[e + 1].cell_off <= c0)) {
+          if (e >= 0) stat_add(d.stats_step, e, ST_REGROWN, grown_e);
+          grown_e = 0;
+          e = env_of_cell(d.env, d.n_envs, c0);
+          ed = d.env[e];
+        }
+        uchar4 cf = cfv[k];
+        const bool any = !((cf.x & (CELL_WALL | CELL_FOOD)) && (cf.y & (CELL_WALL | CELL_FOOD)) &&
+                           (cf.z & (CELL_WALL | CELL_FOOD)) && (cf.w & (CELL_WALL | CELL_FOOD)));
+        if (!any) continue;
+        const U4 r = philox(t, (uint32_t)((c0 - ed.cell_off) >> 2), 0u, 0u, ed.seed, S_REGROW);
+        int mask = 0;
+        if (!(cf.x & (CELL_WALL | CELL_FOOD)) && r.x < R.thr_regrow) { cf.x |= CELL_FOOD; mask |= 1; }
+        if (!(cf.y & (CELL_WALL | CELL_FOOD)) && r.y < R.thr_regrow) { cf.y |= CELL_FOOD; mask |= 2; }
+        if (!(cf.z & (CELL_WALL | CELL_FOOD)) && r.z < R.thr_regrow) { cf.z |= CELL_FOOD; mask |= 4; }
+        if (!(cf.w & (CELL_WALL | CELL_FOOD)) && r.w < R.thr_regrow) { cf.w |= CELL_FOOD; mask |= 8; }
+        if (!mask) continue;
+        grown_e += __popc(mask);
+        if (R.rules == RULES_PAPER)  // one bite of energy on each regrown cell
+          for (int q = 0; q < 4; ++q)
+            if (mask & (1 << q)) d.res[c0 + q] = R.e_food;
+        reinterpret_cast<uchar4 *>(d.cellf)[g] = cf;
+      }
+    }
+    if (e >= 0) stat_add(d.stats_step, e, ST_REGROWN, grown_e);
+    return;
+  }
   for (int g = g0; g < groups; g += gs) {
     const int c0 = g << 2;
     const int e = env_of_cell(d.env, d.n_envs, c0);
@@ -1477,8 +1525,9 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   if (R.rules == RULES_TERRAIN) ph_flow_in(d, g0, gs);
   ph_compact_scatter(d, blockIdx.x, gridDim.x, S.sh, t, fast ? S.free_ : nullptr, fast ? S.nborn : 0, S.cmask);
   if (claimants > 0) {
-    if (nb == 1 && R.precision != PREC_FP8)
-      ph_mutate_flat(d, L, R, t, fast ? S.win : nullptr, fast ? S.free_ : nullptr, fast ? S.nborn : 0);
+    if (R.precision != PREC_FP8)
+      ph_mutate_flat(d, L, R, t, fast ? S.win : nullptr, fast ? S.free_ : nullptr, fast ? S.nborn : 0,
+                     (int)((gridDim.x - 1 - blockIdx.x) * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x));
     else
       ph_mutate(d, L, R, gridDim.x - 1 - blockIdx.x, gridDim.x, msm, s_scale, t, fast ? S.win : nullptr,
                 fast ? S.free_ : nullptr, fast ? S.nborn : 0);

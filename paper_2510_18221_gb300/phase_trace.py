@@ -6,7 +6,7 @@ the last CTA arrived and when CTA 0 passed it, and when the last CTA ended,
 in microseconds from CTA 0's start (median, min and max over the steps;
 steps with and without birth claimants apart for the end).
 
-    python -m paper_2510_18221_gb300.phase_trace [--workload paper]
+    python -m paper_2510_18221_gb300.phase_trace [--workload paper|batched|...]
         [--precision bf16] [--warmup 5] [--steps 60] [--json]
 """
 from __future__ import annotations
@@ -60,8 +60,13 @@ def main() -> None:
     from . import eco, workloads
 
     over = {} if args.precision is None else {"precision": args.precision}
-    w = workloads.get(args.workload, **over)
-    env = eco.Env(w)
+    if args.workload == "batched":
+        # the 64 uneven worlds of the batched workload, in one handle
+        envs = workloads.batched(64, **over)
+        w = {"name": "batched-64worlds-%s" % envs[0]["precision"]}
+    else:
+        envs = w = workloads.get(args.workload, **over)
+    env = eco.Env(envs)
     try:
         env.reset()
         env.prepare()
