@@ -579,7 +579,7 @@ static int autotune(eco_handle *h) {
   // warm-up each, then kRounds rounds that time kPerRound launches of every
   // candidate in turn, so that a drift in clocks or memory state over the
   // tuning affects every candidate alike; the lowest total wins
-  constexpr int kRounds = 3, kPerRound = 3;
+  constexpr int kRounds = 5, kPerRound = 3;
   struct EventPair {  // destroyed on every return path
     cudaEvent_t a = nullptr, b = nullptr;
     ~EventPair() {
@@ -606,16 +606,6 @@ static int autotune(eco_handle *h) {
   size_t best = 0;
   for (size_t c = 1; c < ids.size(); ++c)
     if (total[c] < total[best]) best = c;
-  // Timed alone, variants that differ only in their resident warps can tie
-  // while the step still tells them apart: inside the step (after the
-  // environment kernel) the one with more warps resident hides more
-  // latency (the paper workload: 56 against 64 registers ran 1.5% faster
-  // in the step at equal policy-only times).  Within 0.3% of the fastest,
-  // the most resident warps win.
-  const double tie = total[best] * 1.003;
-  for (size_t c = 0; c < ids.size(); ++c)
-    if (total[c] <= tie && (long long)pls[c].blocks * pls[c].threads > (long long)pls[best].blocks * pls[best].threads)
-      best = c;
   h->variant = ids[best];
   h->pl = pls[best];
   return ECO_OK;
