@@ -942,16 +942,32 @@ __device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs, uint32_t
     if (e >= 0) stat_add(d.stats_step, e, ST_REGROWN, grown_e);
     return;
   }
+  // terrain rules: one group per round (its biomass, energy and remainders
+  // are loaded as 16-byte vectors); the counts are kept per environment
+  int e = -1, grown_e = 0, refilled_e = 0;
+  long long photo_e = 0;
+  EnvDesc ed = d.env[0];
+  auto flush = [&]() {
+    if (e < 0) return;
+    stat_add(d.stats_step, e, ST_REGROWN, grown_e);
+    stat_add(d.stats_step, e, ST_FOOD_REFILLED, refilled_e);
+    stat_add(d.stats_step, e, ST_PHOTO, (int)photo_e);
+    grown_e = refilled_e = 0;
+    photo_e = 0;
+  };
   for (int g = g0; g < groups; g += gs) {
     const int c0 = g << 2;
-    const int e = env_of_cell(d.env, d.n_envs, c0);
-    const EnvDesc ed = d.env[e];
+    if (e < 0 || (e + 1 < d.n_envs && d.env[e + 1].cell_off <= c0)) {
+      flush();
+      e = env_of_cell(d.env, d.n_envs, c0);
+      ed = d.env[e];
+    }
     uchar4 cf = reinterpret_cast<uchar4 *>(d.cellf)[g];
-    // terrain: the group's biomass, remainders and energy, loaded together
-    // (the loads are independent; the chain per cell was the phase's cost)
-    int bio[4] = {0, 0, 0, 0}, res[4] = {0, 0, 0, 0};
-    uint32_t pho[4] = {0u, 0u, 0u, 0u};
-    if (R.rules == RULES_TERRAIN) {
+    // the group's biomass, remainders and energy, loaded together (the
+    // loads are independent; the chain per cell was the phase's cost)
+    int bio[4], res[4];
+    uint32_t pho[4];
+    {
       const int4 b4 = reinterpret_cast<const int4 *>(d.bio)[g];
       const int4 r4 = reinterpret_cast<const int4 *>(d.res)[g];
       const uint4 p4 = reinterpret_cast<const uint4 *>(d.photo)[g];
@@ -962,7 +978,8 @@ __device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs, uint32_t
     int grown = 0;
     const bool any = !((cf.x & (CELL_WALL | CELL_FOOD)) && (cf.y & (CELL_WALL | CELL_FOOD)) &&
                        (cf.z & (CELL_WALL | CELL_FOOD)) && (cf.w & (CELL_WALL | CELL_FOOD)));
-    if (any) {
+    // a zero threshold (no random regrowth) grows nothing: no draw needed
+    if (any && R.thr_regrow != 0u) {
       const U4 r = philox(t, (uint32_t)((c0 - ed.cell_off) >> 2), 0u, 0u, ed.seed, S_REGROW);
       int mask = 0;
       if (!(cf.x & (CELL_WALL | CELL_FOOD)) && r.x < R.thr_regrow) { cf.x |= CELL_FOOD; mask |= 1; }
@@ -970,48 +987,39 @@ __device__ void ph_regrow(const Dev &d, const Rules &R, int g0, int gs, uint32_t
       if (!(cf.z & (CELL_WALL | CELL_FOOD)) && r.z < R.thr_regrow) { cf.z |= CELL_FOOD; mask |= 4; }
       if (!(cf.w & (CELL_WALL | CELL_FOOD)) && r.w < R.thr_regrow) { cf.w |= CELL_FOOD; mask |= 8; }
       grown = __popc(mask);
-      if (grown && R.rules == RULES_PAPER)  // one bite of energy on each regrown cell
-        for (int k = 0; k < 4; ++k)
-          if (mask & (1 << k)) d.res[c0 + k] = R.e_food;
-      if (R.rules == RULES_TERRAIN)  // the same, in the group's registers
-        for (int k = 0; k < 4; ++k)
-          if (mask & (1 << k)) res[k] = R.e_food;
+      for (int k = 0; k < 4; ++k)  // one bite of energy on each regrown cell, in the group's registers
+        if (mask & (1 << k)) res[k] = R.e_food;
     }
     bool changed = grown != 0;
-    if (R.rules == RULES_TERRAIN) {
-      // energy grows on free biomass: a 2^-16 fixed-point remainder per cell
-      // makes the sum over steps exact; at most res_cap energy per cell
-      uint8_t *cfb = reinterpret_cast<uint8_t *>(&cf);
-      int refilled = 0;
-      long long grew = 0;
-      bool touched = grown != 0;
-      for (int k = 0; k < 4; ++k) {
-        const int b = bio[k];
-        if ((cfb[k] & CELL_WALL) || b <= 0) continue;
-        const unsigned long long acc = (unsigned long long)pho[k] + (unsigned long long)b * (unsigned)R.photo_q16;
-        pho[k] = (uint32_t)(acc & 0xFFFFull);
-        touched = true;
-        const int r = res[k];
-        const long long gain = min((long long)(acc >> 16), (long long)R.res_cap - r);
-        if (gain <= 0) continue;
-        if (r == 0) {
-          cfb[k] |= (uint8_t)CELL_FOOD;
-          ++refilled;
-          changed = true;
-        }
-        res[k] = r + (int)gain;
-        grew += gain;
+    // energy grows on free biomass: a 2^-16 fixed-point remainder per cell
+    // makes the sum over steps exact; at most res_cap energy per cell
+    uint8_t *cfb = reinterpret_cast<uint8_t *>(&cf);
+    bool touched = grown != 0;
+    for (int k = 0; k < 4; ++k) {
+      const int b = bio[k];
+      if ((cfb[k] & CELL_WALL) || b <= 0) continue;
+      const unsigned long long acc = (unsigned long long)pho[k] + (unsigned long long)b * (unsigned)R.photo_q16;
+      pho[k] = (uint32_t)(acc & 0xFFFFull);
+      touched = true;
+      const int r = res[k];
+      const long long gain = min((long long)(acc >> 16), (long long)R.res_cap - r);
+      if (gain <= 0) continue;
+      if (r == 0) {
+        cfb[k] |= (uint8_t)CELL_FOOD;
+        ++refilled_e;
+        changed = true;
       }
-      if (touched) {
-        reinterpret_cast<int4 *>(d.res)[g] = make_int4(res[0], res[1], res[2], res[3]);
-        reinterpret_cast<uint4 *>(d.photo)[g] = make_uint4(pho[0], pho[1], pho[2], pho[3]);
-      }
-      stat_add(d.stats_step, e, ST_FOOD_REFILLED, refilled);
-      stat_add(d.stats_step, e, ST_PHOTO, (int)grew);
+      res[k] = r + (int)gain;
+      photo_e += gain;
+    }
+    if (touched) {
+      reinterpret_cast<int4 *>(d.res)[g] = make_int4(res[0], res[1], res[2], res[3]);
+      reinterpret_cast<uint4 *>(d.photo)[g] = make_uint4(pho[0], pho[1], pho[2], pho[3]);
     }
     if (changed) reinterpret_cast<uchar4 *>(d.cellf)[g] = cf;
-    stat_add(d.stats_step, e, ST_REGROWN, grown);
+    grown_e += grown;
   }
+  flush();
 }
 
 // Terrain rules, water flow (Sec. 3.2 "Terrain"), part 1: each cell's
