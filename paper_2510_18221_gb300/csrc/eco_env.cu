@@ -1421,11 +1421,12 @@ __global__ void __launch_bounds__(1024, 1) k_env_persistent(Dev d, Layout L, Rul
   // The launch's first reads, issued together: the step, the failure-
   // detection test words (0 unless armed by eco_arm_barrier_timeout,
   // cleared by eco_reset: a CTA that leaves before its first barrier, and the
-  // poll budget of every wait), the alive count and each thread's first
-  // alive-list entry (loaded once for all phases; the list has total_slots
-  // entries, so the read stays in bounds even past the count).  Every phase
-  // takes the step from here: CTA 0 advances the step word in the last
-  // interval while other CTAs still work on this step.
+  // poll budget of every wait), the phase-trace switch, the alive count and
+  // each thread's first alive-list entry (loaded once for all phases; the
+  // list has total_slots entries, so the read stays in bounds even past the
+  // count).  Every phase takes the step from here: the statistics CTA
+  // advances the step word in the last interval while other CTAs still work
+  // on this step.
   const uint32_t t = (uint32_t)d.step[0];
   const unsigned absent = d.barrier[BAR_ABSENT_CTA], budget_word = d.barrier[BAR_BUDGET];
   const unsigned trace_on = d.barrier[BAR_TRACE];
